@@ -1,0 +1,173 @@
+/*
+ * fnvmc.h - C ABI of the GB300 (sm_103a) variational Monte Carlo hot path.
+ *
+ * The library evaluates a permutation-equivariant fermionic neural-network
+ * wavefunction (method section "FermiNet Model", Eq. 4 envelope) for batches of
+ * walkers, its exact local energy (Eqs. 1-3, exact forward-mode Laplacian), runs
+ * Metropolis-Hastings on |psi|^2 (section "Electron Sampler"), assigns electrons
+ * to atoms with the ionic charge initialisation (Algorithm 1) and computes the
+ * VMC energy gradient (Eq. 6).  Every step runs in the library's CUDA kernels;
+ * there is no CPU fallback.
+ *
+ * Conventions shared by all entry points
+ *   - Lengths in bohr, energies in hartree.
+ *   - d_* pointers are device memory owned by the caller; h_* pointers are host
+ *     memory owned by the caller.  The library owns the system handle and an
+ *     internal device workspace that grows on demand (cudaMalloc happens only
+ *     when a call needs more walkers than any previous call on that handle;
+ *     make such a call once before capturing a stream into a CUDA graph).
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *     void*; NULL is the legacy default stream).  Argument errors return
+ *     immediately and leave device memory untouched.  Numerical problems found
+ *     on the device (non-finite log|psi| or local energy, singular
+ *     determinants of every term) are recorded in a device status word and
+ *     reported by fn_sync() as FN_ERR_NUMERIC.
+ *   - Precision modes fix the dtypes:
+ *       FN_FP64        params double, walkers double, all arithmetic FP64;
+ *       FN_FP32        params float,  walkers float,  all arithmetic FP32
+ *                      (energies accumulated and returned in FP64);
+ *       FN_BF16_MIXED  params float,  walkers float; stream-layer and
+ *                      Laplacian-tangent contractions on tcgen05 tensor cores
+ *                      with BF16 operands and FP32 accumulation; elementwise
+ *                      work FP32; determinants, their inverse-based gradient and
+ *                      Laplacian terms and the local-energy assembly in FP64.
+ *   - Walkers are stored [B][N][3]; electrons 0..n_up-1 are spin up, the rest
+ *     spin down.  Walker index w in a call is global index walker_offset + w
+ *     for the random streams (see fn_set_walker_offset).
+ *   - The handle is not thread-safe: calls on one handle must not overlap in
+ *     time from different host threads, and calls on one handle enqueued on
+ *     different streams must be ordered by the caller (they share a workspace).
+ *   - fn_last_error() returns a thread-local message for the last failing call.
+ */
+#ifndef FNVMC_H
+#define FNVMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FN_OK = 0,
+  FN_ERR_ARG = 1,         /* invalid argument or size                           */
+  FN_ERR_OOM = 2,         /* device allocation failed                           */
+  FN_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed        */
+  FN_ERR_TIMEOUT = 4,     /* fn_sync deadline passed before the stream drained  */
+  FN_ERR_NUMERIC = 5,     /* non-finite or singular result recorded on device   */
+  FN_ERR_EMPTY = 6,       /* system with no electrons                           */
+  FN_ERR_UNSUPPORTED = 7  /* configuration outside the compiled kernel limits   */
+} fn_status;
+
+typedef enum { FN_FP64 = 0, FN_FP32 = 1, FN_BF16_MIXED = 2 } fn_precision;
+typedef enum { FN_ENV_ISOTROPIC = 0, FN_ENV_ANISOTROPIC = 1 } fn_envelope;
+
+/* Network sizes ("FermiNet Model" section):
+ *   n_layers  one-electron stream layers L >= 1 (the two-electron stream has L-1);
+ *   h1        one-electron width, 1..1024, multiple of 8 in FN_BF16_MIXED;
+ *   h2        two-electron width, 1..32;
+ *   n_dets    determinants K, 1..64;
+ *   envelope  fn_envelope: scalar sigma per (k, i, m, spin) or 3x3 sigma (Eq. 4);
+ *   precision fn_precision.                                                      */
+typedef struct {
+  int n_layers, h1, h2, n_dets;
+  int envelope;
+  int precision;
+} fn_net_config;
+
+typedef struct fn_system* fn_system_t;
+
+/* Creates a system: M nuclei at h_nuclei[M][3] with charges h_charges[M]
+ * (integer-valued), n_up + n_down electrons (1..32 in total, each spin <= 16),
+ * and a network configuration.  The ionic charge t = sum Z - n_up - n_down is
+ * derived.  The default electron assignment is Algorithm 1 with partial
+ * charges t/M for every atom.  Returns FN_ERR_EMPTY for zero electrons.     */
+fn_status fn_create_system(const double* h_nuclei, const double* h_charges, int n_nuclei,
+                           int n_up, int n_down, const fn_net_config* cfg, fn_system_t* out);
+fn_status fn_destroy_system(fn_system_t sys);
+
+/* Number of entries of the flat parameter blob (dtype per precision mode).
+ * Blob order: for each layer l: V_l [h1][3 d_h + 2 d_g] (columns: h_i, mean
+ * up h, mean down h, mean up g_i., mean down g_i.), b_l [h1], and for
+ * l < L-1: W_l [h2][d_g], c_l [h2]  (d_h = 4M, d_g = 4 at l = 0, else h1, h2);
+ * then w_up [K n_up][h1], g_up [K n_up], w_down, g_down; then pi_up [K n_up][M],
+ * sigma_up [K n_up][M] or [K n_up][M][3][3], pi_down, sigma_down.  Orbital rows
+ * are ordered k * n_spin + i.  Spin blocks with no electron are absent.      */
+int64_t fn_param_count(fn_system_t sys);
+
+/* Device workspace bytes a call with n_walkers walkers needs (for admission). */
+int64_t fn_workspace_bytes(fn_system_t sys, int n_walkers);
+
+/* Global index of walker 0 in the random streams (default 0), so that a batch
+ * split across devices draws the same numbers as one device.               */
+fn_status fn_set_walker_offset(fn_system_t sys, uint64_t walker_offset);
+
+/* Algorithm 1 (ionic charge initialisation) followed by the spin split, on
+ * the host.  h_partial_charges[M] are Mulliken-style partial charges, or NULL
+ * for t/M each.  Ties go to the lowest atom index; an atom with no electron
+ * left is skipped when removing.  Writes per-atom counts h_counts_out[M] and
+ * the atom of every electron h_electron_atoms_out[N] (either may be NULL) and
+ * makes this the system's assignment for fn_init_walkers.                   */
+fn_status fn_assign_electrons(fn_system_t sys, const double* h_partial_charges,
+                              int* h_counts_out, int* h_electron_atoms_out);
+
+/* Parameter initialisation: dense weights and biases N(0,1)/sqrt(fan_in) from
+ * the Philox4x32-10 stream (counter (j>>1, 0, 0, 3), key = seed), envelope
+ * pi = 1 and sigma = 1 (identity).  Bit-identical to the FP64 definition,
+ * then rounded to the blob dtype.                                           */
+fn_status fn_init_params(fn_system_t sys, uint64_t seed, void* d_params, void* stream);
+
+/* Walker initialisation ("Electron Sampler"): runs fn_assign_electrons with
+ * h_partial_charges (NULL: keep the current assignment), then
+ * r[w][e] = R[atom(e)] + init_std * z, z from the Philox stream
+ * (counter (j>>1, w, 0, 0), j = 3e + axis), computed in FP64 without fused
+ * multiply-add and rounded to the walker dtype: bit-exact.
+ * d_walkers [n_walkers][N][3]; h_atom_counts_out [M] or NULL.              */
+fn_status fn_init_walkers(fn_system_t sys, int n_walkers, uint64_t seed, double init_std,
+                          const double* h_partial_charges, void* d_walkers,
+                          int* h_atom_counts_out, void* stream);
+
+/* log|psi| and sign of psi for every walker (value-only forward pass).
+ * d_log_psi [n_walkers] double, d_sign [n_walkers] int8 (+1/-1, 0 if psi = 0). */
+fn_status fn_log_psi(fn_system_t sys, const void* d_params, const void* d_walkers,
+                     int n_walkers, double* d_log_psi, int8_t* d_sign, void* stream);
+
+/* n_steps Metropolis-Hastings steps on |psi|^2: r' = r + step_size * z for all
+ * 3N coordinates (proposal stream counter (j>>1, w, step, 1)), accept iff
+ * log U <= 2 (log|psi(r')| - log|psi(r)|), U = (m+1) 2^-53 from counter
+ * (0, w, step, 2); step = step_offset + s (low 32 bits).  d_log_psi holds
+ * log|psi| of the incoming walkers on entry (e.g. from fn_log_psi) and of the
+ * outgoing walkers on exit.  d_accept_count [1] int64 is incremented by the
+ * number of accepted moves (NULL to skip).                                  */
+fn_status fn_mcmc_steps(fn_system_t sys, const void* d_params, void* d_walkers, double* d_log_psi,
+                        int n_walkers, int n_steps, double step_size, uint64_t seed,
+                        uint64_t step_offset, int64_t* d_accept_count, void* stream);
+
+/* Local energy with the exact Laplacian (Eqs. 2-3):
+ * E_L = -1/2 sum_c [(d_c log|psi|)^2 + d_c^2 log|psi|] + V_ee + V_ne + V_nn.
+ * d_e_local, d_log_psi [n_walkers] double; d_sign [n_walkers] int8 (either of
+ * the last two may be NULL).                                                */
+fn_status fn_local_energy(fn_system_t sys, const void* d_params, const void* d_walkers,
+                          int n_walkers, double* d_e_local, double* d_log_psi, int8_t* d_sign,
+                          void* stream);
+
+/* VMC energy gradient (Eq. 6): grad = (2/B) sum_w (E_L,w - mean E_L) d log|psi_w| / d theta,
+ * with E_L held fixed.  The value-only forward pass is recomputed; gradients
+ * are written to d_grad [fn_param_count] in blob order and blob dtype.
+ * d_e_mean_out [1] double receives mean E_L (NULL to skip).                 */
+fn_status fn_energy_grad(fn_system_t sys, const void* d_params, const void* d_walkers,
+                         const double* d_e_local, int n_walkers, void* d_grad,
+                         double* d_e_mean_out, void* stream);
+
+/* Waits for the stream with a deadline (polling, no blocking sync), then reads
+ * and clears the device status word.  FN_ERR_TIMEOUT if the deadline passes
+ * (work keeps running), FN_ERR_NUMERIC if a kernel flagged a numerical error. */
+fn_status fn_sync(fn_system_t sys, void* stream, int timeout_ms);
+
+const char* fn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FNVMC_H */

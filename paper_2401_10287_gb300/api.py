@@ -1,0 +1,192 @@
+"""Torch-facing wrappers of the C ABI.  PyTorch provides device memory and streams only;
+every step of the path runs in libfnvmc.so."""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from . import _lib
+
+FP64, FP32, BF16_MIXED = 0, 1, 2
+ISO, ANISO = 0, 1
+_STATUS = {0: "FN_OK", 1: "FN_ERR_ARG", 2: "FN_ERR_OOM", 3: "FN_ERR_CUDA", 4: "FN_ERR_TIMEOUT",
+           5: "FN_ERR_NUMERIC", 6: "FN_ERR_EMPTY", 7: "FN_ERR_UNSUPPORTED"}
+
+
+class FnError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _lib.LIB_PATH
+
+
+def load_library():
+    return _lib.load()
+
+
+def _check(code: int):
+    if code != 0:
+        raise FnError(code, _lib.load().fn_last_error().decode())
+
+
+@dataclass(frozen=True)
+class NetConfig:
+    n_layers: int
+    h1: int
+    h2: int
+    n_dets: int
+    envelope: int = ISO
+    precision: int = FP64
+
+    @staticmethod
+    def from_ansatz(ansatz, precision: int) -> "NetConfig":
+        env = ANISO if ansatz.envelope == "aniso" else ISO
+        return NetConfig(ansatz.n_layers, ansatz.h1, ansatz.h2, ansatz.n_dets, env, precision)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class System:
+    """A molecule (nuclei, charges, spins) plus a network configuration on the current device."""
+
+    def __init__(self, nuclei, charges, n_up: int, n_down: int, cfg: NetConfig):
+        lib = _lib.load()
+        self._lib = lib
+        self.nuclei = np.ascontiguousarray(np.asarray(nuclei, dtype=np.float64).reshape(-1, 3))
+        self.charges = np.ascontiguousarray(np.asarray(charges, dtype=np.float64).reshape(-1))
+        self.n_up, self.n_down, self.cfg = int(n_up), int(n_down), cfg
+        self.n_el = self.n_up + self.n_down
+        c = _lib.NetConfigC(cfg.n_layers, cfg.h1, cfg.h2, cfg.n_dets, cfg.envelope, cfg.precision)
+        h = C.c_void_p()
+        _check(lib.fn_create_system(self.nuclei.ctypes.data_as(_lib._D), self.charges.ctypes.data_as(_lib._D),
+                                    self.nuclei.shape[0], self.n_up, self.n_down, C.byref(c), C.byref(h)))
+        self._h = h
+        self.param_count = int(lib.fn_param_count(h))
+        self.dtype = torch.float64 if cfg.precision == FP64 else torch.float32
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fn_destroy_system(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- host-side -------------------------------------------------------------------
+    def workspace_bytes(self, n_walkers: int) -> int:
+        return int(self._lib.fn_workspace_bytes(self._h, int(n_walkers)))
+
+    def set_walker_offset(self, offset: int):
+        _check(self._lib.fn_set_walker_offset(self._h, int(offset)))
+
+    def assign_electrons(self, partial_charges: Optional[Sequence[float]] = None):
+        counts = (C.c_int * self.nuclei.shape[0])()
+        atoms = (C.c_int * self.n_el)()
+        pc = None
+        if partial_charges is not None:
+            arr = np.ascontiguousarray(np.asarray(partial_charges, dtype=np.float64))
+            pc = arr.ctypes.data_as(_lib._D)
+        _check(self._lib.fn_assign_electrons(self._h, pc, counts, atoms))
+        return list(counts), list(atoms)
+
+    # -- device-side -----------------------------------------------------------------
+    def init_params(self, seed: int, device="cuda", stream=None) -> torch.Tensor:
+        p = torch.empty(self.param_count, dtype=self.dtype, device=device)
+        _check(self._lib.fn_init_params(self._h, int(seed), _ptr(p), _stream(stream)))
+        return p
+
+    def init_walkers(self, n_walkers: int, seed: int, init_std: float,
+                     partial_charges: Optional[Sequence[float]] = None, device="cuda", stream=None):
+        r = torch.empty((n_walkers, self.n_el, 3), dtype=self.dtype, device=device)
+        counts = (C.c_int * self.nuclei.shape[0])()
+        pc = None
+        if partial_charges is not None:
+            arr = np.ascontiguousarray(np.asarray(partial_charges, dtype=np.float64))
+            pc = arr.ctypes.data_as(_lib._D)
+        _check(self._lib.fn_init_walkers(self._h, int(n_walkers), int(seed), float(init_std), pc, _ptr(r), counts,
+                                         _stream(stream)))
+        return r, list(counts)
+
+    def _check_walkers(self, params: torch.Tensor, walkers: torch.Tensor):
+        if params.dtype != self.dtype or walkers.dtype != self.dtype:
+            raise FnError(1, f"params and walkers must be {self.dtype}")
+        if not (params.is_cuda and walkers.is_cuda and params.is_contiguous() and walkers.is_contiguous()):
+            raise FnError(1, "params and walkers must be contiguous CUDA tensors")
+        if params.numel() != self.param_count or walkers.shape[1:] != (self.n_el, 3):
+            raise FnError(1, "parameter or walker shape mismatch")
+
+    def log_psi(self, params, walkers, stream=None) -> Tuple[torch.Tensor, torch.Tensor]:
+        self._check_walkers(params, walkers)
+        B = walkers.shape[0]
+        lp = torch.empty(B, dtype=torch.float64, device=walkers.device)
+        sg = torch.empty(B, dtype=torch.int8, device=walkers.device)
+        _check(self._lib.fn_log_psi(self._h, _ptr(params), _ptr(walkers), B, _ptr(lp), _ptr(sg), _stream(stream)))
+        return lp, sg
+
+    def mcmc_steps(self, params, walkers, log_psi, n_steps: int, step_size: float, seed: int,
+                   step_offset: int = 0, accept_count: Optional[torch.Tensor] = None, stream=None):
+        self._check_walkers(params, walkers)
+        B = walkers.shape[0]
+        _check(self._lib.fn_mcmc_steps(self._h, _ptr(params), _ptr(walkers), _ptr(log_psi), B, int(n_steps),
+                                       float(step_size), int(seed), int(step_offset), _ptr(accept_count),
+                                       _stream(stream)))
+
+    def local_energy(self, params, walkers, stream=None):
+        self._check_walkers(params, walkers)
+        B = walkers.shape[0]
+        e = torch.empty(B, dtype=torch.float64, device=walkers.device)
+        lp = torch.empty(B, dtype=torch.float64, device=walkers.device)
+        sg = torch.empty(B, dtype=torch.int8, device=walkers.device)
+        _check(self._lib.fn_local_energy(self._h, _ptr(params), _ptr(walkers), B, _ptr(e), _ptr(lp), _ptr(sg),
+                                         _stream(stream)))
+        return e, lp, sg
+
+    def energy_grad(self, params, walkers, e_local, stream=None):
+        self._check_walkers(params, walkers)
+        B = walkers.shape[0]
+        g = torch.empty(self.param_count, dtype=self.dtype, device=walkers.device)
+        mean = torch.empty(1, dtype=torch.float64, device=walkers.device)
+        e_local = e_local.to(torch.float64).contiguous()
+        _check(self._lib.fn_energy_grad(self._h, _ptr(params), _ptr(walkers), _ptr(e_local), B, _ptr(g), _ptr(mean),
+                                        _stream(stream)))
+        return g, mean
+
+    def sync(self, timeout_ms: int = 60000, stream=None):
+        _check(self._lib.fn_sync(self._h, _stream(stream), int(timeout_ms)))
+
+
+class EnergyGrad(torch.autograd.Function):
+    """Surrogate loss whose gradient with respect to the parameters is Eq. 6.
+
+    forward(params, walkers, e_local, system) returns mean E_L (a scalar); backward
+    multiplies the library's VMC gradient by the incoming scalar.  The value-only
+    forward is recomputed inside the library, no activations are kept.
+    """
+
+    @staticmethod
+    def forward(ctx, params, walkers, e_local, system: System):
+        g, mean = system.energy_grad(params.detach(), walkers, e_local)
+        ctx.save_for_backward(g)
+        return mean.to(params.dtype).reshape(())
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (g,) = ctx.saved_tensors
+        return g * grad_out, None, None, None

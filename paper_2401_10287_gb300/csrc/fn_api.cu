@@ -1,0 +1,498 @@
+// Host side of the C ABI: argument checks, parameter-blob layout, Algorithm 1
+// (ionic charge initialisation) and the spin split, workspace management and the
+// orchestration of the kernel chain for every entry point.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "fn_internal.cuh"
+
+namespace fn {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+fn_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FN_OK;
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? FN_ERR_OOM : FN_ERR_CUDA;
+}
+
+Shape make_shape(const fn_system* s, int B, int T) {
+  Shape sh;
+  sh.B = B;
+  sh.N = s->N;
+  sh.n_up = s->n_up;
+  sh.n_dn = s->n_dn;
+  sh.M = s->M;
+  sh.T = T;
+  sh.wpt = kTileRows / s->N;
+  sh.tiles = (B + sh.wpt - 1) / sh.wpt;
+  sh.R = (int64_t)sh.tiles * kTileRows;
+  return sh;
+}
+
+int64_t phi_walker_stride(const fn_system* s, int T) {
+  return (int64_t)s->cfg.n_dets * T * ((int64_t)s->n_up * s->n_up + (int64_t)s->n_dn * s->n_dn);
+}
+
+// ---------------------------------------------------------------------------------------
+// Algorithm 1 and the spin split (host, integer arithmetic, charges in double)
+// ---------------------------------------------------------------------------------------
+static fn_status ionic_counts(const std::vector<double>& Z, const double* partial, int t,
+                              std::vector<int>* out) {
+  const int m_atoms = (int)Z.size();
+  std::vector<double> charge(m_atoms);
+  std::vector<int> electron(m_atoms);
+  for (int a = 0; a < m_atoms; ++a) {
+    charge[a] = partial ? partial[a] : (double)t / (double)m_atoms;
+    electron[a] = (int)std::lround(Z[a]);
+  }
+  while (t != 0) {
+    if (t < 0) {                      // anion: lowest partial charge receives an electron
+      int idx = 0;
+      for (int a = 1; a < m_atoms; ++a)
+        if (charge[a] < charge[idx]) idx = a;
+      electron[idx] += 1;
+      t += 1;
+      charge[idx] += 1.0;
+    } else {                          // cation: highest partial charge loses one
+      int idx = -1;
+      for (int a = 0; a < m_atoms; ++a)
+        if (electron[a] > 0 && (idx < 0 || charge[a] > charge[idx])) idx = a;
+      if (idx < 0) {
+        set_error("ionic charge exceeds the number of electrons");
+        return FN_ERR_ARG;
+      }
+      electron[idx] -= 1;
+      t -= 1;
+      charge[idx] -= 1.0;
+    }
+  }
+  *out = electron;
+  return FN_OK;
+}
+
+static void spin_assign(const std::vector<int>& counts, int n_up, int n_dn, std::vector<int>* atoms) {
+  const int m_atoms = (int)counts.size();
+  std::vector<int> up(m_atoms), dn(m_atoms);
+  int su = 0;
+  for (int a = 0; a < m_atoms; ++a) {
+    up[a] = (counts[a] + 1) / 2;
+    dn[a] = counts[a] / 2;
+    su += up[a];
+  }
+  while (su > n_up) {                 // flip up -> down where up - down is largest
+    int best = -1;
+    for (int a = 0; a < m_atoms; ++a)
+      if (up[a] > 0 && (best < 0 || up[a] - dn[a] > up[best] - dn[best])) best = a;
+    up[best] -= 1; dn[best] += 1; su -= 1;
+  }
+  while (su < n_up) {
+    int best = -1;
+    for (int a = 0; a < m_atoms; ++a)
+      if (dn[a] > 0 && (best < 0 || dn[a] - up[a] > dn[best] - up[best])) best = a;
+    dn[best] -= 1; up[best] += 1; su += 1;
+  }
+  atoms->clear();
+  for (int a = 0; a < m_atoms; ++a)
+    for (int k = 0; k < up[a]; ++k) atoms->push_back(a);
+  for (int a = 0; a < m_atoms; ++a)
+    for (int k = 0; k < dn[a]; ++k) atoms->push_back(a);
+  (void)n_dn;
+}
+
+// ---------------------------------------------------------------------------------------
+// layouts
+// ---------------------------------------------------------------------------------------
+static void build_layout(fn_system* s) {
+  const int L = s->cfg.n_layers, h1 = s->cfg.h1, h2 = s->cfg.h2, K = s->cfg.n_dets, M = s->M;
+  int64_t off = 0;
+  for (int l = 0; l < L; ++l) {
+    LayerDims& d = s->layer[l];
+    d.d_h = l == 0 ? 4 * M : h1;
+    d.d_g = l == 0 ? 4 : h2;
+    d.k_self = d.d_h + 2 * d.d_g;
+    d.ldx = (int)round_up(d.k_self, 8);
+    const int f_in = 3 * d.d_h + 2 * d.d_g;
+    d.off_V = off; off += (int64_t)h1 * f_in;
+    d.off_b = off; off += h1;
+    if (l < L - 1) {
+      d.off_W = off; off += (int64_t)h2 * d.d_g;
+      d.off_c = off; off += h2;
+    } else {
+      d.off_W = d.off_c = -1;
+    }
+  }
+  const int ns[2] = {s->n_up, s->n_dn};
+  for (int a = 0; a < 2; ++a) {
+    if (!ns[a]) continue;
+    s->off_w[a] = off; off += (int64_t)K * ns[a] * h1;
+    s->off_g[a] = off; off += (int64_t)K * ns[a];
+  }
+  const int sig_sz = s->cfg.envelope == FN_ENV_ANISOTROPIC ? 9 : 1;
+  for (int a = 0; a < 2; ++a) {
+    if (!ns[a]) continue;
+    s->off_pi[a] = off; off += (int64_t)K * ns[a] * M;
+    s->off_sig[a] = off; off += (int64_t)K * ns[a] * M * sig_sz;
+  }
+  s->P = off;
+
+  PrepLayout& p = s->prep;
+  int64_t q = 0, q16 = 0;
+  for (int l = 0; l < L; ++l) {
+    const LayerDims& d = s->layer[l];
+    p.VsT[l] = q; q += (int64_t)d.k_self * h1;
+    p.UT[l] = q; q += (int64_t)2 * d.d_h * h1;
+    p.b[l] = q; q += h1;
+    if (l < L - 1) {
+      p.W[l] = q; q += (int64_t)h2 * d.d_g;
+      p.c[l] = q; q += h2;
+    }
+    p.Vs16[l] = q16; q16 += (int64_t)h1 * d.ldx;
+    q = round_up(q, 4);
+    q16 = round_up(q16, 64);
+  }
+  for (int a = 0; a < 2; ++a) {
+    const int64_t ko = (int64_t)K * ns[a];
+    p.wT[a] = q; q += ko * h1;
+    p.g[a] = q; q += ko;
+    p.pi[a] = q; q += ko * M;
+    p.sig[a] = q; q += ko * M * sig_sz;
+    q = round_up(q, 4);
+  }
+  p.total = q;
+  p.total16 = q16;
+}
+
+template <class Mode>
+static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
+  using Act = typename Mode::Act; using Cmp = typename Mode::Cmp; using Det = typename Mode::Det;
+  using Wlk = typename Mode::Wlk;
+  const int T = 3 * s->N + 2;
+  const Shape sh = make_shape(s, B, T);
+  const int L = s->cfg.n_layers, h1 = s->cfg.h1, h2 = s->cfg.h2, N = s->N;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = (size_t)round_up((int64_t)(off + bytes), 256); return o; };
+  std::vector<std::pair<void**, size_t>> items;
+  size_t o_X[kMaxLayers], o_Hbar[kMaxLayers], o_act[kMaxLayers], o_gp[kMaxLayers];
+  int max_ldx = 0, max_dh = 0;
+  for (int l = 0; l < L; ++l) {
+    o_X[l] = take((size_t)T * sh.R * s->layer[l].ldx * sizeof(Act));
+    o_Hbar[l] = take((size_t)T * B * 2 * s->layer[l].d_h * sizeof(Cmp));
+    o_act[l] = take((size_t)sh.R * h1 * sizeof(Cmp));
+    o_gp[l] = take((size_t)B * N * N * h2 * sizeof(Cmp));
+    max_ldx = std::max(max_ldx, s->layer[l].ldx);
+    max_dh = std::max(max_dh, s->layer[l].d_h);
+  }
+  const size_t o_HL = take((size_t)T * sh.R * h1 * sizeof(Act));
+  const size_t o_M = take((size_t)T * B * h1 * sizeof(Cmp));
+  const size_t o_Phi = take((size_t)B * phi_walker_stride(s, T) * sizeof(Det));
+  const size_t o_prep = take((size_t)s->prep.total * sizeof(Cmp));
+  const size_t o_prep16 = take((size_t)s->prep.total16 * sizeof(__nv_bfloat16));
+  const size_t o_walk2 = take((size_t)B * N * 3 * sizeof(Wlk));
+  const size_t o_lp2 = take((size_t)B * sizeof(double));
+  const size_t o_scr = take((size_t)B * sizeof(double) * 2);
+  const size_t o_dX = take((size_t)sh.R * max_ldx * sizeof(Cmp));
+  const size_t o_dH = take((size_t)sh.R * h1 * sizeof(Cmp));
+  const size_t o_dZ = take((size_t)sh.R * h1 * sizeof(Cmp));
+  const size_t o_dZw = take((size_t)B * h1 * sizeof(Cmp));
+  const size_t o_dHbar = take((size_t)B * 2 * max_dh * sizeof(Cmp));
+  const size_t o_dG = take((size_t)B * N * N * h2 * sizeof(Cmp));
+  const size_t o_dPhi = take((size_t)B * phi_walker_stride(s, 1) * sizeof(Det));
+  const size_t o_gradc = take((size_t)s->prep.total * sizeof(Cmp));
+  const size_t o_status = take(sizeof(int) * 4);
+  const size_t o_counter = take(sizeof(int64_t) * 4);
+  if (ws && ws->base) {
+    char* b = (char*)ws->base;
+    for (int l = 0; l < L; ++l) {
+      ws->X[l] = b + o_X[l]; ws->Hbar[l] = b + o_Hbar[l]; ws->act[l] = b + o_act[l];
+      ws->gpair[l] = b + o_gp[l];
+    }
+    ws->HL = b + o_HL; ws->Mterm = b + o_M; ws->Phi = b + o_Phi; ws->prep = b + o_prep;
+    ws->prep16 = b + o_prep16; ws->walk2 = b + o_walk2; ws->lp2 = (double*)(b + o_lp2);
+    ws->scratch_d = (double*)(b + o_scr); ws->dX = b + o_dX; ws->dH = b + o_dH; ws->dZ = b + o_dZ;
+    ws->dZw = b + o_dZw; ws->dHbar = b + o_dHbar; ws->dG = b + o_dG; ws->dPhi = b + o_dPhi;
+    ws->gradc = b + o_gradc; ws->status = (int*)(b + o_status); ws->counter = (int64_t*)(b + o_counter);
+  }
+  return off;
+}
+
+template <class F>
+static auto dispatch(const fn_system* s, F&& f) {
+  switch (s->cfg.precision) {
+    case FN_FP64: return f(ModeF64{});
+    case FN_FP32: return f(ModeF32{});
+    default: return f(ModeBF16{});
+  }
+}
+
+static size_t workspace_bytes(fn_system* s, int B) {
+  return dispatch(s, [&](auto m) { return workspace_layout<decltype(m)>(s, B, nullptr); });
+}
+
+static fn_status ensure_workspace(fn_system* s, int B) {
+  if (B <= s->ws.cap_B && s->ws.base) return FN_OK;
+  cudaError_t e = cudaSetDevice(s->device);
+  if (e != cudaSuccess) return cuda_status(e, "cudaSetDevice");
+  if (s->ws.base) {
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_status(e, "cudaDeviceSynchronize");
+    cudaFree(s->ws.base);
+    s->ws.base = nullptr;
+  }
+  const size_t bytes = workspace_bytes(s, B);
+  e = cudaMalloc(&s->ws.base, bytes);
+  if (e != cudaSuccess) {
+    s->ws.base = nullptr;
+    s->ws.cap_B = 0;
+    return cuda_status(e, "workspace allocation");
+  }
+  e = cudaMemset(s->ws.base, 0, bytes);
+  if (e != cudaSuccess) return cuda_status(e, "workspace clear");
+  s->ws.bytes = bytes;
+  s->ws.cap_B = B;
+  dispatch(s, [&](auto m) { return workspace_layout<decltype(m)>(s, B, &s->ws); });
+  return FN_OK;
+}
+
+static fn_status check_launch(const char* what) {
+  return cuda_status(cudaGetLastError(), what);
+}
+
+}  // namespace fn
+
+using namespace fn;
+
+// ---------------------------------------------------------------------------------------
+// entry points
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+const char* fn_last_error(void) { return g_last_error.c_str(); }
+
+fn_status fn_create_system(const double* h_nuclei, const double* h_charges, int n_nuclei,
+                           int n_up, int n_down, const fn_net_config* cfg, fn_system_t* out) {
+  if (!out || !cfg || !h_nuclei || !h_charges) { set_error("null argument"); return FN_ERR_ARG; }
+  *out = nullptr;
+  if (n_nuclei < 1 || n_nuclei > kMaxNuclei) { set_error("1..16 nuclei supported"); return FN_ERR_ARG; }
+  if (n_up < 0 || n_down < 0) { set_error("negative electron count"); return FN_ERR_ARG; }
+  if (n_up + n_down == 0) { set_error("system has no electrons"); return FN_ERR_EMPTY; }
+  if (n_up + n_down > kMaxElectrons || n_up > kMaxSpin || n_down > kMaxSpin) {
+    set_error("at most 32 electrons and 16 per spin"); return FN_ERR_UNSUPPORTED;
+  }
+  if (cfg->n_layers < 1 || cfg->n_layers > kMaxLayers || cfg->h1 < 1 || cfg->h1 > 1024 ||
+      cfg->h2 < 1 || cfg->h2 > 32 || cfg->n_dets < 1 || cfg->n_dets > 64 ||
+      (cfg->envelope != FN_ENV_ISOTROPIC && cfg->envelope != FN_ENV_ANISOTROPIC) ||
+      cfg->precision < FN_FP64 || cfg->precision > FN_BF16_MIXED) {
+    set_error("network configuration out of range"); return FN_ERR_ARG;
+  }
+  if (cfg->precision == FN_BF16_MIXED && cfg->h1 % 8 != 0) {
+    set_error("h1 must be a multiple of 8 in FN_BF16_MIXED"); return FN_ERR_ARG;
+  }
+  double zsum = 0.0;
+  for (int m = 0; m < n_nuclei; ++m) {
+    if (!(h_charges[m] >= 1.0) || std::fabs(h_charges[m] - std::round(h_charges[m])) > 1e-12) {
+      set_error("nuclear charges must be positive integers"); return FN_ERR_ARG;
+    }
+    zsum += h_charges[m];
+  }
+  fn_system* s = new fn_system();
+  s->M = n_nuclei; s->n_up = n_up; s->n_dn = n_down; s->N = n_up + n_down; s->cfg = *cfg;
+  s->nuclei.assign(h_nuclei, h_nuclei + 3 * n_nuclei);
+  s->charges.assign(h_charges, h_charges + n_nuclei);
+  s->total_charge = (int)std::lround(zsum) - s->N;
+  for (int m = 0; m < n_nuclei; ++m)
+    for (int k = m + 1; k < n_nuclei; ++k) {
+      const double dx = h_nuclei[3 * m] - h_nuclei[3 * k], dy = h_nuclei[3 * m + 1] - h_nuclei[3 * k + 1],
+                   dz = h_nuclei[3 * m + 2] - h_nuclei[3 * k + 2];
+      s->v_nn += h_charges[m] * h_charges[k] / std::sqrt(dx * dx + dy * dy + dz * dz);
+    }
+  build_layout(s);
+  fn_status st = ionic_counts(s->charges, nullptr, s->total_charge, &s->counts);
+  if (st != FN_OK) { delete s; return st; }
+  spin_assign(s->counts, n_up, n_down, &s->elec_atom);
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_nuclei, sizeof(double) * (3 * n_nuclei + n_nuclei));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_elec_atom, sizeof(int) * kMaxElectrons);
+  if (e != cudaSuccess) { fn_status r = cuda_status(e, "create_system"); delete s; return r; }
+  s->d_charges = s->d_nuclei + 3 * n_nuclei;
+  e = cudaMemcpy(s->d_nuclei, h_nuclei, sizeof(double) * 3 * n_nuclei, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_charges, h_charges, sizeof(double) * n_nuclei, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_elec_atom, s->elec_atom.data(), sizeof(int) * s->N, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { fn_status r = cuda_status(e, "create_system copy"); fn_destroy_system(s); return r; }
+  st = upload_prep_descs(s);
+  if (st != FN_OK) { fn_destroy_system(s); return st; }
+  *out = s;
+  return FN_OK;
+}
+
+fn_status fn_destroy_system(fn_system_t s) {
+  if (!s) return FN_OK;
+  if (s->ws.base || s->d_nuclei) cudaDeviceSynchronize();
+  if (s->ws.base) cudaFree(s->ws.base);
+  if (s->d_nuclei) cudaFree(s->d_nuclei);
+  if (s->d_elec_atom) cudaFree(s->d_elec_atom);
+  if (s->d_descs) cudaFree(s->d_descs);
+  delete s;
+  return FN_OK;
+}
+
+int64_t fn_param_count(fn_system_t s) { return s ? s->P : -1; }
+
+int64_t fn_workspace_bytes(fn_system_t s, int n_walkers) {
+  if (!s || n_walkers < 1) return -1;
+  return (int64_t)workspace_bytes(s, n_walkers);
+}
+
+fn_status fn_set_walker_offset(fn_system_t s, uint64_t off) {
+  if (!s) { set_error("null system"); return FN_ERR_ARG; }
+  s->walker_offset = off;
+  return FN_OK;
+}
+
+fn_status fn_assign_electrons(fn_system_t s, const double* partial, int* counts_out, int* atoms_out) {
+  if (!s) { set_error("null system"); return FN_ERR_ARG; }
+  std::vector<int> counts, atoms;
+  fn_status st = ionic_counts(s->charges, partial, s->total_charge, &counts);
+  if (st != FN_OK) return st;
+  spin_assign(counts, s->n_up, s->n_dn, &atoms);
+  s->counts = counts;
+  s->elec_atom = atoms;
+  cudaError_t e = cudaMemcpy(s->d_elec_atom, atoms.data(), sizeof(int) * s->N, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_status(e, "assign_electrons copy");
+  if (counts_out) std::memcpy(counts_out, counts.data(), sizeof(int) * s->M);
+  if (atoms_out) std::memcpy(atoms_out, atoms.data(), sizeof(int) * s->N);
+  return FN_OK;
+}
+
+fn_status fn_init_params(fn_system_t s, uint64_t seed, void* d_params, void* stream) {
+  if (!s || !d_params) { set_error("null argument"); return FN_ERR_ARG; }
+  dispatch(s, [&](auto m) { launch_init_params<decltype(m)>(s, seed, d_params, (cudaStream_t)stream); return 0; });
+  return check_launch("init_params");
+}
+
+fn_status fn_init_walkers(fn_system_t s, int B, uint64_t seed, double init_std, const double* partial,
+                          void* d_walkers, int* counts_out, void* stream) {
+  if (!s || !d_walkers || B < 1 || !(init_std >= 0.0)) { set_error("invalid argument"); return FN_ERR_ARG; }
+  if (partial) {
+    fn_status st = fn_assign_electrons(s, partial, nullptr, nullptr);
+    if (st != FN_OK) return st;
+  }
+  if (counts_out) std::memcpy(counts_out, s->counts.data(), sizeof(int) * s->M);
+  dispatch(s, [&](auto m) { launch_init_walkers<decltype(m)>(s, B, seed, init_std, d_walkers, (cudaStream_t)stream); return 0; });
+  return check_launch("init_walkers");
+}
+
+fn_status fn_log_psi(fn_system_t s, const void* d_params, const void* d_walkers, int B,
+                     double* d_log_psi, int8_t* d_sign, void* stream) {
+  if (!s || !d_params || !d_walkers || B < 1 || !d_log_psi) { set_error("invalid argument"); return FN_ERR_ARG; }
+  fn_status st = ensure_workspace(s, B);
+  if (st != FN_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  dispatch(s, [&](auto m) {
+    using Mode = decltype(m);
+    const Shape sh = make_shape(s, B, 1);
+    launch_prep_params<Mode>(s, d_params, cs);
+    launch_forward<Mode>(s, d_walkers, sh, false, cs);
+    launch_det_energy<Mode>(s, d_walkers, sh, nullptr, d_log_psi, d_sign, false, cs);
+    return 0;
+  });
+  return check_launch("log_psi");
+}
+
+fn_status fn_local_energy(fn_system_t s, const void* d_params, const void* d_walkers, int B,
+                          double* d_e_local, double* d_log_psi, int8_t* d_sign, void* stream) {
+  if (!s || !d_params || !d_walkers || B < 1 || !d_e_local) { set_error("invalid argument"); return FN_ERR_ARG; }
+  fn_status st = ensure_workspace(s, B);
+  if (st != FN_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  dispatch(s, [&](auto m) {
+    using Mode = decltype(m);
+    const Shape sh = make_shape(s, B, 3 * s->N + 2);
+    launch_prep_params<Mode>(s, d_params, cs);
+    launch_forward<Mode>(s, d_walkers, sh, false, cs);
+    launch_det_energy<Mode>(s, d_walkers, sh, d_e_local, d_log_psi, d_sign, false, cs);
+    return 0;
+  });
+  return check_launch("local_energy");
+}
+
+fn_status fn_mcmc_steps(fn_system_t s, const void* d_params, void* d_walkers, double* d_log_psi, int B,
+                        int n_steps, double step_size, uint64_t seed, uint64_t step_offset,
+                        int64_t* d_accept, void* stream) {
+  if (!s || !d_params || !d_walkers || !d_log_psi || B < 1 || n_steps < 0 || !(step_size >= 0.0)) {
+    set_error("invalid argument"); return FN_ERR_ARG;
+  }
+  if (n_steps == 0) return FN_OK;
+  fn_status st = ensure_workspace(s, B);
+  if (st != FN_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  dispatch(s, [&](auto m) {
+    using Mode = decltype(m);
+    const Shape sh = make_shape(s, B, 1);
+    launch_prep_params<Mode>(s, d_params, cs);
+    for (int k = 0; k < n_steps; ++k) {
+      const uint32_t step = (uint32_t)(step_offset + (uint64_t)k);
+      launch_propose<Mode>(s, B, d_walkers, s->ws.walk2, step_size, seed, step, cs);
+      launch_forward<Mode>(s, s->ws.walk2, sh, false, cs);
+      launch_det_energy<Mode>(s, s->ws.walk2, sh, nullptr, s->ws.lp2, nullptr, false, cs);
+      launch_accept<Mode>(s, B, d_walkers, s->ws.walk2, d_log_psi, s->ws.lp2, seed, step, d_accept, cs);
+    }
+    return 0;
+  });
+  return check_launch("mcmc_steps");
+}
+
+fn_status fn_energy_grad(fn_system_t s, const void* d_params, const void* d_walkers, const double* d_e_local,
+                         int B, void* d_grad, double* d_e_mean, void* stream) {
+  if (!s || !d_params || !d_walkers || !d_e_local || !d_grad || B < 1) {
+    set_error("invalid argument"); return FN_ERR_ARG;
+  }
+  fn_status st = ensure_workspace(s, B);
+  if (st != FN_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  dispatch(s, [&](auto m) {
+    using Mode = decltype(m);
+    const Shape sh = make_shape(s, B, 1);
+    launch_prep_params<Mode>(s, d_params, cs);
+    launch_forward<Mode>(s, d_walkers, sh, true, cs);
+    launch_det_energy<Mode>(s, d_walkers, sh, nullptr, s->ws.lp2, nullptr, true, cs);
+    launch_backward<Mode>(s, d_walkers, sh, d_e_local, d_grad, d_e_mean, cs);
+    return 0;
+  });
+  return check_launch("energy_grad");
+}
+
+fn_status fn_sync(fn_system_t s, void* stream, int timeout_ms) {
+  if (!s) { set_error("null system"); return FN_ERR_ARG; }
+  cudaStream_t cs = (cudaStream_t)stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t q = cudaStreamQuery(cs);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return cuda_status(q, "stream");
+    const auto el = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_ms >= 0 && el > timeout_ms) { set_error("fn_sync deadline passed"); return FN_ERR_TIMEOUT; }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  if (!s->ws.base) return FN_OK;
+  int word = 0;
+  cudaError_t e = cudaMemcpy(&word, s->ws.status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e, "status read");
+  if (word) {
+    const int zero = 0;
+    cudaMemcpy(s->ws.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    set_error(word & kStatusSingular ? "all determinants singular for some walker" : "non-finite result");
+    return FN_ERR_NUMERIC;
+  }
+  return FN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,36 @@
+// Small device helpers: typed loads/stores (BF16 storage with FP32 arithmetic) and
+// precision-overloaded math.
+#pragma once
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace fn {
+
+__device__ __forceinline__ double ld(const double* p) { return *p; }
+__device__ __forceinline__ float ld(const float* p) { return *p; }
+__device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void st(double* p, double v) { *p = v; }
+__device__ __forceinline__ void st(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st(float* p, double v) { *p = (float)v; }
+__device__ __forceinline__ void st(double* p, float v) { *p = (double)v; }
+__device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void st(__nv_bfloat16* p, double v) { *p = __float2bfloat16_rn((float)v); }
+
+__device__ __forceinline__ float f_tanh(float x) { return tanhf(x); }
+__device__ __forceinline__ double f_tanh(double x) { return tanh(x); }
+__device__ __forceinline__ float f_exp(float x) { return expf(x); }
+__device__ __forceinline__ double f_exp(double x) { return exp(x); }
+__device__ __forceinline__ float f_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double f_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float f_log(float x) { return logf(x); }
+__device__ __forceinline__ double f_log(double x) { return log(x); }
+__device__ __forceinline__ float f_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double f_abs(double x) { return fabs(x); }
+
+// Row of electron i of walker w in the walker-aligned tile layout.
+__device__ __forceinline__ int64_t tile_row(int w, int i, int N, int wpt) {
+  const int q = w / wpt;
+  return (int64_t)q * 128 + (int64_t)(w - q * wpt) * N + i;
+}
+
+}  // namespace fn

@@ -1,0 +1,668 @@
+// Forward pass of the wavefunction with forward-mode Laplacian tangents
+// ("FermiNet Model" section; Eq. 4 envelope), SIMT kernels for FP64/FP32 and the
+// glue of the BF16 mode:
+//   k_prep          parameter blob -> internal layouts (one launch, descriptor table)
+//   k_features_en   one-electron stream input [r_i - R_m, |r_i - R_m|] with tangents
+//   k_features_mean spin means of the one-electron input
+//   k_pair_stream   two-electron stream (sparse tangents: only r_i and r_j move a pair)
+//                   and its spin means for every layer
+//   k_gemm          tiled SIMT GEMM (mean-field term U [hbar_up, hbar_dn] + b)
+//   k_layer         one-electron layer GEMM over all tangent slabs with the fused
+//                   tanh forward-Laplacian epilogue, residual and next spin means
+//   k_orbitals      orbital projection x envelope with the product rule
+#include <algorithm>
+#include <vector>
+
+#include "fn_device.cuh"
+#include "fn_internal.cuh"
+
+namespace fn {
+
+// ---------------------------------------------------------------------------------------
+// parameter preparation
+// ---------------------------------------------------------------------------------------
+struct CopyDesc {
+  int64_t src, s_rs, s_cs;   // source offset and strides (row, col) in the blob
+  int64_t dst, d_rs, d_cs;   // destination offset and strides
+  int rows, cols;
+  int to16;                  // 1: destination is the bf16 array
+};
+
+template <typename Par, typename Cmp>
+__global__ void k_prep(const Par* __restrict__ blob, const CopyDesc* __restrict__ descs, int n_desc,
+                       Cmp* __restrict__ prep, __nv_bfloat16* __restrict__ prep16) {
+  const CopyDesc d = descs[blockIdx.y];
+  const int64_t n = (int64_t)d.rows * d.cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / d.cols, c = e % d.cols;
+    const Par v = blob[d.src + r * d.s_rs + c * d.s_cs];
+    if (d.to16) prep16[d.dst + r * d.d_rs + c * d.d_cs] = __float2bfloat16_rn((float)v);
+    else prep[d.dst + r * d.d_rs + c * d.d_cs] = (Cmp)v;
+  }
+}
+
+static std::vector<CopyDesc> build_descs(const fn_system* s, bool with16) {
+  std::vector<CopyDesc> v;
+  const int L = s->cfg.n_layers, h1 = s->cfg.h1, h2 = s->cfg.h2, K = s->cfg.n_dets, M = s->M;
+  const PrepLayout& p = s->prep;
+  for (int l = 0; l < L; ++l) {
+    const LayerDims& d = s->layer[l];
+    const int f_in = 3 * d.d_h + 2 * d.d_g;
+    // VsT[k][n] = V[n][k] for k < d_h, V[n][3 d_h + (k - d_h)] for the pair-mean columns
+    v.push_back({d.off_V, 1, f_in, p.VsT[l], h1, 1, d.d_h, h1, 0});
+    v.push_back({d.off_V + 3 * d.d_h, 1, f_in, p.VsT[l] + (int64_t)d.d_h * h1, h1, 1, 2 * d.d_g, h1, 0});
+    v.push_back({d.off_V + d.d_h, 1, f_in, p.UT[l], h1, 1, 2 * d.d_h, h1, 0});
+    v.push_back({d.off_b, 0, 1, p.b[l], 0, 1, 1, h1, 0});
+    if (l < L - 1) {
+      v.push_back({d.off_W, d.d_g, 1, p.W[l], d.d_g, 1, h2, d.d_g, 0});
+      v.push_back({d.off_c, 0, 1, p.c[l], 0, 1, 1, h2, 0});
+    }
+    if (with16) {
+      v.push_back({d.off_V, f_in, 1, p.Vs16[l], d.ldx, 1, h1, d.d_h, 1});
+      v.push_back({d.off_V + 3 * d.d_h, f_in, 1, p.Vs16[l] + d.d_h, d.ldx, 1, h1, 2 * d.d_g, 1});
+    }
+  }
+  const int ns[2] = {s->n_up, s->n_dn};
+  const int sig_sz = s->cfg.envelope == FN_ENV_ANISOTROPIC ? 9 : 1;
+  for (int a = 0; a < 2; ++a) {
+    if (!ns[a]) continue;
+    const int ko = K * ns[a];
+    v.push_back({s->off_w[a], 1, h1, p.wT[a], ko, 1, h1, ko, 0});
+    v.push_back({s->off_g[a], 0, 1, p.g[a], 0, 1, 1, ko, 0});
+    v.push_back({s->off_pi[a], 0, 1, p.pi[a], 0, 1, 1, ko * M, 0});
+    v.push_back({s->off_sig[a], 0, 1, p.sig[a], 0, 1, 1, ko * M * sig_sz, 0});
+  }
+  return v;
+}
+
+fn_status upload_prep_descs(fn_system* s) {
+  std::vector<CopyDesc> v = build_descs(s, s->cfg.precision == FN_BF16_MIXED);
+  cudaError_t e = cudaMalloc(&s->d_descs, sizeof(CopyDesc) * v.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(s->d_descs, v.data(), sizeof(CopyDesc) * v.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_status(e, "parameter descriptor upload");
+  s->n_descs = (int)v.size();
+  return FN_OK;
+}
+
+template <class Mode>
+void launch_prep_params(const fn_system* s, const void* params, cudaStream_t st) {
+  using Par = typename Mode::Par; using Cmp = typename Mode::Cmp;
+  dim3 grid(32, s->n_descs);
+  k_prep<Par, Cmp><<<grid, 256, 0, st>>>((const Par*)params, (const CopyDesc*)s->d_descs, s->n_descs,
+                                         (Cmp*)s->ws.prep,
+                                         (__nv_bfloat16*)s->ws.prep16);
+}
+
+// ---------------------------------------------------------------------------------------
+// input features
+// ---------------------------------------------------------------------------------------
+template <typename Act, typename Wlk>
+__global__ void k_features_en(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh,
+                              Act* __restrict__ X0, int ldx) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)sh.B * sh.N) return;
+  const int w = (int)(gid / sh.N), i = (int)(gid % sh.N);
+  const int64_t row = tile_row(w, i, sh.N, sh.wpt);
+  const int64_t slab = sh.R * ldx;
+  const double rx = (double)r[gid * 3], ry = (double)r[gid * 3 + 1], rz = (double)r[gid * 3 + 2];
+  for (int m = 0; m < sh.M; ++m) {
+    const double d[3] = {rx - nuc[3 * m], ry - nuc[3 * m + 1], rz - nuc[3 * m + 2]};
+    const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    Act* base = X0 + row * ldx + 4 * m;
+    for (int a = 0; a < 3; ++a) st(base + a, d[a]);
+    st(base + 3, dist);
+    if (sh.T == 1) continue;
+    for (int t = 1; t < sh.T; ++t) {
+      Act* o = base + t * slab;
+      const int e = (t - 1) / 3, c = (t - 1) % 3;
+      if (t == sh.T - 1) {
+        st(o, 0.0); st(o + 1, 0.0); st(o + 2, 0.0); st(o + 3, 2.0 / dist);
+      } else if (e == i) {
+        for (int a = 0; a < 3; ++a) st(o + a, a == c ? 1.0 : 0.0);
+        st(o + 3, d[c] / dist);
+      } else {
+        for (int a = 0; a < 4; ++a) st(o + a, 0.0);
+      }
+    }
+  }
+}
+
+// Hbar0[t][w][spin * 4M + 4m + a]: mean over the electrons of one spin of h0.
+template <typename Cmp, typename Wlk>
+__global__ void k_features_mean(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh,
+                                Cmp* __restrict__ Hbar) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)sh.B * 2 * sh.M) return;
+  const int w = (int)(gid / (2 * sh.M)), spin = (int)((gid / sh.M) % 2), m = (int)(gid % sh.M);
+  const int lo = spin ? sh.n_up : 0, hi = spin ? sh.N : sh.n_up;
+  const int n_s = hi - lo;
+  const int width = 2 * 4 * sh.M;
+  const int64_t slab = (int64_t)sh.B * width;
+  Cmp* base = Hbar + (int64_t)w * width + spin * 4 * sh.M + 4 * m;
+  const double inv = n_s ? 1.0 / n_s : 0.0;
+  double v[4] = {0, 0, 0, 0}, lap = 0.0;
+  for (int e = lo; e < hi; ++e) {
+    const Wlk* re = r + ((int64_t)w * sh.N + e) * 3;
+    const double d[3] = {(double)re[0] - nuc[3 * m], (double)re[1] - nuc[3 * m + 1], (double)re[2] - nuc[3 * m + 2]};
+    const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    v[0] += d[0]; v[1] += d[1]; v[2] += d[2]; v[3] += dist;
+    lap += 2.0 / dist;
+    if (sh.T > 1)
+      for (int c = 0; c < 3; ++c) {
+        Cmp* o = base + (1 + 3 * e + c) * slab;
+        for (int a = 0; a < 3; ++a) o[a] = (Cmp)(a == c ? inv : 0.0);
+        o[3] = (Cmp)(d[c] / dist * inv);
+      }
+  }
+  for (int a = 0; a < 4; ++a) base[a] = (Cmp)(v[a] * inv);
+  if (sh.T == 1) return;
+  Cmp* o = base + (sh.T - 1) * slab;
+  o[0] = o[1] = o[2] = (Cmp)0; o[3] = (Cmp)(lap * inv);
+  // slabs of the other spin's electrons are zero
+  const int olo = spin ? 0 : sh.n_up, ohi = spin ? sh.n_up : sh.N;
+  for (int e = olo; e < ohi; ++e)
+    for (int c = 0; c < 3; ++c) {
+      Cmp* q = base + (1 + 3 * e + c) * slab;
+      q[0] = q[1] = q[2] = q[3] = (Cmp)0;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// two-electron stream: one warp per (walker, electron i), lane = channel
+// ---------------------------------------------------------------------------------------
+struct PairArgs {
+  void* X[kMaxLayers];
+  int ldx[kMaxLayers];
+  int col0[kMaxLayers];       // first mean-g column of X_l (= d_h of layer l)
+  int d_g[kMaxLayers];
+  const void* W[kMaxLayers];  // prepared pair weights [h2][d_g]
+  const void* c[kMaxLayers];
+  void* gstore[kMaxLayers];   // value of g^l for l >= 1, [B][N][N][h2] (backward), or null
+  int L, h2;
+};
+
+template <typename Act, typename Cmp, typename Wlk, bool FULL>
+__global__ void k_pair_stream(const Wlk* __restrict__ r, Shape sh, PairArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (gw >= (int64_t)sh.B * sh.N) return;
+  const int w = (int)(gw / sh.N), i = (int)(gw % sh.N);
+  const int64_t row = tile_row(w, i, sh.N, sh.wpt);
+  const Wlk* rw = r + (int64_t)w * sh.N * 3;
+  const double ri[3] = {(double)rw[3 * i], (double)rw[3 * i + 1], (double)rw[3 * i + 2]};
+  const int nsp[2] = {sh.n_up, sh.n_dn};
+  // per layer, per spin: sums of value, Laplacian and derivatives along r_i
+  Cmp acc_v[kMaxLayers][2], acc_l[kMaxLayers][2], acc_d[kMaxLayers][2][3];
+  for (int l = 0; l < a.L; ++l)
+    for (int s = 0; s < 2; ++s) {
+      acc_v[l][s] = acc_l[l][s] = 0;
+      acc_d[l][s][0] = acc_d[l][s][1] = acc_d[l][s][2] = 0;
+    }
+  for (int j = 0; j < sh.N; ++j) {
+    const int sj = j < sh.n_up ? 0 : 1;
+    const Cmp inv_n = (Cmp)1 / (Cmp)nsp[sj];
+    // jets of g^0_ij in lanes 0..3: v, d/dr_i (3), d/dr_j (3), Laplacian
+    Cmp v = 0, di[3] = {0, 0, 0}, dj[3] = {0, 0, 0}, lp = 0;
+    if (j != i) {
+      const double d[3] = {ri[0] - (double)rw[3 * j], ri[1] - (double)rw[3 * j + 1], ri[2] - (double)rw[3 * j + 2]};
+      const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      if (lane < 3) {
+        v = (Cmp)d[lane];
+        di[lane] = (Cmp)1;
+        dj[lane] = (Cmp)-1;
+      } else if (lane == 3) {
+        v = (Cmp)dist;
+        for (int c = 0; c < 3; ++c) { di[c] = (Cmp)(d[c] / dist); dj[c] = -di[c]; }
+        lp = (Cmp)(4.0 / dist);
+      }
+    }
+    for (int l = 0; l < a.L; ++l) {
+      const int dg = a.d_g[l];
+      if (lane < dg) {
+        acc_v[l][sj] += v;
+        acc_l[l][sj] += lp;
+        for (int c = 0; c < 3; ++c) acc_d[l][sj][c] += di[c];
+        if (FULL && j != i) {
+          Act* X = (Act*)a.X[l];
+          const int64_t slab = sh.R * a.ldx[l];
+          for (int c = 0; c < 3; ++c) {
+            Act* o = X + (1 + 3 * j + c) * slab + row * a.ldx[l] + a.col0[l];
+            st(o + sj * dg + lane, dj[c] * inv_n);
+            st(o + (1 - sj) * dg + lane, (Cmp)0);
+          }
+        }
+      }
+      if (l == a.L - 1) break;
+      // pair layer l: g <- tanh(W g + c) (+ g for l >= 1)
+      const Cmp* W = (const Cmp*)a.W[l];
+      const Cmp* cb = (const Cmp*)a.c[l];
+      const int h2 = a.h2;
+      Cmp zv = lane < h2 ? cb[lane] : (Cmp)0, zi[3] = {0, 0, 0}, zj[3] = {0, 0, 0}, zl = 0;
+      for (int k = 0; k < dg; ++k) {
+        const Cmp wk = lane < h2 ? W[lane * dg + k] : (Cmp)0;
+        zv += wk * __shfl_sync(0xffffffffu, v, k);
+        if (FULL) {
+          for (int c = 0; c < 3; ++c) {
+            zi[c] += wk * __shfl_sync(0xffffffffu, di[c], k);
+            zj[c] += wk * __shfl_sync(0xffffffffu, dj[c], k);
+          }
+          zl += wk * __shfl_sync(0xffffffffu, lp, k);
+        }
+      }
+      const Cmp h = f_tanh(zv);
+      const Cmp dh = (Cmp)1 - h * h;
+      Cmp nv = h, ni[3], nj[3], nl = 0;
+      if (FULL) {
+        Cmp sq = 0;
+        for (int c = 0; c < 3; ++c) {
+          ni[c] = dh * zi[c];
+          nj[c] = dh * zj[c];
+          sq += zi[c] * zi[c] + zj[c] * zj[c];
+        }
+        nl = dh * zl - (Cmp)2 * h * dh * sq;
+      }
+      if (l > 0) {
+        nv += v;
+        if (FULL) {
+          for (int c = 0; c < 3; ++c) { ni[c] += di[c]; nj[c] += dj[c]; }
+          nl += lp;
+        }
+      }
+      if (lane >= h2) { nv = 0; nl = 0; }
+      v = nv;
+      if (FULL) {
+        for (int c = 0; c < 3; ++c) {
+          di[c] = lane < h2 ? ni[c] : (Cmp)0;
+          dj[c] = lane < h2 ? nj[c] : (Cmp)0;
+        }
+        lp = nl;
+      }
+      if (a.gstore[l + 1] && lane < h2)
+        ((Cmp*)a.gstore[l + 1])[(((int64_t)w * sh.N + i) * sh.N + j) * h2 + lane] = v;
+    }
+  }
+  // slabs accumulated over j: value, Laplacian, derivatives along r_i
+  for (int l = 0; l < a.L; ++l) {
+    const int dg = a.d_g[l];
+    if (lane >= dg) continue;
+    Act* X = (Act*)a.X[l];
+    const int64_t slab = sh.R * a.ldx[l];
+    Act* base = X + row * a.ldx[l] + a.col0[l] + lane;
+    for (int s = 0; s < 2; ++s) {
+      const Cmp inv_n = nsp[s] ? (Cmp)1 / (Cmp)nsp[s] : (Cmp)0;
+      st(base + s * dg, acc_v[l][s] * inv_n);
+      if (FULL) {
+        st(base + (sh.T - 1) * slab + s * dg, acc_l[l][s] * inv_n);
+        for (int c = 0; c < 3; ++c) st(base + (1 + 3 * i + c) * slab + s * dg, acc_d[l][s][c] * inv_n);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// tiled SIMT GEMM: C(m,n) (+)= sum_k A(m,k) B(k,n) + bias[n] (rows m < bias_rows)
+// ---------------------------------------------------------------------------------------
+template <typename TA, typename TB, typename TC, typename Cmp>
+__global__ void __launch_bounds__(256) k_gemm(int Mr, int Nc, int Kd, const TA* __restrict__ A, int64_t sam,
+                                              int64_t sak, const TB* __restrict__ Bm, int64_t sbk, int64_t sbn,
+                                              TC* __restrict__ C, int64_t scm, int64_t scn,
+                                              const Cmp* __restrict__ bias, int64_t bias_rows, int atomic_acc) {
+  __shared__ Cmp As[16][64 + 1];
+  __shared__ Cmp Bs[16][64 + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+  const int kchunk = (Kd + gridDim.z - 1) / gridDim.z;
+  const int kbeg = blockIdx.z * kchunk, kend = min(Kd, kbeg + kchunk);
+  Cmp acc[4][4] = {};
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
+    for (int e = tid; e < 16 * 64; e += 256) {
+      const int kk = e / 64, mm = e % 64;
+      const int64_t m = m0 + mm;
+      const int k = k0 + kk;
+      As[kk][mm] = (m < Mr && k < kend) ? (Cmp)ld(A + m * sam + k * sak) : (Cmp)0;
+      const int64_t n = n0 + mm;
+      Bs[kk][mm] = (n < Nc && k < kend) ? (Cmp)ld(Bm + k * sbk + n * sbn) : (Cmp)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      Cmp av[4], bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { av[q] = As[kk][ty * 4 + q]; bv[q] = Bs[kk][tx * 4 + q]; }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc[q][p] += av[q] * bv[p];
+    }
+    __syncthreads();
+  }
+  for (int q = 0; q < 4; ++q) {
+    const int64_t m = m0 + ty * 4 + q;
+    if (m >= Mr) continue;
+    for (int p = 0; p < 4; ++p) {
+      const int64_t n = n0 + tx * 4 + p;
+      if (n >= Nc) continue;
+      Cmp v = acc[q][p];
+      if (bias && m < bias_rows && blockIdx.z == 0) v += bias[n];
+      TC* o = C + m * scm + n * scn;
+      if (atomic_acc) atomicAdd(o, (TC)v);
+      else st(o, v);
+    }
+  }
+}
+
+template <typename TA, typename TB, typename TC, typename Cmp>
+void gemm(cudaStream_t st, int Mr, int Nc, int Kd, const TA* A, int64_t sam, int64_t sak, const TB* Bm,
+          int64_t sbk, int64_t sbn, TC* C, int64_t scm, int64_t scn, const Cmp* bias, int64_t bias_rows,
+          int split_k, bool atomic_acc) {
+  if (Mr <= 0 || Nc <= 0 || Kd <= 0) return;
+  dim3 grid((Nc + 63) / 64, (Mr + 63) / 64, std::max(1, split_k));
+  k_gemm<TA, TB, TC, Cmp><<<grid, 256, 0, st>>>(Mr, Nc, Kd, A, sam, sak, Bm, sbk, sbn, C, scm, scn, bias,
+                                                 bias_rows, (atomic_acc || split_k > 1) ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------------------
+// one-electron layer: for every 128-row walker tile and 64 output columns, loop over
+// the tangent slabs: value first (h = tanh z), then every gradient slab
+// ((1 - h^2) z_t, accumulating sum_t z_t^2), then the Laplacian slab
+// ((1 - h^2) z_lap - 2 h (1 - h^2) sum_t z_t^2); plus the residual and the spin means
+// of the output for the next layer.
+// ---------------------------------------------------------------------------------------
+struct LayerArgs {
+  const void* X; int ldx; int k_self;
+  const void* VsT;      // [k_self][h1]
+  const void* Mterm;    // [T][B][h1]
+  void* Y; int ldy;     // output [T][R][ldy]
+  int residual;
+  void* Hbar_out;       // [T][B][2 h1] or null
+  void* act_out;        // [R][h1] tanh values (value pass) or null
+  int h1;
+};
+
+template <typename Act, typename Cmp, bool FULL>
+__global__ void __launch_bounds__(256) k_layer(Shape sh, LayerArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cmp* xs = (Cmp*)smem_raw;                // [32][132]
+  Cmp* ws = xs + 32 * 132;                 // [32][64]
+  Cmp* ys = ws + 32 * 64;                  // [128][65]
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int tile = blockIdx.x, n0 = blockIdx.y * 64;
+  const int64_t row0 = (int64_t)tile * 128;
+  const Act* X = (const Act*)a.X;
+  const Cmp* VsT = (const Cmp*)a.VsT;
+  const Cmp* Mt = (const Cmp*)a.Mterm;
+  Act* Y = (Act*)a.Y;
+  const int64_t xslab = sh.R * a.ldx, yslab = sh.R * a.ldy;
+  Cmp hv[8][4], sq[8][4];
+  int wv[8];
+  for (int q = 0; q < 8; ++q) {
+    const int rl = ty * 8 + q, wl = rl / sh.N;
+    const int w = tile * sh.wpt + wl;
+    wv[q] = (wl < sh.wpt && w < sh.B) ? w : -1;
+  }
+  for (int t = 0; t < sh.T; ++t) {
+    Cmp acc[8][4] = {};
+    const Act* Xt = X + t * xslab + row0 * a.ldx;
+    for (int k0 = 0; k0 < a.k_self; k0 += 32) {
+      for (int e = tid; e < 128 * 32; e += 256) {
+        const int rr = e / 32, kk = e % 32;
+        const int k = k0 + kk;
+        xs[kk * 132 + rr] = k < a.k_self ? (Cmp)ld(Xt + (int64_t)rr * a.ldx + k) : (Cmp)0;
+      }
+      for (int e = tid; e < 32 * 64; e += 256) {
+        const int kk = e / 64, nn = e % 64;
+        const int k = k0 + kk, n = n0 + nn;
+        ws[kk * 64 + nn] = (k < a.k_self && n < a.h1) ? VsT[(int64_t)k * a.h1 + n] : (Cmp)0;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < 32; ++kk) {
+        Cmp av[8], bv[4];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) av[q] = xs[kk * 132 + ty * 8 + q];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) bv[p] = ws[kk * 64 + tx * 4 + p];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+          for (int p = 0; p < 4; ++p) acc[q][p] += av[q] * bv[p];
+      }
+      __syncthreads();
+    }
+    // epilogue
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int rl = ty * 8 + q;
+      const int64_t row = row0 + rl;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int cl = tx * 4 + p, col = n0 + cl;
+        Cmp out = 0;
+        if (wv[q] >= 0 && col < a.h1) {
+          const Cmp z = acc[q][p] + Mt[((int64_t)t * sh.B + wv[q]) * a.h1 + col];
+          if (t == 0) {
+            const Cmp h = f_tanh(z);
+            hv[q][p] = h;
+            sq[q][p] = 0;
+            out = h;
+            if (a.act_out) ((Cmp*)a.act_out)[row * a.h1 + col] = h;
+          } else if (t < sh.T - 1) {
+            const Cmp h = hv[q][p];
+            out = ((Cmp)1 - h * h) * z;
+            sq[q][p] += z * z;
+          } else {
+            const Cmp h = hv[q][p], d = (Cmp)1 - h * h;
+            out = d * z - (Cmp)2 * h * d * sq[q][p];
+          }
+          if (a.residual) out += (Cmp)ld(X + t * xslab + row * a.ldx + col);
+          st(Y + t * yslab + row * a.ldy + col, out);
+        }
+        ys[rl * 65 + cl] = out;
+      }
+    }
+    if (a.Hbar_out) {
+      __syncthreads();
+      Cmp* Hb = (Cmp*)a.Hbar_out;
+      for (int e = tid; e < sh.wpt * 2 * 64; e += 256) {
+        const int wl = e / 128, s = (e / 64) % 2, cl = e % 64, col = n0 + cl;
+        const int w = tile * sh.wpt + wl;
+        if (w >= sh.B || col >= a.h1) continue;
+        const int lo = s ? sh.n_up : 0, hi = s ? sh.N : sh.n_up;
+        Cmp sum = 0;
+        for (int i = lo; i < hi; ++i) sum += ys[(wl * sh.N + i) * 65 + cl];
+        Hb[((int64_t)t * sh.B + w) * 2 * a.h1 + s * a.h1 + col] = hi > lo ? sum / (Cmp)(hi - lo) : (Cmp)0;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// orbitals: phi^{k}_i(r_j) = (w_ki . h_j + g_ki) * env_ki(r_j), with the product rule
+// over the tangent slabs; envelope derivatives only along r_j.
+// ---------------------------------------------------------------------------------------
+struct OrbArgs {
+  const void* HL;               // [T][R][h1]
+  const void* wT[2]; const void* g[2]; const void* pi[2]; const void* sig[2];
+  void* Phi;                    // [B][PW]
+  int64_t PW;                   // elements per walker
+  int h1, K, aniso;
+};
+
+template <typename Act, typename Cmp, typename Det, typename Wlk, bool FULL>
+__global__ void k_orbitals(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh, OrbArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cmp* hs = (Cmp*)smem_raw;     // [h1]
+  const int w = blockIdx.x / sh.N, j = blockIdx.x % sh.N;
+  const int spin = j < sh.n_up ? 0 : 1;
+  const int n_s = spin ? sh.n_dn : sh.n_up;
+  const int jj = j - (spin ? sh.n_up : 0);
+  const int n_ko = a.K * n_s;
+  const int ko = threadIdx.x;
+  const bool active = ko < n_ko;
+  const int64_t row = tile_row(w, j, sh.N, sh.wpt);
+  const Cmp* wT = (const Cmp*)a.wT[spin];
+  // envelope value, gradient along r_j and Laplacian
+  Cmp env = 0, ge[3] = {0, 0, 0}, le = 0;
+  const Wlk* rj = r + ((int64_t)w * sh.N + j) * 3;
+  if (active) {
+    const Cmp* pi = (const Cmp*)a.pi[spin] + (int64_t)ko * sh.M;
+    for (int m = 0; m < sh.M; ++m) {
+      const Cmp d[3] = {(Cmp)((double)rj[0] - nuc[3 * m]), (Cmp)((double)rj[1] - nuc[3 * m + 1]),
+                        (Cmp)((double)rj[2] - nuc[3 * m + 2])};
+      Cmp s, gs[3], ls;
+      if (!a.aniso) {
+        const Cmp sg = ((const Cmp*)a.sig[spin])[(int64_t)ko * sh.M + m];
+        const Cmp dist = f_sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        s = sg * dist;
+        for (int c = 0; c < 3; ++c) gs[c] = sg * d[c] / dist;
+        ls = (Cmp)2 * sg / dist;
+      } else {
+        const Cmp* S = (const Cmp*)a.sig[spin] + ((int64_t)ko * sh.M + m) * 9;
+        Cmp u[3];
+        for (int x = 0; x < 3; ++x) u[x] = S[3 * x] * d[0] + S[3 * x + 1] * d[1] + S[3 * x + 2] * d[2];
+        s = f_sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        Cmp stu[3], frob = 0, n2 = 0;
+        for (int y = 0; y < 3; ++y) stu[y] = S[y] * u[0] + S[3 + y] * u[1] + S[6 + y] * u[2];
+        for (int q = 0; q < 9; ++q) frob += S[q] * S[q];
+        for (int y = 0; y < 3; ++y) { gs[y] = stu[y] / s; n2 += stu[y] * stu[y]; }
+        ls = (frob - n2 / (s * s)) / s;
+      }
+      const Cmp e = pi[m] * f_exp(-s);
+      env += e;
+      Cmp g2 = 0;
+      for (int c = 0; c < 3; ++c) { ge[c] -= e * gs[c]; g2 += gs[c] * gs[c]; }
+      le += e * (g2 - ls);
+    }
+  }
+  const int k = active ? ko / n_s : 0, i = active ? ko % n_s : 0;
+  Det* out = (Det*)a.Phi + (int64_t)w * a.PW +
+             (spin ? (int64_t)a.K * sh.T * sh.n_up * sh.n_up : 0) + (int64_t)k * sh.T * n_s * n_s +
+             (int64_t)i * n_s + jj;
+  const int64_t tstride = (int64_t)n_s * n_s;
+  const int64_t hslab = sh.R * a.h1;
+  const Act* HL = (const Act*)a.HL;
+  Cmp p0 = 0, pj[3] = {0, 0, 0};
+  for (int t = 0; t < sh.T; ++t) {
+    for (int c = threadIdx.x; c < a.h1; c += blockDim.x) hs[c] = (Cmp)ld(HL + t * hslab + row * a.h1 + c);
+    __syncthreads();
+    if (active) {
+      Cmp p = t == 0 ? ((const Cmp*)a.g[spin])[ko] : (Cmp)0;
+      for (int c = 0; c < a.h1; ++c) p += hs[c] * wT[(int64_t)c * n_ko + ko];
+      Cmp phi;
+      if (t == 0) {
+        p0 = p;
+        phi = p * env;
+      } else if (t < sh.T - 1) {
+        const int e = (t - 1) / 3, c = (t - 1) % 3;
+        phi = p * env;
+        if (e == j) { pj[c] = p; phi += p0 * ge[c]; }
+      } else {
+        phi = p * env + (Cmp)2 * (pj[0] * ge[0] + pj[1] * ge[1] + pj[2] * ge[2]) + p0 * le;
+      }
+      out[t * tstride] = (Det)phi;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// orchestration
+// ---------------------------------------------------------------------------------------
+template <class Mode>
+void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bool keep, cudaStream_t st) {
+  using Act = typename Mode::Act; using Cmp = typename Mode::Cmp; using Det = typename Mode::Det;
+  using Wlk = typename Mode::Wlk;
+  const Workspace& ws = s->ws;
+  const int L = s->cfg.n_layers, h1 = s->cfg.h1, h2 = s->cfg.h2;
+  const Cmp* prep = (const Cmp*)ws.prep;
+  const bool full = sh.T > 1;
+  const Wlk* r = (const Wlk*)walkers;
+  // inputs
+  {
+    const int64_t n = (int64_t)sh.B * sh.N;
+    k_features_en<Act, Wlk><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(r, s->d_nuclei, sh, (Act*)ws.X[0],
+                                                                           s->layer[0].ldx);
+    const int64_t m = (int64_t)sh.B * 2 * sh.M;
+    k_features_mean<Cmp, Wlk><<<(unsigned)((m + 127) / 128), 128, 0, st>>>(r, s->d_nuclei, sh, (Cmp*)ws.Hbar[0]);
+  }
+  {
+    PairArgs pa{};
+    pa.L = L;
+    pa.h2 = h2;
+    for (int l = 0; l < L; ++l) {
+      pa.X[l] = ws.X[l];
+      pa.ldx[l] = s->layer[l].ldx;
+      pa.col0[l] = s->layer[l].d_h;
+      pa.d_g[l] = s->layer[l].d_g;
+      if (l < L - 1) { pa.W[l] = prep + s->prep.W[l]; pa.c[l] = prep + s->prep.c[l]; }
+      pa.gstore[l] = (keep && l >= 1) ? ws.gpair[l] : nullptr;
+    }
+    const int64_t threads = (int64_t)sh.B * sh.N * 32;
+    const unsigned blocks = (unsigned)((threads + 127) / 128);
+    if (full) k_pair_stream<Act, Cmp, Wlk, true><<<blocks, 128, 0, st>>>(r, sh, pa);
+    else k_pair_stream<Act, Cmp, Wlk, false><<<blocks, 128, 0, st>>>(r, sh, pa);
+  }
+  for (int l = 0; l < L; ++l) {
+    const LayerDims& d = s->layer[l];
+    // mean-field term M = Hbar_l U_l^T + b_l (bias on the value slab only)
+    const Cmp* Hb = (const Cmp*)ws.Hbar[l];
+    gemm<Cmp, Cmp, Cmp, Cmp>(st, sh.T * sh.B, h1, 2 * d.d_h, Hb, 2 * d.d_h, 1, prep + s->prep.UT[l], h1, 1,
+                             (Cmp*)ws.Mterm, h1, 1, prep + s->prep.b[l], sh.B, 1, false);
+    LayerArgs la{};
+    la.X = ws.X[l]; la.ldx = d.ldx; la.k_self = d.k_self;
+    la.VsT = prep + s->prep.VsT[l];
+    la.Mterm = ws.Mterm;
+    const bool last = l == L - 1;
+    la.Y = last ? ws.HL : ws.X[l + 1];
+    la.ldy = last ? h1 : s->layer[l + 1].ldx;
+    la.residual = l > 0;
+    la.Hbar_out = last ? nullptr : ws.Hbar[l + 1];
+    la.act_out = keep ? ws.act[l] : nullptr;
+    la.h1 = h1;
+    const size_t smem = sizeof(Cmp) * (32 * 132 + 32 * 64 + 128 * 65);
+    dim3 grid(sh.tiles, (h1 + 63) / 64);
+    if (full) {
+      cudaFuncSetAttribute(k_layer<Act, Cmp, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_layer<Act, Cmp, true><<<grid, 256, smem, st>>>(sh, la);
+    } else {
+      cudaFuncSetAttribute(k_layer<Act, Cmp, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_layer<Act, Cmp, false><<<grid, 256, smem, st>>>(sh, la);
+    }
+  }
+  {
+    OrbArgs oa{};
+    oa.HL = ws.HL;
+    for (int a = 0; a < 2; ++a) {
+      oa.wT[a] = prep + s->prep.wT[a]; oa.g[a] = prep + s->prep.g[a];
+      oa.pi[a] = prep + s->prep.pi[a]; oa.sig[a] = prep + s->prep.sig[a];
+    }
+    oa.Phi = ws.Phi;
+    oa.PW = phi_walker_stride(s, sh.T);
+    oa.h1 = h1; oa.K = s->cfg.n_dets; oa.aniso = s->cfg.envelope == FN_ENV_ANISOTROPIC;
+    const int ko_max = s->cfg.n_dets * std::max(s->n_up, s->n_dn);
+    const int threads = (int)std::min<int64_t>(1024, round_up(ko_max, 32));
+    const size_t smem = sizeof(Cmp) * h1;
+    const unsigned blocks = (unsigned)((int64_t)sh.B * sh.N);
+    if (full) k_orbitals<Act, Cmp, Det, Wlk, true><<<blocks, threads, smem, st>>>(r, s->d_nuclei, sh, oa);
+    else k_orbitals<Act, Cmp, Det, Wlk, false><<<blocks, threads, smem, st>>>(r, s->d_nuclei, sh, oa);
+  }
+}
+
+template void launch_prep_params<ModeF64>(const fn_system*, const void*, cudaStream_t);
+template void launch_prep_params<ModeF32>(const fn_system*, const void*, cudaStream_t);
+template void launch_prep_params<ModeBF16>(const fn_system*, const void*, cudaStream_t);
+template void launch_forward<ModeF64>(const fn_system*, const void*, const Shape&, bool, cudaStream_t);
+template void launch_forward<ModeF32>(const fn_system*, const void*, const Shape&, bool, cudaStream_t);
+template void launch_forward<ModeBF16>(const fn_system*, const void*, const Shape&, bool, cudaStream_t);
+
+// explicit GEMM instantiations used by the backward pass
+template void gemm<float, float, float, float>(cudaStream_t, int, int, int, const float*, int64_t, int64_t,
+                                               const float*, int64_t, int64_t, float*, int64_t, int64_t,
+                                               const float*, int64_t, int, bool);
+template void gemm<double, double, double, double>(cudaStream_t, int, int, int, const double*, int64_t, int64_t,
+                                                   const double*, int64_t, int64_t, double*, int64_t, int64_t,
+                                                   const double*, int64_t, int, bool);
+
+}  // namespace fn

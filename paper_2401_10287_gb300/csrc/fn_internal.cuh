@@ -1,0 +1,182 @@
+// Internal declarations of the fnvmc CUDA library: precision traits, the system
+// handle, the device workspace layout and the kernel launchers shared between
+// translation units.
+//
+// Data layout in device memory (B walkers, N electrons, T tangent slabs):
+//   * T = 1 for value-only passes (Metropolis, log|psi|, energy gradient) and
+//     T = 3N + 2 for the local energy: slab 0 is the value, slab 1 + 3e + c the
+//     derivative along coordinate c of electron e, slab 3N + 1 the Laplacian.
+//   * Electron rows are grouped in walker-aligned tiles of 128 rows: tile q holds
+//     walkers q*wpt .. q*wpt + wpt - 1 (wpt = floor(128 / N)), row
+//     q*128 + (w - q*wpt)*N + i; the last 128 - wpt*N rows of a tile are padding.
+//     A tile therefore contains every electron of its walkers, so spin means
+//     over electrons never cross a tile.
+//   * Stream-layer inputs X_l are [T][R][ldx_l] (R = tiles*128 rows), columns
+//     [h_i (d_h) | mean-up g_i. (d_g) | mean-down g_i. (d_g)].
+//   * Spin means of h, Hbar_l, are [T][B][2 d_h]; the mean-field term
+//     M_l = Hbar_l U_l^T (+ b_l on slab 0) is [T][B][h1].
+//   * Orbital matrices Phi are [B][spin block][K][T][n_s][n_s] with element
+//     (i, j) = orbital i evaluated at electron j of that spin.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fnvmc.h"
+
+namespace fn {
+
+constexpr int kTileRows = 128;
+constexpr int kMaxLayers = 8;
+constexpr int kMaxElectrons = 32;
+constexpr int kMaxSpin = 16;
+constexpr int kMaxNuclei = 16;
+
+// Status bits written by kernels into the device status word.
+constexpr int kStatusNonFinite = 1;
+constexpr int kStatusSingular = 2;
+
+// ---- precision traits ------------------------------------------------------------
+// Act: storage of stream activations; Cmp: elementwise arithmetic; Det: determinant
+// stage; Wlk: walker coordinates; Par: parameter blob.
+struct ModeF64 {
+  using Act = double; using Cmp = double; using Det = double; using Wlk = double; using Par = double;
+  static constexpr fn_precision kMode = FN_FP64;
+};
+struct ModeF32 {
+  using Act = float; using Cmp = float; using Det = float; using Wlk = float; using Par = float;
+  static constexpr fn_precision kMode = FN_FP32;
+};
+struct ModeBF16 {
+  using Act = __nv_bfloat16; using Cmp = float; using Det = double; using Wlk = float; using Par = float;
+  static constexpr fn_precision kMode = FN_BF16_MIXED;
+};
+
+__host__ __device__ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// ---- geometry of one call ----------------------------------------------------------
+struct Shape {
+  int B = 0;        // walkers in the call
+  int N = 0, n_up = 0, n_dn = 0, M = 0;
+  int T = 1;        // tangent slabs of this pass
+  int wpt = 0;      // walkers per 128-row tile
+  int tiles = 0;
+  int64_t R = 0;    // padded electron rows
+};
+
+// ---- per-layer sizes -----------------------------------------------------------------
+struct LayerDims {
+  int d_h, d_g;     // input widths of the one- and two-electron features
+  int k_self;       // d_h + 2 d_g
+  int ldx;          // row stride of X_l (k_self rounded up to 8)
+  int64_t off_V, off_b, off_W, off_c;   // offsets in the parameter blob
+};
+
+// ---- prepared (internal layout) parameters ------------------------------------------
+// All offsets are element offsets into a Cmp-typed array, except the bf16 copies.
+struct PrepLayout {
+  int64_t VsT[kMaxLayers];   // [k_self][h1]   self part of V, transposed
+  int64_t UT[kMaxLayers];    // [2 d_h][h1]    mean-field part of V, transposed
+  int64_t b[kMaxLayers];     // [h1]
+  int64_t W[kMaxLayers];     // [h2][d_g]      pair weights (as in the blob)
+  int64_t c[kMaxLayers];     // [h2]
+  int64_t wT[2];             // [h1][K n_s]    orbital projection, transposed
+  int64_t g[2];              // [K n_s]
+  int64_t pi[2];             // [K n_s][M]
+  int64_t sig[2];            // [K n_s][M] or [K n_s][M][9]
+  int64_t total;
+  int64_t Vs16[kMaxLayers];  // bf16 [h1][ldx_l] self part of V, K contiguous (BF16 mode)
+  int64_t total16;
+};
+
+struct Workspace {
+  void* base = nullptr;
+  size_t bytes = 0;
+  int cap_B = 0;
+  // carved pointers (valid for cap_B walkers, full T)
+  void* X[kMaxLayers] = {};
+  void* HL = nullptr;            // last layer output [T][R][h1] (Act)
+  void* Hbar[kMaxLayers] = {};   // [T][B][2 d_h] (Cmp)
+  void* Mterm = nullptr;         // [T][B][h1] (Cmp)
+  void* Phi = nullptr;           // [B][per-walker orbital block] (Det)
+  void* prep = nullptr;          // prepared params (Cmp)
+  void* prep16 = nullptr;        // bf16 weights
+  void* walk2 = nullptr;         // proposal walkers [B][N][3] (Wlk)
+  double* lp2 = nullptr;         // proposal log|psi| [B]
+  double* scratch_d = nullptr;   // [B] doubles (per-walker weights etc.)
+  // backward (value-only) storage
+  void* act[kMaxLayers] = {};    // tanh outputs a_l [R][h1] (Cmp)
+  void* gpair[kMaxLayers] = {};  // pair stream g^l [B][N][N][h2] (Cmp), l = 1..L-1
+  void* dX = nullptr;            // [R][max ldx] (Cmp)
+  void* dH = nullptr;            // [R][h1] (Cmp) running gradient wrt h
+  void* dZ = nullptr;            // [R][h1] (Cmp)
+  void* dZw = nullptr;           // [B][h1] (Cmp) walker sums of dZ
+  void* dHbar = nullptr;         // [B][2 max d_h] (Cmp)
+  void* dG = nullptr;            // [B][N][N][h2] (Cmp) gradient wrt the pair stream
+  void* dPhi = nullptr;          // [B][orbital block, value slab] (Det)
+  void* gradc = nullptr;         // prepared-layout gradient accumulator (Cmp)
+  int* status = nullptr;         // device status word
+  int64_t* counter = nullptr;    // scratch counter
+};
+
+}  // namespace fn
+
+struct fn_system {
+  int M = 0, n_up = 0, n_dn = 0, N = 0;
+  fn_net_config cfg{};
+  std::vector<double> nuclei, charges;
+  int total_charge = 0;
+  std::vector<int> counts, elec_atom;
+  fn::LayerDims layer[fn::kMaxLayers];
+  int64_t off_w[2] = {0, 0}, off_g[2] = {0, 0}, off_pi[2] = {0, 0}, off_sig[2] = {0, 0};
+  int64_t P = 0;
+  fn::PrepLayout prep{};
+  uint64_t walker_offset = 0;
+  double v_nn = 0.0;
+  int device = 0;
+  int sm_count = 0;
+  fn::Workspace ws;
+  // small device constants
+  double* d_nuclei = nullptr;    // [M][3]
+  double* d_charges = nullptr;   // [M]
+  int* d_elec_atom = nullptr;    // [N]
+  void* d_descs = nullptr;       // parameter-preparation copy descriptors
+  int n_descs = 0;
+};
+
+namespace fn {
+
+void set_error(const std::string& msg);
+fn_status cuda_status(cudaError_t e, const char* what);
+
+fn_status upload_prep_descs(fn_system* s);
+
+// Shapes and sizes
+Shape make_shape(const fn_system* s, int B, int T);
+int64_t phi_walker_stride(const fn_system* s, int T);   // elements per walker of Phi
+
+// ---- launchers (one instantiation per precision mode) --------------------------------
+template <class Mode> void launch_prep_params(const fn_system* s, const void* params, cudaStream_t st);
+template <class Mode> void launch_forward(const fn_system* s, const void* walkers, const Shape& sh,
+                                          bool keep_for_backward, cudaStream_t st);
+template <class Mode> void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh,
+                                             double* e_local, double* log_psi, int8_t* sign,
+                                             bool keep_inverse, cudaStream_t st);
+template <class Mode> void launch_init_walkers(const fn_system* s, int B, uint64_t seed, double std_,
+                                               void* walkers, cudaStream_t st);
+template <class Mode> void launch_init_params(const fn_system* s, uint64_t seed, void* params,
+                                              cudaStream_t st);
+template <class Mode> void launch_propose(const fn_system* s, int B, const void* walkers, void* out,
+                                          double step, uint64_t seed, uint32_t step_idx, cudaStream_t st);
+template <class Mode> void launch_accept(const fn_system* s, int B, void* walkers, const void* prop,
+                                         double* lp, const double* lp_new, uint64_t seed,
+                                         uint32_t step_idx, int64_t* accept_count, cudaStream_t st);
+template <class Mode> void launch_backward(const fn_system* s, const void* walkers, const Shape& sh,
+                                           const double* e_local, void* grad, double* e_mean,
+                                           cudaStream_t st);
+
+}  // namespace fn
