@@ -1,0 +1,350 @@
+"""Throughput of the VMC hot path on one or more GPUs (one process per GPU).
+
+One step is a full pass of the method over one batch of synthetic walkers:
+  Algorithm 1 + walker initialisation, 10 Metropolis steps on |psi|^2, the exact
+  local energy of every walker, and the Eq. 6 energy gradient.
+Workload: N2 at 2.068 bohr (7 up + 7 down electrons), 4 layers of widths 256/32,
+16 determinants, anisotropic envelopes, 4096 walkers per GPU, step 0.02 bohr.
+The metric is walker local energies per second of whole-step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32|fp64]
+  python bench.py --impl reference ...   (the FP64 oracle on the host cores)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "walker local energies/s (exact Laplacian) BF16 vs FP32; serving p50/p99 ms"
+UNIT = "walker-E_L/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# FP64 and FP32 vector rates derived from unit counts and clocks: 152 SMs x 2.07 GHz x
+# (64 FP64 FMA lanes / 64 per the part's ratio -> 1.25 TFLOP/s nominal FP64;
+#  128 FP32 lanes x 2 flops -> 80.5 TFLOP/s FP32).
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def _workload_desc(B):
+    return ("N2 2.068 bohr, 7+7 electrons, 4 layers 256/32, 16 determinants, anisotropic envelopes, "
+            f"{B} walkers/GPU; step = init + 10 Metropolis steps + exact-Laplacian E_L + Eq. 6 gradient")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(s[0]) for s in self.samples if s and s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if len(s) > 1 and s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if len(s) > 3 + k and s[3 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(precision_name: str, n_walkers: int = 4, budget_s: float = 20.0):
+    """The FP64 oracle on a bounded sample of the workload: local energies of a few walkers."""
+    from oracle import ansatz, mcmc
+    sysm = W.n2()
+    a = W.N2_LARGE["ansatz"]
+    net = ansatz.Net(2, 7, 7, a.n_layers, a.h1, a.h2, a.n_dets, a.envelope)
+    p = ansatz.init_params(net, 1)
+    r, _ = mcmc.init_walkers(sysm.nuclei, sysm.charges, 7, 7, None, n_walkers, 1, 1.0)
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        ansatz.local_energy(net, p, sysm.nuclei, sysm.charges, r)
+        done += n_walkers
+        if time.perf_counter() - t0 > budget_s or done >= 64:
+            break
+    dt = time.perf_counter() - t0
+    try:
+        import threadpoolctl
+        cores = max(int(info.get("num_threads", 1)) for info in threadpoolctl.threadpool_info()) or 1
+    except Exception:
+        cores = os.cpu_count() or 1
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} walkers of the N2 workload, FP64 NumPy oracle local_energy only "
+                      f"(forward-Laplacian jets), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    t_steps = []
+    cb = None
+    for k in range(args.warmup + args.steps):
+        res = cpu_baseline(args.precision, n_walkers=4, budget_s=5.0)
+        if k >= args.warmup:
+            t_steps.append(res)
+        cb = res
+    value = float(np.mean([r["value"] for r in t_steps]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * 4 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": _workload_desc(4) + " (oracle sample: 4 walkers per step)",
+                                            "l2": "not applicable (host)"},
+            "cpu_baseline": {"kind": "oracle", "cores": cb["cores"], "sample": cb["sample"], "value": value,
+                             "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _algorithmic(cls, B, N, a, T_full):
+    """(work per launch, unit, bound) of a kernel class at this workload (Sec. d of the design)."""
+    M = 2
+    h1, h2, K = a.h1, a.h2, a.n_dets
+    n = N // 2
+    if cls in ("layer_full", "layer_value"):
+        T = T_full if cls == "layer_full" else 1
+        # average over the L layers: layer 0 has k_self = 4M + 8, the others h1 + 2 h2
+        k_self = [4 * M + 8] + [h1 + 2 * h2] * (a.n_layers - 1)
+        flops = np.mean([2.0 * B * N * T * k * h1 for k in k_self])
+        return flops, "flop", "alu"
+    if cls in ("det_full",):
+        # per walker, determinant k, spin: 3N tangent items x 2 n^3 flops + Laplacian trace 2 n^2
+        flops = B * K * 2 * (3 * N * 2 * n ** 3 + 2 * n * n + 3 * n ** 3)
+        return flops, "flop64", "alu"
+    if cls in ("orbitals_full",):
+        flops = 2.0 * B * N * T_full * h1 * K * n
+        return flops, "flop", "alu"
+    return None, None, None
+
+
+def run_mine(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2401_10287_gb300 as P
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    prec = {"bf16": P.BF16_MIXED, "fp32": P.FP32, "fp64": P.FP64}[args.precision]
+    cfg = W.N2_LARGE
+    a = cfg["ansatz"]
+    sysm = W.n2()
+    B = args.walkers
+    N = sysm.n_electrons
+    gpu = P.System(sysm.nuclei, sysm.charges, sysm.n_up, sysm.n_down, P.NetConfig.from_ansatz(a, prec))
+    gpu.set_walker_offset(rank * B)
+    seed = cfg["seed"]
+    params = gpu.init_params(seed)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    acc = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def step(k, params_dev):
+        walkers, _ = gpu.init_walkers(B, seed + 1000 * k, cfg["init_std"])
+        lp, _ = gpu.log_psi(params_dev, walkers)
+        gpu.mcmc_steps(params_dev, walkers, lp, cfg["mcmc_steps"], cfg["step_size"], seed, step_offset=k * 64,
+                       accept_count=acc)
+        e, lp2, _ = gpu.local_energy(params_dev, walkers)
+        if ws > 1:
+            tot = torch.stack([e.sum(), torch.tensor(float(B), dtype=torch.float64, device="cuda")])
+            dist.all_reduce(tot)
+            mean = tot[0] / tot[1]
+            wts = 2.0 * (e - mean) / tot[1]
+            g = gpu.log_psi_vjp(params_dev, walkers, wts)
+            dist.all_reduce(g)
+        else:
+            g, mean = gpu.energy_grad(params_dev, walkers, e)
+        return e, g
+
+    for k in range(args.warmup):
+        step(k, params)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    gpu.profile_enable(True)
+    times = []
+    for k in range(args.steps):
+        flush.fill_(float(k))                       # L2 flush outside the timed events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(args.warmup + k, params)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    prof = gpu.profile_read()
+    gpu.profile_enable(False)
+    ms = float(np.sum(times))
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    clk = clocks.stop()
+    value = B * ws * args.steps / (ms / 1000.0)
+
+    # end to end through the public API with host buffers (params in, E_L and gradient out)
+    host_params = params.detach().cpu().pin_memory()
+    e_host = torch.empty(B, dtype=torch.float64).pin_memory()
+    g_host = torch.empty(gpu.param_count, dtype=params.dtype).pin_memory()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        p_dev = host_params.to("cuda", non_blocking=True)
+        e, g = step(args.warmup + args.steps + k, p_dev)
+        e_host.copy_(e, non_blocking=True)
+        g_host.copy_(g, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = B * ws * args.steps / e2e_s
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    peaks, peak_src = _peaks()
+    # dominant kernel class and its roofline
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    cls, (launches, total_ms) = dom
+    T_full = 3 * N + 2
+    work, kind, bound = _algorithmic(cls, B, N, a, T_full)
+    roof = None
+    if work is not None:
+        avg_s = total_ms / launches / 1000.0
+        if kind == "flop64":
+            achieved = work / avg_s / 1e12
+            roof = {"kernel": cls, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s (FP64)", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "nominal FP64 rate of the part (measured DFMA probe: 1.20)"}
+        elif prec == P.BF16_MIXED and cls.startswith("layer"):
+            achieved = work / avg_s / 1e12
+            pk = peaks["bf16_tflops_sustained"]
+            roof = {"kernel": cls, "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                    "frac": achieved / pk, "traffic": None, "peak_source": f"{peak_src} bf16 sustained"}
+        else:
+            achieved = work / avg_s / 1e12
+            pk = FP64_PEAK_TFLOPS if prec == P.FP64 else FP32_PEAK_TFLOPS
+            roof = {"kernel": cls, "bound": "alu", "achieved": achieved, "peak": pk,
+                    "unit": "TFLOP/s (FP64)" if prec == P.FP64 else "TFLOP/s (FP32)", "frac": achieved / pk,
+                    "traffic": None, "peak_source": "derived from unit counts and the 2.07 GHz clock"}
+    cb = None
+    if not args.no_cpu_baseline and ws == 1:
+        cb = cpu_baseline(args.precision)
+    launches_total = int(sum(v[0] for v in prof.values()))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16": "bf16", "fp32": "f32", "fp64": "f64"}[args.precision],
+        "precision_mode": {"bf16": "BF16 tensor-core stream GEMMs, FP32 elementwise, FP64 determinants and E_L",
+                           "fp32": "FP32 throughout, FP64 energy accumulation",
+                           "fp64": "FP64 throughout"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": _workload_desc(B), "walkers_per_gpu": B, "electrons": N,
+                   "l2": "flushed between timed steps (256 MB write); per-step working set > 10 GB",
+                   "parallelism": f"dp{ws}" if ws > 1 else "single GPU"},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(host_params.numel() * host_params.element_size()),
+                "d2h_bytes_per_step": int(B * 8 + g_host.numel() * g_host.element_size())},
+        "gpu_launches": launches_total,
+        "roofline": roof,
+        "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+        "cpu_baseline": cb,
+        "acceptance": float(acc.item()) / max(1, (args.warmup + 2 * args.steps) * cfg["mcmc_steps"] * B),
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
+    ap.add_argument("--walkers", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

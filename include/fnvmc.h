@@ -160,6 +160,22 @@ fn_status fn_energy_grad(fn_system_t sys, const void* d_params, const void* d_wa
                          const double* d_e_local, int n_walkers, void* d_grad,
                          double* d_e_mean_out, void* stream);
 
+/* Weighted parameter gradient of log|psi|: d_grad = sum_w d_weights[w] d log|psi_w| / d theta
+ * (the vector-Jacobian product of the value-only forward pass).  fn_energy_grad is this
+ * with weights 2 (E_L,w - mean E_L) / B; a batch split across devices uses it with
+ * weights built from the global mean and count, then sums the gradients (Eq. 6).
+ * d_weights [n_walkers] double; d_grad [fn_param_count] blob dtype.           */
+fn_status fn_log_psi_vjp(fn_system_t sys, const void* d_params, const void* d_walkers,
+                         const double* d_weights, int n_walkers, void* d_grad, void* stream);
+
+/* Kernel timing: while enabled, every kernel the handle launches is bracketed by a
+ * CUDA event pair on its stream (adds a few microseconds per launch).  Enabling or
+ * disabling clears the counters.  fn_profile_read waits for the recorded events and
+ * returns the number of kernel classes; for 0 <= index < that number it writes the
+ * class name (static storage), the launch count and the summed device time in ms. */
+fn_status fn_profile_enable(fn_system_t sys, int enable);
+int fn_profile_read(fn_system_t sys, int index, const char** name, int64_t* launches, double* total_ms);
+
 /* Waits for the stream with a deadline (polling, no blocking sync), then reads
  * and clears the device status word.  FN_ERR_TIMEOUT if the deadline passes
  * (work keeps running), FN_ERR_NUMERIC if a kernel flagged a numerical error. */

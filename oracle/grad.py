@@ -39,3 +39,37 @@ def directional_fd(net, params, nuclei, r, e_local, direction, h: float = 1e-5) 
     v = np.asarray(direction, dtype=np.float64)
     return (surrogate(net, params + h * v, nuclei, r, e_local)
             - surrogate(net, params - h * v, nuclei, r, e_local)) / (2 * h)
+
+
+# Central differences carry an O(h^2) truncation error, which near a node of psi (where
+# log|psi| has large third derivatives) exceeds 1e-4 relative at h = 1e-5.  Richardson
+# extrapolation of the steps h and h/2, (4 D(h/2) - D(h)) / 3, cancels that term.
+
+def energy_gradient_richardson(net, params, nuclei, r, e_local, indices, h: float = 1e-5) -> np.ndarray:
+    d1 = energy_gradient_fd(net, params, nuclei, r, e_local, indices, h)
+    d2 = energy_gradient_fd(net, params, nuclei, r, e_local, indices, h / 2)
+    return (4.0 * d2 - d1) / 3.0
+
+
+def directional_richardson(net, params, nuclei, r, e_local, direction, h: float = 1e-5) -> float:
+    d1 = directional_fd(net, params, nuclei, r, e_local, direction, h)
+    d2 = directional_fd(net, params, nuclei, r, e_local, direction, h / 2)
+    return (4.0 * d2 - d1) / 3.0
+
+
+def term_magnitude_fd(net, params, nuclei, r, e_local, indices, h: float = 1e-5) -> np.ndarray:
+    """sum_w |c_w d log|psi_w| / d theta_p| for the given indices (per-walker central
+    differences).  The size of the terms that Eq. 6 sums: a reduced-precision gradient can
+    only be accurate relative to it when the terms cancel."""
+    params = np.asarray(params, dtype=np.float64)
+    e = np.asarray(e_local, dtype=np.float64)
+    c = 2.0 * (e - e.mean()) / e.shape[0]
+    out = np.zeros(len(indices))
+    for n, idx in enumerate(indices):
+        pp = params.copy()
+        pp[idx] += h
+        pm = params.copy()
+        pm[idx] -= h
+        d = (ansatz.log_psi(net, pp, nuclei, r)[0] - ansatz.log_psi(net, pm, nuclei, r)[0]) / (2 * h)
+        out[n] = float(np.sum(np.abs(c * d)))
+    return out

@@ -168,6 +168,32 @@ class System:
                                         _stream(stream)))
         return g, mean
 
+    def log_psi_vjp(self, params, walkers, weights, stream=None):
+        """sum_w weights[w] d log|psi_w| / d theta (blob order, blob dtype)."""
+        self._check_walkers(params, walkers)
+        B = walkers.shape[0]
+        g = torch.empty(self.param_count, dtype=self.dtype, device=walkers.device)
+        weights = weights.to(torch.float64).contiguous()
+        _check(self._lib.fn_log_psi_vjp(self._h, _ptr(params), _ptr(walkers), _ptr(weights), B, _ptr(g),
+                                        _stream(stream)))
+        return g
+
+    def profile_enable(self, enable: bool = True):
+        _check(self._lib.fn_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kernel class: (launches, total device ms)} since the last enable."""
+        out = {}
+        n = self._lib.fn_profile_read(self._h, -1, None, None, None)
+        for i in range(n):
+            name = C.c_char_p()
+            cnt = C.c_int64()
+            ms = C.c_double()
+            self._lib.fn_profile_read(self._h, i, C.byref(name), C.byref(cnt), C.byref(ms))
+            if cnt.value:
+                out[name.value.decode()] = (int(cnt.value), float(ms.value))
+        return out
+
     def sync(self, timeout_ms: int = 60000, stream=None):
         _check(self._lib.fn_sync(self._h, _stream(stream), int(timeout_ms)))
 

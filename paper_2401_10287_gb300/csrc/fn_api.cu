@@ -206,6 +206,7 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
   const size_t o_dG = take((size_t)B * N * N * h2 * sizeof(Cmp));
   const size_t o_dPhi = take((size_t)B * phi_walker_stride(s, 1) * sizeof(Det));
   const size_t o_gradc = take((size_t)s->prep.total * sizeof(Cmp));
+  const size_t o_dP = take((size_t)sh.R * s->cfg.n_dets * N * sizeof(Cmp));
   const size_t o_status = take(sizeof(int) * 4);
   const size_t o_counter = take(sizeof(int64_t) * 4);
   if (ws && ws->base) {
@@ -218,7 +219,7 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
     ws->prep16 = b + o_prep16; ws->walk2 = b + o_walk2; ws->lp2 = (double*)(b + o_lp2);
     ws->scratch_d = (double*)(b + o_scr); ws->dX = b + o_dX; ws->dH = b + o_dH; ws->dZ = b + o_dZ;
     ws->dZw = b + o_dZw; ws->dHbar = b + o_dHbar; ws->dG = b + o_dG; ws->dPhi = b + o_dPhi;
-    ws->gradc = b + o_gradc; ws->status = (int*)(b + o_status); ws->counter = (int64_t*)(b + o_counter);
+    ws->gradc = b + o_gradc; ws->dP = b + o_dP; ws->status = (int*)(b + o_status); ws->counter = (int64_t*)(b + o_counter);
   }
   return off;
 }
@@ -340,6 +341,7 @@ fn_status fn_destroy_system(fn_system_t s) {
   if (s->d_nuclei) cudaFree(s->d_nuclei);
   if (s->d_elec_atom) cudaFree(s->d_elec_atom);
   if (s->d_descs) cudaFree(s->d_descs);
+  delete s->prof;
   delete s;
   return FN_OK;
 }
@@ -464,10 +466,50 @@ fn_status fn_energy_grad(fn_system_t s, const void* d_params, const void* d_walk
     launch_prep_params<Mode>(s, d_params, cs);
     launch_forward<Mode>(s, d_walkers, sh, true, cs);
     launch_det_energy<Mode>(s, d_walkers, sh, nullptr, s->ws.lp2, nullptr, true, cs);
-    launch_backward<Mode>(s, d_walkers, sh, d_e_local, d_grad, d_e_mean, cs);
+    launch_energy_weights<Mode>(s, B, d_e_local, s->ws.scratch_d, d_e_mean, cs);
+    launch_backward<Mode>(s, d_walkers, sh, s->ws.scratch_d, d_grad, cs);
     return 0;
   });
   return check_launch("energy_grad");
+}
+
+fn_status fn_log_psi_vjp(fn_system_t s, const void* d_params, const void* d_walkers, const double* d_weights,
+                         int B, void* d_grad, void* stream) {
+  if (!s || !d_params || !d_walkers || !d_weights || !d_grad || B < 1) {
+    set_error("invalid argument"); return FN_ERR_ARG;
+  }
+  fn_status st = ensure_workspace(s, B);
+  if (st != FN_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  dispatch(s, [&](auto m) {
+    using Mode = decltype(m);
+    const Shape sh = make_shape(s, B, 1);
+    launch_prep_params<Mode>(s, d_params, cs);
+    launch_forward<Mode>(s, d_walkers, sh, true, cs);
+    launch_det_energy<Mode>(s, d_walkers, sh, nullptr, s->ws.lp2, nullptr, true, cs);
+    launch_backward<Mode>(s, d_walkers, sh, d_weights, d_grad, cs);
+    return 0;
+  });
+  return check_launch("log_psi_vjp");
+}
+
+fn_status fn_profile_enable(fn_system_t s, int enable) {
+  if (!s) { set_error("null system"); return FN_ERR_ARG; }
+  if (!s->prof) s->prof = new Profiler();
+  s->prof->reset();
+  s->prof->on = enable != 0;
+  return FN_OK;
+}
+
+int fn_profile_read(fn_system_t s, int index, const char** name, int64_t* launches, double* total_ms) {
+  if (!s) return -1;
+  if (s->prof) s->prof->collect();
+  if (index >= 0 && index < kProfCount) {
+    if (name) *name = prof_name(index);
+    if (launches) *launches = s->prof ? s->prof->launches[index] : 0;
+    if (total_ms) *total_ms = s->prof ? s->prof->ms[index] : 0.0;
+  }
+  return kProfCount;
 }
 
 fn_status fn_sync(fn_system_t s, void* stream, int timeout_ms) {

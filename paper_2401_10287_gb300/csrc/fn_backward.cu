@@ -1,21 +1,397 @@
-// VMC energy gradient (Eq. 6) - reverse pass over the value-only forward.
+// VMC energy gradient (Eq. 6): grad = sum_w c_w d log|psi_w| / d theta with
+// c_w = 2 (E_L,w - mean E_L) / B, E_L held fixed.  A reverse pass over the
+// value-only forward (recomputed by the caller with keep_for_backward; no tangent
+// slab is stored):
+//   determinants   d log|psi| / d A_k = rho_k A_k^{-T}   (written by the det kernel)
+//   orbitals       phi = P env:  dP = dphi env,  d env = dphi P;
+//                  d pi, d sigma accumulated per thread, flushed once per CTA
+//   projection     dW_orb = dP^T h_L, dg = column sums of dP, dh_L = dP W_orb
+//   stream layer   dz = dh (1 - a^2); dV_self = X^T dz, db = sum dz,
+//                  dU = Hbar^T (walker sums of dz); dX = dz V_self;
+//                  dh_l = dX_h + dh_{l+1} (residual) + dHbar / n_spin
+//   pair layer     one warp per pair, lane = channel; dW, dc reduced in registers,
+//                  then per CTA, then one atomic per element
+// Parameter gradients accumulate in the internal layout and are scattered back to
+// the blob order at the end.
+#include <algorithm>
+
 #include "fn_device.cuh"
+#include "fn_gemm.cuh"
 #include "fn_internal.cuh"
 
 namespace fn {
 
-template <class Mode>
-void launch_backward(const fn_system* s, const void* walkers, const Shape& sh, const double* e_local, void* grad,
-                     double* e_mean, cudaStream_t st) {
-  (void)walkers; (void)sh; (void)e_local; (void)e_mean;
-  cudaMemsetAsync(grad, 0, sizeof(typename Mode::Par) * s->P, st);
+// ---- weights c_w = 2 (E_w - mean) / B -------------------------------------------------
+__global__ void k_energy_weights(int B, const double* __restrict__ e, double* __restrict__ c, double* __restrict__ mean_out) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (int w = threadIdx.x; w < B; w += blockDim.x) s += e[w];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  const double mean = red[0] / B;
+  for (int w = threadIdx.x; w < B; w += blockDim.x) c[w] = 2.0 * (e[w] - mean) / B;
+  if (threadIdx.x == 0 && mean_out) *mean_out = mean;
 }
 
-template void launch_backward<ModeF64>(const fn_system*, const void*, const Shape&, const double*, void*, double*,
-                                       cudaStream_t);
-template void launch_backward<ModeF32>(const fn_system*, const void*, const Shape&, const double*, void*, double*,
-                                       cudaStream_t);
-template void launch_backward<ModeBF16>(const fn_system*, const void*, const Shape&, const double*, void*, double*,
-                                        cudaStream_t);
+template <class Mode>
+void launch_energy_weights(const fn_system* s, int B, const double* e_local, double* weights, double* e_mean,
+                           cudaStream_t st) {
+  ProfScope ps(s->prof, kProfBwdMisc, st);
+  k_energy_weights<<<1, 1024, 0, st>>>(B, e_local, weights, e_mean);
+}
+
+// ---- column sums (atomic) -------------------------------------------------------------
+template <typename T, typename Cmp>
+__global__ void k_colsum(const T* __restrict__ src, int64_t rows, int64_t lds, int cols, Cmp* __restrict__ dst) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  const int64_t chunk = (rows + gridDim.y - 1) / gridDim.y;
+  const int64_t r0 = blockIdx.y * chunk, r1 = min(rows, r0 + chunk);
+  Cmp acc = 0;
+  for (int64_t r = r0; r < r1; ++r) acc += (Cmp)ld(src + r * lds + c);
+  atomicAdd(dst + c, acc);
+}
+
+template <typename T, typename Cmp>
+static void colsum(const fn_system* s, cudaStream_t st, const T* src, int64_t rows, int64_t ld, int cols, Cmp* dst) {
+  ProfScope ps(s->prof, kProfBwdMisc, st);
+  dim3 grid((cols + 127) / 128, (unsigned)std::min<int64_t>(64, std::max<int64_t>(1, rows / 256)));
+  k_colsum<T, Cmp><<<grid, 128, 0, st>>>(src, rows, ld, cols, dst);
+}
+
+// ---- orbitals and envelopes ----------------------------------------------------------
+struct OrbBwdArgs {
+  const void* HL;            // [R][h1] value slab
+  const void* wT[2]; const void* g[2]; const void* pi[2]; const void* sig[2];
+  const void* dPhi;          // [B][K (nu^2 + nd^2)] rho_k A^{-T}
+  const double* cw;          // [B]
+  void* dP;                  // [R][K N]
+  void* gpi[2]; void* gsig[2];
+  int h1, K, aniso, chunk;
+};
+
+template <typename Act, typename Cmp, typename Det, typename Wlk>
+__global__ void k_orb_bwd(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh, OrbBwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cmp* hs = (Cmp*)smem_raw;
+  const int spin = blockIdx.y;
+  const int n = spin ? sh.n_dn : sh.n_up;
+  if (n == 0) return;
+  const int n_ko = a.K * n, ko = threadIdx.x;
+  const bool active = ko < n_ko;
+  const int k = active ? ko / n : 0, i = active ? ko % n : 0;
+  const int sig_sz = a.aniso ? 9 : 1;
+  const Cmp* wT = (const Cmp*)a.wT[spin];
+  const Cmp* pi = (const Cmp*)a.pi[spin] + (int64_t)(active ? ko : 0) * sh.M;
+  const Cmp* sg = (const Cmp*)a.sig[spin] + (int64_t)(active ? ko : 0) * sh.M * sig_sz;
+  const int64_t PW1 = (int64_t)a.K * (sh.n_up * sh.n_up + sh.n_dn * sh.n_dn);
+  const int64_t inv_off = spin ? (int64_t)a.K * sh.n_up * sh.n_up : 0;
+  const int ldp = a.K * sh.N, poff = spin ? a.K * sh.n_up : 0;
+  Cmp acc_pi[kMaxNuclei], acc_sig[kMaxNuclei * 9], em[kMaxNuclei];
+  for (int q = 0; q < sh.M; ++q) acc_pi[q] = 0;
+  for (int q = 0; q < sh.M * sig_sz; ++q) acc_sig[q] = 0;
+  const int w0 = blockIdx.x * a.chunk, w1 = min(sh.B, w0 + a.chunk);
+  for (int w = w0; w < w1; ++w) {
+    for (int jj = 0; jj < n; ++jj) {
+      const int j = jj + (spin ? sh.n_up : 0);
+      const int64_t row = tile_row(w, j, sh.N, sh.wpt);
+      for (int c = threadIdx.x; c < a.h1; c += blockDim.x) hs[c] = (Cmp)ld((const Act*)a.HL + row * a.h1 + c);
+      __syncthreads();
+      if (active) {
+        Cmp P = ((const Cmp*)a.g[spin])[ko];
+        for (int c = 0; c < a.h1; ++c) P += hs[c] * wT[(int64_t)c * n_ko + ko];
+        const Wlk* rj = r + ((int64_t)w * sh.N + j) * 3;
+        Cmp env = 0;
+        Cmp dv[kMaxNuclei][3];
+        Cmp sv[kMaxNuclei];
+        for (int m = 0; m < sh.M; ++m) {
+          for (int c = 0; c < 3; ++c) dv[m][c] = (Cmp)((double)rj[c] - nuc[3 * m + c]);
+          Cmp s;
+          if (!a.aniso) {
+            s = sg[m] * f_sqrt(dv[m][0] * dv[m][0] + dv[m][1] * dv[m][1] + dv[m][2] * dv[m][2]);
+          } else {
+            const Cmp* S = sg + m * 9;
+            Cmp u2 = 0;
+            for (int x = 0; x < 3; ++x) {
+              const Cmp u = S[3 * x] * dv[m][0] + S[3 * x + 1] * dv[m][1] + S[3 * x + 2] * dv[m][2];
+              u2 += u * u;
+            }
+            s = f_sqrt(u2);
+          }
+          sv[m] = s;
+          em[m] = f_exp(-s);
+          env += pi[m] * em[m];
+        }
+        const Cmp dphi = (Cmp)(a.cw[w] * (double)((const Det*)a.dPhi)[(int64_t)w * PW1 + inv_off +
+                                                                     (int64_t)k * n * n + i * n + jj]);
+        const Cmp dPv = dphi * env, denv = dphi * P;
+        ((Cmp*)a.dP)[row * ldp + poff + ko] = dPv;
+        for (int m = 0; m < sh.M; ++m) {
+          acc_pi[m] += denv * em[m];
+          const Cmp f = -denv * pi[m] * em[m];
+          if (!a.aniso) {
+            acc_sig[m] += f * f_sqrt(dv[m][0] * dv[m][0] + dv[m][1] * dv[m][1] + dv[m][2] * dv[m][2]);
+          } else {
+            const Cmp* S = sg + m * 9;
+            for (int x = 0; x < 3; ++x) {
+              const Cmp u = S[3 * x] * dv[m][0] + S[3 * x + 1] * dv[m][1] + S[3 * x + 2] * dv[m][2];
+              for (int y = 0; y < 3; ++y) acc_sig[m * 9 + 3 * x + y] += f * u * dv[m][y] / sv[m];
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (active) {
+    for (int m = 0; m < sh.M; ++m) atomicAdd((Cmp*)a.gpi[spin] + (int64_t)ko * sh.M + m, acc_pi[m]);
+    for (int q = 0; q < sh.M * sig_sz; ++q)
+      atomicAdd((Cmp*)a.gsig[spin] + (int64_t)ko * sh.M * sig_sz + q, acc_sig[q]);
+  }
+}
+
+// ---- stream layers -------------------------------------------------------------------
+template <typename Cmp>
+__global__ void k_bwd_tanh(Shape sh, int h1, const Cmp* __restrict__ dH, const Cmp* __restrict__ act,
+                           Cmp* __restrict__ dZ, Cmp* __restrict__ dZw) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)sh.B * h1) return;
+  const int w = (int)(gid / h1), c = (int)(gid % h1);
+  Cmp sum = 0;
+  for (int i = 0; i < sh.N; ++i) {
+    const int64_t row = tile_row(w, i, sh.N, sh.wpt);
+    const Cmp a = act[row * h1 + c];
+    const Cmp dz = dH[row * h1 + c] * ((Cmp)1 - a * a);
+    dZ[row * h1 + c] = dz;
+    sum += dz;
+  }
+  dZw[(int64_t)w * h1 + c] = sum;
+}
+
+template <typename Cmp>
+__global__ void k_bwd_dh(Shape sh, int h1, int ldx, int d_h, const Cmp* __restrict__ dX,
+                         const Cmp* __restrict__ dHbar, Cmp* __restrict__ dH) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)sh.B * sh.N * h1) return;
+  const int c = (int)(gid % h1);
+  const int64_t wi = gid / h1;
+  const int w = (int)(wi / sh.N), i = (int)(wi % sh.N);
+  const int s = i < sh.n_up ? 0 : 1;
+  const int ns = s ? sh.n_dn : sh.n_up;
+  const int64_t row = tile_row(w, i, sh.N, sh.wpt);
+  dH[row * h1 + c] = dX[row * ldx + c] + dH[row * h1 + c] + dHbar[(int64_t)w * 2 * d_h + s * d_h + c] / (Cmp)ns;
+}
+
+// ---- two-electron stream, level l ----------------------------------------------------
+struct PairBwdArgs {
+  int l, L, h2, d_g;          // level, layers, pair width, input width of level l
+  const void* g_in;           // g^l values [B][N][N][h2] (l >= 1), null: recompute features
+  const void* g_out;          // g^{l+1} values (l < L-1)
+  const void* W; const void* c;   // pair layer l weights [h2][d_g], [h2] (l < L-1)
+  void* gW; void* gc;         // gradients of W_l, c_l
+  void* dG;                   // [B][N][N][h2]: in dg^{l+1}, out dg^l
+  const void* dX; int ldx; int col0;   // mean-g columns of the one-electron layer-l input gradient
+};
+
+template <typename Cmp, typename Wlk>
+__global__ void __launch_bounds__(128) k_pair_bwd(const Wlk* __restrict__ r, Shape sh, PairBwdArgs a) {
+  __shared__ Cmp red[4][32][33];
+  const int w = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int N = sh.N;
+  const bool has_layer = a.l < a.L - 1;
+  Cmp accW[32];
+  for (int q = 0; q < 32; ++q) accW[q] = 0;
+  Cmp accc = 0;
+  const Wlk* rw = r + (int64_t)w * N * 3;
+  for (int p = warp; p < N * N; p += 4) {
+    const int i = p / N, j = p % N;
+    const int64_t pidx = ((int64_t)w * N + i) * N + j;
+    // input g^l of this lane's channel
+    Cmp gin = 0;
+    if (a.g_in) {
+      gin = lane < a.d_g ? ((const Cmp*)a.g_in)[pidx * a.h2 + lane] : (Cmp)0;
+    } else if (i != j && lane < 4) {
+      const double d[3] = {(double)rw[3 * i] - (double)rw[3 * j], (double)rw[3 * i + 1] - (double)rw[3 * j + 1],
+                           (double)rw[3 * i + 2] - (double)rw[3 * j + 2]};
+      gin = lane < 3 ? (Cmp)d[lane] : (Cmp)sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    }
+    Cmp dgl = 0;
+    if (has_layer) {
+      const Cmp dgn = lane < a.h2 ? ((const Cmp*)a.dG)[pidx * a.h2 + lane] : (Cmp)0;
+      const Cmp gout = lane < a.h2 ? ((const Cmp*)a.g_out)[pidx * a.h2 + lane] : (Cmp)0;
+      const Cmp t = a.l >= 1 ? gout - gin : gout;
+      const Cmp dz = lane < a.h2 ? dgn * ((Cmp)1 - t * t) : (Cmp)0;
+      accc += dz;
+      const Cmp* W = (const Cmp*)a.W;
+      for (int q = 0; q < a.h2; ++q) {
+        const Cmp dzq = __shfl_sync(0xffffffffu, dz, q);
+        accW[q] += dzq * gin;                                   // dW[q][lane]
+        if (lane < a.d_g) dgl += W[q * a.d_g + lane] * dzq;
+      }
+      if (a.l >= 1) dgl += dgn;
+    }
+    if (lane < a.d_g) {
+      const int sj = j < sh.n_up ? 0 : 1;
+      const int nsj = sj ? sh.n_dn : sh.n_up;
+      const int64_t row = tile_row(w, i, N, sh.wpt);
+      dgl += ((const Cmp*)a.dX)[row * a.ldx + a.col0 + sj * a.d_g + lane] / (Cmp)nsj;
+    }
+    if (a.l >= 1 && lane < a.h2) ((Cmp*)a.dG)[pidx * a.h2 + lane] = dgl;
+  }
+  if (!has_layer) return;
+  // block reduction of dW (lane = column, q = row) and dc
+  for (int q = 0; q < 32; ++q) red[warp][q][lane] = accW[q];
+  __syncthreads();
+  for (int e = threadIdx.x; e < a.h2 * a.d_g; e += blockDim.x) {
+    const int q = e / a.d_g, c = e % a.d_g;
+    const Cmp v = red[0][q][c] + red[1][q][c] + red[2][q][c] + red[3][q][c];
+    atomicAdd((Cmp*)a.gW + e, v);
+  }
+  __syncthreads();
+  red[warp][0][lane] = accc;
+  __syncthreads();
+  if (threadIdx.x < a.h2)
+    atomicAdd((Cmp*)a.gc + threadIdx.x, red[0][0][threadIdx.x] + red[1][0][threadIdx.x] + red[2][0][threadIdx.x] +
+                                             red[3][0][threadIdx.x]);
+}
+
+// ---- internal layout -> blob order ---------------------------------------------------
+template <typename Par, typename Cmp>
+__global__ void k_unprep(Par* __restrict__ blob, const CopyDesc* __restrict__ descs, const Cmp* __restrict__ gradc) {
+  const CopyDesc d = descs[blockIdx.y];
+  if (d.to16) return;
+  const int64_t n = (int64_t)d.rows * d.cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t rr = e / d.cols, cc = e % d.cols;
+    blob[d.src + rr * d.s_rs + cc * d.s_cs] = (Par)gradc[d.dst + rr * d.d_rs + cc * d.d_cs];
+  }
+}
+
+template <class Mode>
+void launch_backward(const fn_system* s, const void* walkers, const Shape& sh, const double* weights, void* grad,
+                     cudaStream_t st) {
+  using Act = typename Mode::Act; using Cmp = typename Mode::Cmp; using Det = typename Mode::Det;
+  using Wlk = typename Mode::Wlk; using Par = typename Mode::Par;
+  const Workspace& ws = s->ws;
+  const int L = s->cfg.n_layers, h1 = s->cfg.h1, h2 = s->cfg.h2, K = s->cfg.n_dets, N = s->N;
+  const Cmp* prep = (const Cmp*)ws.prep;
+  Cmp* gradc = (Cmp*)ws.gradc;
+  const PrepLayout& pl = s->prep;
+  const Wlk* r = (const Wlk*)walkers;
+  const int64_t R = sh.R;
+  const int ldp = K * N;
+  const int split = (int)std::max<int64_t>(1, std::min<int64_t>(64, R / 1024));
+  cudaMemsetAsync(gradc, 0, sizeof(Cmp) * pl.total, st);
+  cudaMemsetAsync(ws.dP, 0, sizeof(Cmp) * R * ldp, st);
+  cudaMemsetAsync(ws.dH, 0, sizeof(Cmp) * R * h1, st);
+  // orbitals + envelopes
+  {
+    OrbBwdArgs a{};
+    a.HL = ws.HL;
+    for (int q = 0; q < 2; ++q) {
+      a.wT[q] = prep + pl.wT[q]; a.g[q] = prep + pl.g[q]; a.pi[q] = prep + pl.pi[q]; a.sig[q] = prep + pl.sig[q];
+      a.gpi[q] = gradc + pl.pi[q]; a.gsig[q] = gradc + pl.sig[q];
+    }
+    a.dPhi = ws.dPhi; a.cw = weights; a.dP = ws.dP;
+    a.h1 = h1; a.K = K; a.aniso = s->cfg.envelope == FN_ENV_ANISOTROPIC;
+    a.chunk = std::max(1, sh.B / (2 * s->sm_count));
+    const int threads = (int)std::min<int64_t>(1024, round_up((int64_t)K * std::max(s->n_up, s->n_dn), 32));
+    dim3 grid((sh.B + a.chunk - 1) / a.chunk, 2);
+    ProfScope ps(s->prof, kProfBwdOrb, st);
+    k_orb_bwd<Act, Cmp, Det, Wlk><<<grid, threads, sizeof(Cmp) * h1, st>>>(r, s->d_nuclei, sh, a);
+  }
+  const int ns[2] = {s->n_up, s->n_dn};
+  for (int q = 0; q < 2; ++q) {
+    if (!ns[q]) continue;
+    const int n_ko = K * ns[q];
+    const Cmp* dPq = (const Cmp*)ws.dP + (q ? K * s->n_up : 0);
+    // dW_orb^T [h1][K n]: sum over rows of h_L[row][c] dP[row][ko]
+    {
+      ProfScope ps(s->prof, kProfBwdGemm, st);
+      gemm<Act, Cmp, Cmp, Cmp>(st, h1, n_ko, (int)R, (const Act*)ws.HL, 1, h1, dPq, ldp, 1, gradc + pl.wT[q], n_ko, 1,
+                               (const Cmp*)nullptr, 0, split, true);
+    }
+    colsum<Cmp, Cmp>(s, st, dPq, R, ldp, n_ko, gradc + pl.g[q]);
+    // dh_L[row][c] += sum_ko dP[row][ko] w[ko][c]
+    {
+      ProfScope ps(s->prof, kProfBwdGemm, st);
+      gemm<Cmp, Cmp, Cmp, Cmp>(st, (int)R, h1, n_ko, dPq, ldp, 1, prep + pl.wT[q], 1, n_ko, (Cmp*)ws.dH, h1, 1,
+                               (const Cmp*)nullptr, 0, 1, true);
+    }
+  }
+  Cmp* dH = (Cmp*)ws.dH;
+  Cmp* dZ = (Cmp*)ws.dZ;
+  Cmp* dZw = (Cmp*)ws.dZw;
+  Cmp* dX = (Cmp*)ws.dX;
+  Cmp* dHbar = (Cmp*)ws.dHbar;
+  for (int l = L - 1; l >= 0; --l) {
+    const LayerDims& d = s->layer[l];
+    cudaMemsetAsync(dZ, 0, sizeof(Cmp) * R * h1, st);
+    {
+      const int64_t n = (int64_t)sh.B * h1;
+      ProfScope ps(s->prof, kProfBwdMisc, st);
+      k_bwd_tanh<Cmp><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sh, h1, dH, (const Cmp*)ws.act[l], dZ, dZw);
+    }
+    const Act* X = (const Act*)ws.X[l];
+    // dV_self (internal [k_self][h1]) += X^T dZ
+    {
+      ProfScope ps(s->prof, kProfBwdGemm, st);
+      gemm<Act, Cmp, Cmp, Cmp>(st, d.k_self, h1, (int)R, X, 1, d.ldx, dZ, h1, 1, gradc + pl.VsT[l], h1, 1,
+                               (const Cmp*)nullptr, 0, split, true);
+    }
+    colsum<Cmp, Cmp>(s, st, dZw, sh.B, h1, h1, gradc + pl.b[l]);
+    // dU (internal [2 d_h][h1]) += Hbar^T dZw
+    const int splitB = (int)std::max(1, std::min(32, sh.B / 256));
+    {
+      ProfScope ps(s->prof, kProfBwdGemm, st);
+      gemm<Cmp, Cmp, Cmp, Cmp>(st, 2 * d.d_h, h1, sh.B, (const Cmp*)ws.Hbar[l], 1, 2 * d.d_h, dZw, h1, 1,
+                               gradc + pl.UT[l], h1, 1, (const Cmp*)nullptr, 0, splitB, true);
+    }
+    // dX = dZ V_self^T  ([R][k_self], row stride ldx)
+    {
+      ProfScope ps(s->prof, kProfBwdGemm, st);
+      gemm<Cmp, Cmp, Cmp, Cmp>(st, (int)R, d.k_self, h1, dZ, h1, 1, prep + pl.VsT[l], 1, h1, dX, d.ldx, 1,
+                               (const Cmp*)nullptr, 0, 1, false);
+    }
+    if (l >= 1) {
+      {
+        ProfScope ps(s->prof, kProfBwdGemm, st);
+        gemm<Cmp, Cmp, Cmp, Cmp>(st, sh.B, 2 * d.d_h, h1, dZw, h1, 1, prep + pl.UT[l], 1, h1, dHbar, 2 * d.d_h, 1,
+                                 (const Cmp*)nullptr, 0, 1, false);
+      }
+      const int64_t n = (int64_t)sh.B * N * h1;
+      ProfScope ps(s->prof, kProfBwdMisc, st);
+      k_bwd_dh<Cmp><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sh, h1, d.ldx, d.d_h, dX, dHbar, dH);
+    }
+    // two-electron stream level l
+    if (L > 1) {
+      PairBwdArgs a{};
+      a.l = l; a.L = L; a.h2 = h2; a.d_g = d.d_g;
+      a.g_in = l >= 1 ? ws.gpair[l] : nullptr;
+      a.g_out = l < L - 1 ? ws.gpair[l + 1] : nullptr;
+      if (l < L - 1) {
+        a.W = prep + pl.W[l]; a.c = prep + pl.c[l];
+        a.gW = gradc + pl.W[l]; a.gc = gradc + pl.c[l];
+      }
+      a.dG = ws.dG; a.dX = dX; a.ldx = d.ldx; a.col0 = d.d_h;
+      ProfScope ps(s->prof, kProfBwdPair, st);
+      k_pair_bwd<Cmp, Wlk><<<sh.B, 128, 0, st>>>(r, sh, a);
+    }
+  }
+  dim3 grid(32, s->n_descs);
+  ProfScope ps(s->prof, kProfBwdMisc, st);
+  k_unprep<Par, Cmp><<<grid, 256, 0, st>>>((Par*)grad, (const CopyDesc*)s->d_descs, gradc);
+}
+
+#define FN_INST(M)                                                                                           \
+  template void launch_energy_weights<M>(const fn_system*, int, const double*, double*, double*, cudaStream_t); \
+  template void launch_backward<M>(const fn_system*, const void*, const Shape&, const double*, void*, cudaStream_t);
+FN_INST(ModeF64)
+FN_INST(ModeF32)
+FN_INST(ModeBF16)
 
 }  // namespace fn

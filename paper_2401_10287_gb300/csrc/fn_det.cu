@@ -297,6 +297,7 @@ void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh,
   const bool full = sh.T > 1 && e_local != nullptr;
   const int nmax = std::max(s->n_up, s->n_dn), NC = 3 * s->N, K = s->cfg.n_dets;
   const size_t smem = sizeof(Det) * (4 * nmax * nmax + 4 * K + (full ? K * NC + 4 * NC : 0) + 8 + 128);
+  ProfScope ps(s->prof, full ? kProfDetFull : kProfDetValue, st);
   if (full) {
     cudaFuncSetAttribute(k_det_energy<Det, Wlk, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_det_energy<Det, Wlk, true><<<sh.B, 128, smem, st>>>((const Wlk*)walkers, s->d_nuclei, sh, a);

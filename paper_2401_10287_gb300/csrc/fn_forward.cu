@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "fn_device.cuh"
+#include "fn_gemm.cuh"
 #include "fn_internal.cuh"
 
 namespace fn {
@@ -21,12 +22,6 @@ namespace fn {
 // ---------------------------------------------------------------------------------------
 // parameter preparation
 // ---------------------------------------------------------------------------------------
-struct CopyDesc {
-  int64_t src, s_rs, s_cs;   // source offset and strides (row, col) in the blob
-  int64_t dst, d_rs, d_cs;   // destination offset and strides
-  int rows, cols;
-  int to16;                  // 1: destination is the bf16 array
-};
 
 template <typename Par, typename Cmp>
 __global__ void k_prep(const Par* __restrict__ blob, const CopyDesc* __restrict__ descs, int n_desc,
@@ -89,6 +84,7 @@ template <class Mode>
 void launch_prep_params(const fn_system* s, const void* params, cudaStream_t st) {
   using Par = typename Mode::Par; using Cmp = typename Mode::Cmp;
   dim3 grid(32, s->n_descs);
+  ProfScope ps(s->prof, kProfPrep, st);
   k_prep<Par, Cmp><<<grid, 256, 0, st>>>((const Par*)params, (const CopyDesc*)s->d_descs, s->n_descs,
                                          (Cmp*)s->ws.prep,
                                          (__nv_bfloat16*)s->ws.prep16);
@@ -298,68 +294,6 @@ __global__ void k_pair_stream(const Wlk* __restrict__ r, Shape sh, PairArgs a) {
       }
     }
   }
-}
-
-// ---------------------------------------------------------------------------------------
-// tiled SIMT GEMM: C(m,n) (+)= sum_k A(m,k) B(k,n) + bias[n] (rows m < bias_rows)
-// ---------------------------------------------------------------------------------------
-template <typename TA, typename TB, typename TC, typename Cmp>
-__global__ void __launch_bounds__(256) k_gemm(int Mr, int Nc, int Kd, const TA* __restrict__ A, int64_t sam,
-                                              int64_t sak, const TB* __restrict__ Bm, int64_t sbk, int64_t sbn,
-                                              TC* __restrict__ C, int64_t scm, int64_t scn,
-                                              const Cmp* __restrict__ bias, int64_t bias_rows, int atomic_acc) {
-  __shared__ Cmp As[16][64 + 1];
-  __shared__ Cmp Bs[16][64 + 1];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
-  const int kchunk = (Kd + gridDim.z - 1) / gridDim.z;
-  const int kbeg = blockIdx.z * kchunk, kend = min(Kd, kbeg + kchunk);
-  Cmp acc[4][4] = {};
-  for (int k0 = kbeg; k0 < kend; k0 += 16) {
-    for (int e = tid; e < 16 * 64; e += 256) {
-      const int kk = e / 64, mm = e % 64;
-      const int64_t m = m0 + mm;
-      const int k = k0 + kk;
-      As[kk][mm] = (m < Mr && k < kend) ? (Cmp)ld(A + m * sam + k * sak) : (Cmp)0;
-      const int64_t n = n0 + mm;
-      Bs[kk][mm] = (n < Nc && k < kend) ? (Cmp)ld(Bm + k * sbk + n * sbn) : (Cmp)0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      Cmp av[4], bv[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) { av[q] = As[kk][ty * 4 + q]; bv[q] = Bs[kk][tx * 4 + q]; }
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) acc[q][p] += av[q] * bv[p];
-    }
-    __syncthreads();
-  }
-  for (int q = 0; q < 4; ++q) {
-    const int64_t m = m0 + ty * 4 + q;
-    if (m >= Mr) continue;
-    for (int p = 0; p < 4; ++p) {
-      const int64_t n = n0 + tx * 4 + p;
-      if (n >= Nc) continue;
-      Cmp v = acc[q][p];
-      if (bias && m < bias_rows && blockIdx.z == 0) v += bias[n];
-      TC* o = C + m * scm + n * scn;
-      if (atomic_acc) atomicAdd(o, (TC)v);
-      else st(o, v);
-    }
-  }
-}
-
-template <typename TA, typename TB, typename TC, typename Cmp>
-void gemm(cudaStream_t st, int Mr, int Nc, int Kd, const TA* A, int64_t sam, int64_t sak, const TB* Bm,
-          int64_t sbk, int64_t sbn, TC* C, int64_t scm, int64_t scn, const Cmp* bias, int64_t bias_rows,
-          int split_k, bool atomic_acc) {
-  if (Mr <= 0 || Nc <= 0 || Kd <= 0) return;
-  dim3 grid((Nc + 63) / 64, (Mr + 63) / 64, std::max(1, split_k));
-  k_gemm<TA, TB, TC, Cmp><<<grid, 256, 0, st>>>(Mr, Nc, Kd, A, sam, sak, Bm, sbk, sbn, C, scm, scn, bias,
-                                                 bias_rows, (atomic_acc || split_k > 1) ? 1 : 0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -582,6 +516,7 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
   // inputs
   {
     const int64_t n = (int64_t)sh.B * sh.N;
+    ProfScope ps(s->prof, kProfFeatures, st);
     k_features_en<Act, Wlk><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(r, s->d_nuclei, sh, (Act*)ws.X[0],
                                                                            s->layer[0].ldx);
     const int64_t m = (int64_t)sh.B * 2 * sh.M;
@@ -601,6 +536,7 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     }
     const int64_t threads = (int64_t)sh.B * sh.N * 32;
     const unsigned blocks = (unsigned)((threads + 127) / 128);
+    ProfScope ps(s->prof, kProfPair, st);
     if (full) k_pair_stream<Act, Cmp, Wlk, true><<<blocks, 128, 0, st>>>(r, sh, pa);
     else k_pair_stream<Act, Cmp, Wlk, false><<<blocks, 128, 0, st>>>(r, sh, pa);
   }
@@ -608,8 +544,11 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     const LayerDims& d = s->layer[l];
     // mean-field term M = Hbar_l U_l^T + b_l (bias on the value slab only)
     const Cmp* Hb = (const Cmp*)ws.Hbar[l];
+    {
+    ProfScope ps(s->prof, kProfMeanGemm, st);
     gemm<Cmp, Cmp, Cmp, Cmp>(st, sh.T * sh.B, h1, 2 * d.d_h, Hb, 2 * d.d_h, 1, prep + s->prep.UT[l], h1, 1,
                              (Cmp*)ws.Mterm, h1, 1, prep + s->prep.b[l], sh.B, 1, false);
+    }
     LayerArgs la{};
     la.X = ws.X[l]; la.ldx = d.ldx; la.k_self = d.k_self;
     la.VsT = prep + s->prep.VsT[l];
@@ -623,6 +562,7 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     la.h1 = h1;
     const size_t smem = sizeof(Cmp) * (32 * 132 + 32 * 64 + 128 * 65);
     dim3 grid(sh.tiles, (h1 + 63) / 64);
+    ProfScope ps(s->prof, full ? kProfLayerFull : kProfLayerValue, st);
     if (full) {
       cudaFuncSetAttribute(k_layer<Act, Cmp, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_layer<Act, Cmp, true><<<grid, 256, smem, st>>>(sh, la);
@@ -645,6 +585,7 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     const int threads = (int)std::min<int64_t>(1024, round_up(ko_max, 32));
     const size_t smem = sizeof(Cmp) * h1;
     const unsigned blocks = (unsigned)((int64_t)sh.B * sh.N);
+    ProfScope ps(s->prof, full ? kProfOrbFull : kProfOrbValue, st);
     if (full) k_orbitals<Act, Cmp, Det, Wlk, true><<<blocks, threads, smem, st>>>(r, s->d_nuclei, sh, oa);
     else k_orbitals<Act, Cmp, Det, Wlk, false><<<blocks, threads, smem, st>>>(r, s->d_nuclei, sh, oa);
   }
@@ -656,13 +597,5 @@ template void launch_prep_params<ModeBF16>(const fn_system*, const void*, cudaSt
 template void launch_forward<ModeF64>(const fn_system*, const void*, const Shape&, bool, cudaStream_t);
 template void launch_forward<ModeF32>(const fn_system*, const void*, const Shape&, bool, cudaStream_t);
 template void launch_forward<ModeBF16>(const fn_system*, const void*, const Shape&, bool, cudaStream_t);
-
-// explicit GEMM instantiations used by the backward pass
-template void gemm<float, float, float, float>(cudaStream_t, int, int, int, const float*, int64_t, int64_t,
-                                               const float*, int64_t, int64_t, float*, int64_t, int64_t,
-                                               const float*, int64_t, int, bool);
-template void gemm<double, double, double, double>(cudaStream_t, int, int, int, const double*, int64_t, int64_t,
-                                                   const double*, int64_t, int64_t, double*, int64_t, int64_t,
-                                                   const double*, int64_t, int, bool);
 
 }  // namespace fn

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "../../include/fnvmc.h"
+#include "fn_profile.cuh"
 
 namespace fn {
 
@@ -93,6 +94,14 @@ struct PrepLayout {
   int64_t total16;
 };
 
+// One strided copy of the parameter preparation: blob -> internal layout.
+struct CopyDesc {
+  int64_t src, s_rs, s_cs;   // source offset and strides (row, col) in the blob
+  int64_t dst, d_rs, d_cs;   // destination offset and strides
+  int rows, cols;
+  int to16;                  // 1: destination is the bf16 array
+};
+
 struct Workspace {
   void* base = nullptr;
   size_t bytes = 0;
@@ -119,6 +128,7 @@ struct Workspace {
   void* dG = nullptr;            // [B][N][N][h2] (Cmp) gradient wrt the pair stream
   void* dPhi = nullptr;          // [B][orbital block, value slab] (Det)
   void* gradc = nullptr;         // prepared-layout gradient accumulator (Cmp)
+  void* dP = nullptr;            // [R][K (n_up + n_dn)] gradient wrt orbital projections (Cmp)
   int* status = nullptr;         // device status word
   int64_t* counter = nullptr;    // scratch counter
 };
@@ -146,6 +156,7 @@ struct fn_system {
   int* d_elec_atom = nullptr;    // [N]
   void* d_descs = nullptr;       // parameter-preparation copy descriptors
   int n_descs = 0;
+  fn::Profiler* prof = nullptr;  // kernel-class timing (fn_profile_enable)
 };
 
 namespace fn {
@@ -175,8 +186,9 @@ template <class Mode> void launch_propose(const fn_system* s, int B, const void*
 template <class Mode> void launch_accept(const fn_system* s, int B, void* walkers, const void* prop,
                                          double* lp, const double* lp_new, uint64_t seed,
                                          uint32_t step_idx, int64_t* accept_count, cudaStream_t st);
+template <class Mode> void launch_energy_weights(const fn_system* s, int B, const double* e_local, double* weights,
+                                                 double* e_mean, cudaStream_t st);
 template <class Mode> void launch_backward(const fn_system* s, const void* walkers, const Shape& sh,
-                                           const double* e_local, void* grad, double* e_mean,
-                                           cudaStream_t st);
+                                           const double* weights, void* grad, cudaStream_t st);
 
 }  // namespace fn

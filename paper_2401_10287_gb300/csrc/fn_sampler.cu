@@ -90,6 +90,7 @@ template <class Mode>
 void launch_init_walkers(const fn_system* s, int B, uint64_t seed, double std_, void* walkers, cudaStream_t st) {
   using Wlk = typename Mode::Wlk;
   const int64_t n = (int64_t)B * s->N * 3;
+  ProfScope ps(s->prof, kProfInit, st);
   k_init_walkers<Wlk><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(B, s->N, s->d_elec_atom, s->d_nuclei, std_, seed,
                                                                      s->walker_offset, (Wlk*)walkers);
 }
@@ -99,6 +100,7 @@ void launch_propose(const fn_system* s, int B, const void* walkers, void* out, d
                     uint32_t step_idx, cudaStream_t st) {
   using Wlk = typename Mode::Wlk;
   const int64_t n = (int64_t)B * s->N * 3;
+  ProfScope ps(s->prof, kProfSampler, st);
   k_propose<Wlk><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(B, s->N, (const Wlk*)walkers, (Wlk*)out, step, seed,
                                                                 step_idx, s->walker_offset);
 }
@@ -107,6 +109,7 @@ template <class Mode>
 void launch_accept(const fn_system* s, int B, void* walkers, const void* prop, double* lp, const double* lp_new,
                    uint64_t seed, uint32_t step_idx, int64_t* accept_count, cudaStream_t st) {
   using Wlk = typename Mode::Wlk;
+  ProfScope ps(s->prof, kProfSampler, st);
   k_accept<Wlk><<<(B + 127) / 128, 128, 0, st>>>(B, s->N, (Wlk*)walkers, (const Wlk*)prop, lp, lp_new, seed, step_idx,
                                                   s->walker_offset, (unsigned long long*)accept_count);
 }
@@ -141,6 +144,7 @@ void launch_init_params(const fn_system* s, uint64_t seed, void* params, cudaStr
       const int64_t end = (a == 0 && ns[1]) ? s->off_pi[1] : s->P;
       add(s->off_sig[a], end, s->cfg.envelope == FN_ENV_ANISOTROPIC ? 2 : 1, 1);
     }
+  ProfScope ps(s->prof, kProfInit, st);
   k_init_params<Par><<<(unsigned)((s->P + 255) / 256), 256, 0, st>>>(s->P, g, seed, (Par*)params);
 }
 

@@ -92,3 +92,17 @@ def test_gradient_directional_linearity():
     v[idx] = w
     d = grad.directional_fd(net, blob, s.nuclei, r, e, v)
     assert abs(d - g @ w) < 1e-5 * max(1.0, abs(g @ w))
+
+
+def test_richardson_removes_h2_term():
+    """On a gradient with large curvature the extrapolated value is h-independent to ~1e-9."""
+    s = W.lih(1)
+    net = ansatz.Net(2, 2, 1, 2, 8, 4, 2, "aniso")
+    blob = ansatz.init_params(net, 2)
+    r, _ = mcmc.init_walkers(s.nuclei, s.charges, 2, 1, s.partial_charges, 12, 1, 0.5)
+    e, _, _ = ansatz.local_energy(net, blob, s.nuclei, s.charges, r)
+    a = grad.energy_gradient_richardson(net, blob, s.nuclei, r, e, [3], h=1e-4)
+    b = grad.energy_gradient_richardson(net, blob, s.nuclei, r, e, [3], h=5e-5)
+    plain = grad.energy_gradient_fd(net, blob, s.nuclei, r, e, [3], h=1e-4)
+    assert abs(a[0] - b[0]) < 1e-7 * abs(a[0])
+    assert abs(plain[0] - b[0]) > 10 * abs(a[0] - b[0])
