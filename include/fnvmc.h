@@ -65,7 +65,7 @@ typedef enum { FN_ENV_ISOTROPIC = 0, FN_ENV_ANISOTROPIC = 1 } fn_envelope;
 
 /* Network sizes ("FermiNet Model" section):
  *   n_layers  one-electron stream layers L >= 1 (the two-electron stream has L-1);
- *   h1        one-electron width, 1..1024, multiple of 8 in FN_BF16_MIXED;
+ *   h1        one-electron width, 1..1024, multiple of 32 in FN_BF16_MIXED;
  *   h2        two-electron width, 1..32;
  *   n_dets    determinants K, 1..64;
  *   envelope  fn_envelope: scalar sigma per (k, i, m, spin) or 3x3 sigma (Eq. 4);
@@ -178,7 +178,8 @@ int fn_profile_read(fn_system_t sys, int index, const char** name, int64_t* laun
 
 /* Waits for the stream with a deadline (polling, no blocking sync), then reads
  * and clears the device status word.  FN_ERR_TIMEOUT if the deadline passes
- * (work keeps running), FN_ERR_NUMERIC if a kernel flagged a numerical error. */
+ * (work keeps running) or if a tensor-core kernel gave up on a bounded wait,
+ * FN_ERR_NUMERIC if a kernel flagged a numerical error.                     */
 fn_status fn_sync(fn_system_t sys, void* stream, int timeout_ms);
 
 const char* fn_last_error(void);

@@ -262,7 +262,13 @@ static fn_status ensure_workspace(fn_system* s, int B) {
   return FN_OK;
 }
 
-static fn_status check_launch(const char* what) {
+static fn_status check_launch(fn_system* s, const char* what) {
+  if (s->host_error != FN_OK) {
+    const fn_status e = s->host_error;
+    s->host_error = FN_OK;
+    set_error(std::string(what) + ": a TMA tensor map could not be encoded");
+    return e;
+  }
   return cuda_status(cudaGetLastError(), what);
 }
 
@@ -293,8 +299,8 @@ fn_status fn_create_system(const double* h_nuclei, const double* h_charges, int 
       cfg->precision < FN_FP64 || cfg->precision > FN_BF16_MIXED) {
     set_error("network configuration out of range"); return FN_ERR_ARG;
   }
-  if (cfg->precision == FN_BF16_MIXED && cfg->h1 % 8 != 0) {
-    set_error("h1 must be a multiple of 8 in FN_BF16_MIXED"); return FN_ERR_ARG;
+  if (cfg->precision == FN_BF16_MIXED && cfg->h1 % 32 != 0) {
+    set_error("h1 must be a multiple of 32 in FN_BF16_MIXED"); return FN_ERR_ARG;
   }
   double zsum = 0.0;
   for (int m = 0; m < n_nuclei; ++m) {
@@ -330,6 +336,9 @@ fn_status fn_create_system(const double* h_nuclei, const double* h_charges, int 
   if (e != cudaSuccess) { fn_status r = cuda_status(e, "create_system copy"); fn_destroy_system(s); return r; }
   st = upload_prep_descs(s);
   if (st != FN_OK) { fn_destroy_system(s); return st; }
+  if (cfg->precision == FN_BF16_MIXED && !tc_available()) {
+    set_error("the driver does not provide cuTensorMapEncodeTiled"); fn_destroy_system(s); return FN_ERR_UNSUPPORTED;
+  }
   *out = s;
   return FN_OK;
 }
@@ -377,7 +386,7 @@ fn_status fn_assign_electrons(fn_system_t s, const double* partial, int* counts_
 fn_status fn_init_params(fn_system_t s, uint64_t seed, void* d_params, void* stream) {
   if (!s || !d_params) { set_error("null argument"); return FN_ERR_ARG; }
   dispatch(s, [&](auto m) { launch_init_params<decltype(m)>(s, seed, d_params, (cudaStream_t)stream); return 0; });
-  return check_launch("init_params");
+  return check_launch(s, "init_params");
 }
 
 fn_status fn_init_walkers(fn_system_t s, int B, uint64_t seed, double init_std, const double* partial,
@@ -389,7 +398,7 @@ fn_status fn_init_walkers(fn_system_t s, int B, uint64_t seed, double init_std, 
   }
   if (counts_out) std::memcpy(counts_out, s->counts.data(), sizeof(int) * s->M);
   dispatch(s, [&](auto m) { launch_init_walkers<decltype(m)>(s, B, seed, init_std, d_walkers, (cudaStream_t)stream); return 0; });
-  return check_launch("init_walkers");
+  return check_launch(s, "init_walkers");
 }
 
 fn_status fn_log_psi(fn_system_t s, const void* d_params, const void* d_walkers, int B,
@@ -406,7 +415,7 @@ fn_status fn_log_psi(fn_system_t s, const void* d_params, const void* d_walkers,
     launch_det_energy<Mode>(s, d_walkers, sh, nullptr, d_log_psi, d_sign, false, cs);
     return 0;
   });
-  return check_launch("log_psi");
+  return check_launch(s, "log_psi");
 }
 
 fn_status fn_local_energy(fn_system_t s, const void* d_params, const void* d_walkers, int B,
@@ -423,7 +432,7 @@ fn_status fn_local_energy(fn_system_t s, const void* d_params, const void* d_wal
     launch_det_energy<Mode>(s, d_walkers, sh, d_e_local, d_log_psi, d_sign, false, cs);
     return 0;
   });
-  return check_launch("local_energy");
+  return check_launch(s, "local_energy");
 }
 
 fn_status fn_mcmc_steps(fn_system_t s, const void* d_params, void* d_walkers, double* d_log_psi, int B,
@@ -449,7 +458,7 @@ fn_status fn_mcmc_steps(fn_system_t s, const void* d_params, void* d_walkers, do
     }
     return 0;
   });
-  return check_launch("mcmc_steps");
+  return check_launch(s, "mcmc_steps");
 }
 
 fn_status fn_energy_grad(fn_system_t s, const void* d_params, const void* d_walkers, const double* d_e_local,
@@ -470,7 +479,7 @@ fn_status fn_energy_grad(fn_system_t s, const void* d_params, const void* d_walk
     launch_backward<Mode>(s, d_walkers, sh, s->ws.scratch_d, d_grad, cs);
     return 0;
   });
-  return check_launch("energy_grad");
+  return check_launch(s, "energy_grad");
 }
 
 fn_status fn_log_psi_vjp(fn_system_t s, const void* d_params, const void* d_walkers, const double* d_weights,
@@ -490,7 +499,7 @@ fn_status fn_log_psi_vjp(fn_system_t s, const void* d_params, const void* d_walk
     launch_backward<Mode>(s, d_walkers, sh, d_weights, d_grad, cs);
     return 0;
   });
-  return check_launch("log_psi_vjp");
+  return check_launch(s, "log_psi_vjp");
 }
 
 fn_status fn_profile_enable(fn_system_t s, int enable) {
@@ -531,7 +540,9 @@ fn_status fn_sync(fn_system_t s, void* stream, int timeout_ms) {
   if (word) {
     const int zero = 0;
     cudaMemcpy(s->ws.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
-    set_error(word & kStatusSingular ? "all determinants singular for some walker" : "non-finite result");
+    set_error(word & kStatusTimeout ? "a tensor-core kernel wait expired (timeout bit)"
+              : (word & kStatusSingular ? "all determinants singular for some walker" : "non-finite result"));
+    if (word & kStatusTimeout) return FN_ERR_TIMEOUT;
     return FN_ERR_NUMERIC;
   }
   return FN_OK;

@@ -34,248 +34,306 @@ struct DetArgs {
   int* status;
 };
 
-// LU with partial pivoting of the n x n row-major matrix A (in place) by one warp,
-// then C = A^{-1}.  Returns log|det| and sign (0 when a pivot is exactly zero).
+// One thread factorises one small matrix held in shared memory with element (i, j) at
+// A[(i n + j) ST] (ST = number of matrices interleaved, so neighbouring threads touch
+// neighbouring words).  Partial pivoting picks the first maximal |pivot|; the
+// determinant is tracked as mantissa * 2^exponent so that a single log per matrix is
+// needed; the pivot reciprocals are kept for the inverse.
 template <typename Det>
-__device__ void warp_lu_inverse(Det* A, Det* C, int n, Det* ld_out, Det* sign_out) {
-  const int lane = threadIdx.x & 31;
-  int perm = lane;
-  Det sgn = 1;
+__device__ void thread_lu(Det* A, int n, int ST, int* perm, Det* rcp, Det* ld_out, Det* sign_out) {
+  Det sgn = 1, mant = 1;
+  int expo = 0;
   bool singular = false;
+  for (int i = 0; i < n; ++i) perm[i * ST] = i;
   for (int c = 0; c < n; ++c) {
-    Det v = (lane >= c && lane < n) ? f_abs(A[lane * n + c]) : (Det)-1;
-    int idx = lane;
-    for (int off = 16; off > 0; off >>= 1) {
-      const Det ov = __shfl_down_sync(0xffffffffu, v, off);
-      const int oi = __shfl_down_sync(0xffffffffu, idx, off);
-      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    int piv = c;
+    Det best = f_abs(A[(c * n + c) * ST]);
+    for (int r = c + 1; r < n; ++r) {
+      const Det v = f_abs(A[(r * n + c) * ST]);
+      if (v > best) { best = v; piv = r; }
     }
-    const int piv = __shfl_sync(0xffffffffu, idx, 0);
-    const Det pv = __shfl_sync(0xffffffffu, v, 0);
-    if (!(pv > (Det)0)) { singular = true; break; }
+    if (!(best > (Det)0)) { singular = true; break; }
     if (piv != c) {
-      if (lane < n) {
-        const Det tmp = A[c * n + lane];
-        A[c * n + lane] = A[piv * n + lane];
-        A[piv * n + lane] = tmp;
+      for (int j = 0; j < n; ++j) {
+        const Det t = A[(c * n + j) * ST];
+        A[(c * n + j) * ST] = A[(piv * n + j) * ST];
+        A[(piv * n + j) * ST] = t;
       }
-      const int pc = __shfl_sync(0xffffffffu, perm, c);
-      const int pp = __shfl_sync(0xffffffffu, perm, piv);
-      if (lane == c) perm = pp;
-      if (lane == piv) perm = pc;
+      const int tp = perm[c * ST]; perm[c * ST] = perm[piv * ST]; perm[piv * ST] = tp;
       sgn = -sgn;
     }
-    __syncwarp();
-    if (lane > c && lane < n) {
-      const Det f = A[lane * n + c] / A[c * n + c];
-      A[lane * n + c] = f;
-      for (int j = c + 1; j < n; ++j) A[lane * n + j] -= f * A[c * n + j];
-    }
-    __syncwarp();
-  }
-  // log|det| = sum of log|pivot|; sign = permutation sign (warp-uniform) * pivot signs
-  Det ld = 0;
-  int neg = 0;
-  if (!singular && lane < n) {
-    const Det d = A[lane * n + lane];
-    ld = f_log(f_abs(d));
-    neg = d < 0 ? 1 : 0;
-  }
-  for (int off = 16; off > 0; off >>= 1) {
-    ld += __shfl_down_sync(0xffffffffu, ld, off);
-    neg += __shfl_down_sync(0xffffffffu, neg, off);
-  }
-  if (lane == 0) {
-    *ld_out = singular ? (Det)0 : ld;
-    *sign_out = singular ? (Det)0 : ((neg & 1) ? -sgn : sgn);
-  }
-  // inverse: lane j solves A x = e_j with P A = L U
-  for (int i = 0; i < n; ++i) {
-    const int pi = __shfl_sync(0xffffffffu, perm, i);
-    if (lane < n) {
-      if (singular) { C[i * n + lane] = 0; continue; }
-      Det y = (pi == lane) ? (Det)1 : (Det)0;
-      for (int k = 0; k < i; ++k) y -= A[i * n + k] * C[k * n + lane];
-      C[i * n + lane] = y;
+    const Det p = A[(c * n + c) * ST];
+    const Det rp = (Det)1 / p;
+    rcp[c * ST] = rp;
+    int e;
+    mant *= frexp(p, &e);
+    expo += e;
+    int e2;
+    mant = frexp(mant, &e2);
+    expo += e2;
+    for (int r = c + 1; r < n; ++r) {
+      const Det f = A[(r * n + c) * ST] * rp;
+      A[(r * n + c) * ST] = f;
+      for (int j = c + 1; j < n; ++j) A[(r * n + j) * ST] -= f * A[(c * n + j) * ST];
     }
   }
-  __syncwarp();
-  if (lane < n && !singular)
-    for (int i = n - 1; i >= 0; --i) {
-      Det x = C[i * n + lane];
-      for (int k = i + 1; k < n; ++k) x -= A[i * n + k] * C[k * n + lane];
-      C[i * n + lane] = x / A[i * n + i];
-    }
-  __syncwarp();
+  if (singular) {
+    *ld_out = 0;
+    *sign_out = 0;
+    return;
+  }
+  *sign_out = mant < 0 ? -sgn : sgn;
+  *ld_out = f_log(f_abs(mant)) + (Det)expo * (Det)0.6931471805599453;
 }
 
-template <typename Det, typename Wlk, bool FULL>
+// C = A^{-1} from the factors of thread_lu (same interleaving): column j of C solves
+// L U x = e_{perm^-1(j)}.
+template <typename Det>
+__device__ void thread_inverse(const Det* A, const int* perm, const Det* rcp, int n, int ST, Det* C) {
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < n; ++i) {
+      Det y = perm[i * ST] == j ? (Det)1 : (Det)0;
+      for (int k = 0; k < i; ++k) y -= A[(i * n + k) * ST] * C[(k * n + j) * ST];
+      C[(i * n + j) * ST] = y;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      Det x = C[(i * n + j) * ST];
+      for (int k = i + 1; k < n; ++k) x -= A[(i * n + k) * ST] * C[(k * n + j) * ST];
+      C[(i * n + j) * ST] = x * rcp[i * ST];
+    }
+  }
+}
+
+// Local-energy pass: one CTA per walker.  Threads 0..2K-1 factorise and invert the
+// (determinant, spin) blocks; then every thread takes (block, coordinate) items
+// g_t = tr(C d_t A), q_t = tr((C d_t A)^2) and tr(C lap A); then the determinant terms
+// are combined and E_L assembled.
+template <typename Det, typename Wlk>
 __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, const double* __restrict__ nuc,
                                                     Shape sh, DetArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int w = blockIdx.x;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int N = sh.N, T = sh.T, K = a.K, NC = 3 * N;
+  const int w = blockIdx.x, tid = threadIdx.x;
+  const int N = sh.N, T = sh.T, K = a.K, NC = 3 * N, NM = 2 * K;
+  const int ST = (int)round_up(NM, 32);
   const int ns[2] = {sh.n_up, sh.n_dn};
   const int nmax = max(ns[0], ns[1]);
-  Det* lu = (Det*)smem_raw;                  // [2][nmax^2]
-  Det* inv = lu + 2 * nmax * nmax;           // [2][nmax^2]
-  Det* ldk = inv + 2 * nmax * nmax;          // [K]
-  Det* sk = ldk + K;                         // [K]
-  Det* lapk = sk + K;                        // [K]
-  Det* rho = lapk + K;                       // [K]
-  Det* gradk = rho + K;                      // [K][NC]   (FULL)
-  Det* gt = gradk + (FULL ? K * NC : 0);     // [2][NC]
-  Det* qt = gt + (FULL ? 2 * NC : 0);        // [2][NC]
-  Det* misc = qt + (FULL ? 2 * NC : 0);      // [8]
-  Det* red = misc + 8;                       // [128]
+  Det* A = (Det*)smem_raw;                                // [nmax^2][ST]
+  Det* C = A + (int64_t)nmax * nmax * ST;                 // [nmax^2][ST]
+  Det* rcp = C + (int64_t)nmax * nmax * ST;               // [nmax][ST]
+  Det* ld2 = rcp + (int64_t)nmax * ST;                   // [NM]
+  Det* sg2 = ld2 + NM;                                   // [NM]
+  Det* gt = sg2 + NM;                                    // [NM][NC]
+  Det* qt = gt + NM * NC;                                // [NM][NC]
+  Det* lt = qt + NM * NC;                                // [NM]
+  Det* gradk = lt + NM;                                  // [K][NC]
+  Det* lapk = gradk + K * NC;                            // [K]
+  Det* rho = lapk + K;                                   // [K]
+  Det* red = rho + K;                                    // [128]
+  int* perm = (int*)(red + 128);                         // [nmax][ST]
   const Det* Phi = (const Det*)a.Phi + (int64_t)w * a.PW;
   const int64_t blk_off[2] = {0, (int64_t)K * T * ns[0] * ns[0]};
-  const int64_t inv_off[2] = {0, (int64_t)K * ns[0] * ns[0]};
-
-  for (int k = 0; k < K; ++k) {
-    for (int e = tid; e < ns[0] * ns[0] + ns[1] * ns[1]; e += blockDim.x) {
-      const int s = e < ns[0] * ns[0] ? 0 : 1;
-      const int idx = s ? e - ns[0] * ns[0] : e;
-      lu[s * nmax * nmax + idx] = Phi[blk_off[s] + (int64_t)k * T * ns[s] * ns[s] + idx];
+  // value slabs of every block, interleaved by block (thread 2k + spin)
+  for (int sp = 0; sp < 2; ++sp) {
+    const int nn = ns[sp] * ns[sp];
+    for (int e = tid; e < K * nn; e += blockDim.x) {
+      const int k = e / nn, idx = e % nn;
+      A[(int64_t)idx * ST + 2 * k + sp] = Phi[blk_off[sp] + (int64_t)k * T * nn + idx];
     }
-    __syncthreads();
-    if (warp < 2) {
-      if (ns[warp] > 0) {
-        warp_lu_inverse<Det>(lu + warp * nmax * nmax, inv + warp * nmax * nmax, ns[warp], misc + warp,
-                             misc + 2 + warp);
-      } else if ((tid & 31) == 0) {
-        misc[warp] = 0;
-        misc[2 + warp] = 1;
-      }
-    }
-    __syncthreads();
-    if (FULL) {
-      // items: (spin, t) for the 3N gradient slabs, then (spin) for the Laplacian slab
-      const int per = NC + 1;
-      for (int it = tid; it < 2 * per; it += blockDim.x) {
-        const int s = it / per, tr = it % per;
-        const int n = ns[s];
-        if (n == 0) {
-          if (tr < NC) { gt[s * NC + tr] = 0; qt[s * NC + tr] = 0; } else { misc[4 + s] = 0; }
-          continue;
-        }
-        const Det* Cm = inv + s * nmax * nmax;
-        const int t = tr < NC ? 1 + tr : T - 1;
-        const Det* D = Phi + blk_off[s] + (int64_t)k * T * n * n + (int64_t)t * n * n;
-        if (tr < NC) {
-          Det g = 0, q = 0;
-          for (int i = 0; i < n; ++i) {
-            for (int j = i; j < n; ++j) {
-              Det bij = 0;
-              for (int m = 0; m < n; ++m) bij += Cm[i * n + m] * D[m * n + j];
-              if (j == i) {
-                g += bij;
-                q += bij * bij;
-              } else {
-                Det bji = 0;
-                for (int m = 0; m < n; ++m) bji += Cm[j * n + m] * D[m * n + i];
-                q += (Det)2 * bij * bji;
-              }
-            }
-          }
-          gt[s * NC + tr] = g;
-          qt[s * NC + tr] = q;
-        } else {
-          Det l = 0;
-          for (int i = 0; i < n; ++i)
-            for (int j = 0; j < n; ++j) l += Cm[j * n + i] * D[i * n + j];
-          misc[4 + s] = l;
-        }
-      }
-      __syncthreads();
-      for (int t = tid; t < NC; t += blockDim.x) gradk[k * NC + t] = gt[t] + gt[NC + t];
-      if (warp == 0) {
-        Det qs = 0;
-        for (int t = tid; t < 2 * NC; t += 32) qs += qt[t];
-        for (int off = 16; off > 0; off >>= 1) qs += __shfl_down_sync(0xffffffffu, qs, off);
-        if (tid == 0) lapk[k] = misc[4] + misc[5] - qs;
-      }
-    }
-    if (tid == 0) {
-      ldk[k] = misc[0] + misc[1];
-      sk[k] = misc[2] * misc[3];
-    }
-    if (a.inv_out) {
-      Det* io = (Det*)a.inv_out + (int64_t)w * K * (ns[0] * ns[0] + ns[1] * ns[1]);
-      for (int e = tid; e < ns[0] * ns[0] + ns[1] * ns[1]; e += blockDim.x) {
-        const int s = e < ns[0] * ns[0] ? 0 : 1;
-        const int idx = s ? e - ns[0] * ns[0] : e;
-        const int n = ns[s], i = idx / n, j = idx % n;
-        io[inv_off[s] + (int64_t)k * n * n + idx] = inv[s * nmax * nmax + j * n + i];   // A^{-T}
-      }
-    }
-    __syncthreads();
   }
-  // signed log-sum-exp over determinants
+  __syncthreads();
+  if (tid < NM) {
+    const int n = ns[tid & 1];
+    if (n == 0) {
+      ld2[tid] = 0;
+      sg2[tid] = 1;
+    } else {
+      thread_lu<Det>(A + tid, n, ST, perm + tid, rcp + tid, ld2 + tid, sg2 + tid);
+      if (sg2[tid] != 0) thread_inverse<Det>(A + tid, perm + tid, rcp + tid, n, ST, C + tid);
+      else for (int e = 0; e < n * n; ++e) C[(int64_t)e * ST + tid] = 0;
+    }
+  }
+  __syncthreads();
+  // items: (block p, coordinate t < NC) and (block p, Laplacian)
+  const int per = NC + 1;
+  for (int it = tid; it < NM * per; it += blockDim.x) {
+    const int p = it / per, tr = it % per;
+    const int k = p >> 1, sp = p & 1, n = ns[sp];
+    if (n == 0) {
+      if (tr < NC) { gt[p * NC + tr] = 0; qt[p * NC + tr] = 0; } else { lt[p] = 0; }
+      continue;
+    }
+    const Det* Cm = C + p;
+    const int t = tr < NC ? 1 + tr : T - 1;
+    const Det* D = Phi + blk_off[sp] + (int64_t)k * T * n * n + (int64_t)t * n * n;
+    if (tr < NC) {
+      Det g = 0, q = 0;
+      for (int i = 0; i < n; ++i) {
+        for (int j = i; j < n; ++j) {
+          Det bij = 0;
+          for (int m = 0; m < n; ++m) bij += Cm[(int64_t)(i * n + m) * ST] * D[m * n + j];
+          if (j == i) {
+            g += bij;
+            q += bij * bij;
+          } else {
+            Det bji = 0;
+            for (int m = 0; m < n; ++m) bji += Cm[(int64_t)(j * n + m) * ST] * D[m * n + i];
+            q += (Det)2 * bij * bji;
+          }
+        }
+      }
+      gt[p * NC + tr] = g;
+      qt[p * NC + tr] = q;
+    } else {
+      Det l = 0;
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) l += Cm[(int64_t)(j * n + i) * ST] * D[i * n + j];
+      lt[p] = l;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < K * NC; e += blockDim.x) {
+    const int k = e / NC, t = e % NC;
+    gradk[e] = gt[(2 * k) * NC + t] + gt[(2 * k + 1) * NC + t];
+  }
+  for (int k = tid; k < K; k += blockDim.x) {
+    Det qs = 0;
+    for (int t = 0; t < NC; ++t) qs += qt[(2 * k) * NC + t] + qt[(2 * k + 1) * NC + t];
+    lapk[k] = lt[2 * k] + lt[2 * k + 1] - qs;
+  }
+  __syncthreads();
   if (tid == 0) {
     Det m = -INFINITY;
-    for (int k = 0; k < K; ++k)
-      if (sk[k] != 0 && ldk[k] > m) m = ldk[k];
+    for (int k = 0; k < K; ++k) {
+      const Det sk = sg2[2 * k] * sg2[2 * k + 1];
+      if (sk != 0 && ld2[2 * k] + ld2[2 * k + 1] > m) m = ld2[2 * k] + ld2[2 * k + 1];
+    }
     Det S = 0;
     for (int k = 0; k < K; ++k) {
-      rho[k] = sk[k] != 0 ? sk[k] * f_exp(ldk[k] - m) : (Det)0;
+      const Det sk = sg2[2 * k] * sg2[2 * k + 1];
+      rho[k] = sk != 0 ? sk * f_exp(ld2[2 * k] + ld2[2 * k + 1] - m) : (Det)0;
       S += rho[k];
     }
     for (int k = 0; k < K; ++k) rho[k] = S != 0 ? rho[k] / S : (Det)0;
-    misc[6] = m + f_log(f_abs(S));
-    misc[7] = S > 0 ? 1 : (S < 0 ? -1 : 0);
+    red[0] = m + f_log(f_abs(S));
+    red[1] = S > 0 ? 1 : (S < 0 ? -1 : 0);
   }
   __syncthreads();
-  const double lpsi = (double)misc[6];
-  const int sgn = (int)misc[7];
-  if (a.inv_out) {
-    Det* io = (Det*)a.inv_out + (int64_t)w * K * (ns[0] * ns[0] + ns[1] * ns[1]);
-    // scale each determinant's block by rho_k
-    for (int s = 0; s < 2; ++s) {
-      const int nn = ns[s] * ns[s];
-      for (int e = tid; e < K * nn; e += blockDim.x) io[inv_off[s] + e] *= rho[e / nn];
-    }
+  const double lpsi = (double)red[0];
+  const int sgn = (int)red[1];
+  __syncthreads();
+  // E_kin = -1/2 (|grad log psi|^2 + lap log psi) = -1/2 sum_k rho_k (lap_k + |g_k|^2)
+  Det kin = 0;
+  for (int k = tid; k < K; k += blockDim.x) {
+    Det g2 = 0;
+    for (int t = 0; t < NC; ++t) g2 += gradk[k * NC + t] * gradk[k * NC + t];
+    kin += rho[k] * (lapk[k] + g2);
   }
-  if (FULL) {
-    // E_kin = -1/2 (|grad log psi|^2 + lap log psi) = -1/2 sum_k rho_k (lap_k + |g_k|^2)
-    Det kin = 0;
-    for (int k = tid; k < K; k += blockDim.x) {
-      Det g2 = 0;
-      for (int t = 0; t < NC; ++t) g2 += gradk[k * NC + t] * gradk[k * NC + t];
-      kin += rho[k] * (lapk[k] + g2);
-    }
-    double pot = 0.0;
-    const Wlk* rw = r + (int64_t)w * N * 3;
-    for (int p = tid; p < N * N; p += blockDim.x) {
-      const int i = p / N, j = p % N;
-      if (j <= i) continue;
-      const double dx = (double)rw[3 * i] - (double)rw[3 * j], dy = (double)rw[3 * i + 1] - (double)rw[3 * j + 1],
-                   dz = (double)rw[3 * i + 2] - (double)rw[3 * j + 2];
-      pot += 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
-    }
-    for (int p = tid; p < N * sh.M; p += blockDim.x) {
-      const int i = p / sh.M, m = p % sh.M;
-      const double dx = (double)rw[3 * i] - nuc[3 * m], dy = (double)rw[3 * i + 1] - nuc[3 * m + 1],
-                   dz = (double)rw[3 * i + 2] - nuc[3 * m + 2];
-      pot -= a.charges[m] / sqrt(dx * dx + dy * dy + dz * dz);
-    }
-    red[tid] = (Det)(-0.5) * kin + (Det)pot;
+  double pot = 0.0;
+  const Wlk* rw = r + (int64_t)w * N * 3;
+  for (int p = tid; p < N * N; p += blockDim.x) {
+    const int i = p / N, j = p % N;
+    if (j <= i) continue;
+    const double dx = (double)rw[3 * i] - (double)rw[3 * j], dy = (double)rw[3 * i + 1] - (double)rw[3 * j + 1],
+                 dz = (double)rw[3 * i + 2] - (double)rw[3 * j + 2];
+    pot += 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  for (int p = tid; p < N * sh.M; p += blockDim.x) {
+    const int i = p / sh.M, m = p % sh.M;
+    const double dx = (double)rw[3 * i] - nuc[3 * m], dy = (double)rw[3 * i + 1] - nuc[3 * m + 1],
+                 dz = (double)rw[3 * i + 2] - nuc[3 * m + 2];
+    pot -= a.charges[m] / sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  red[tid] = (Det)(-0.5) * kin + (Det)pot;
+  __syncthreads();
+  for (int off = 64; off > 0; off >>= 1) {
+    if (tid < off) red[tid] += red[tid + off];
     __syncthreads();
-    for (int off = 64; off > 0; off >>= 1) {
-      if (tid < off) red[tid] += red[tid + off];
-      __syncthreads();
-    }
-    if (tid == 0) {
-      const double e = (double)red[0] + a.v_nn;
-      a.e_local[w] = e;
-      if (!isfinite(e) || !isfinite(lpsi)) atomicOr(a.status, kStatusNonFinite);
-    }
   }
   if (tid == 0) {
+    const double e = (double)red[0] + a.v_nn;
+    a.e_local[w] = e;
     if (a.log_psi) a.log_psi[w] = lpsi;
     if (a.sign) a.sign[w] = (int8_t)sgn;
     if (sgn == 0) atomicOr(a.status, kStatusSingular);
+    else if (!isfinite(e) || !isfinite(lpsi)) atomicOr(a.status, kStatusNonFinite);
+  }
+}
+
+// Value pass (log|psi|, plus the backward seed rho_k A^{-T} when requested): one CTA per
+// walker, one thread per (determinant, spin) block.
+template <typename Det>
+__global__ void k_det_value(Shape sh, DetArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = blockIdx.x, tid = threadIdx.x;
+  const int K = a.K, NM = 2 * K, ST = blockDim.x;
+  const int ns[2] = {sh.n_up, sh.n_dn};
+  const int nmax = max(ns[0], ns[1]);
+  const bool want_inv = a.inv_out != nullptr;
+  Det* A = (Det*)smem_raw;                                // [nmax^2][ST]
+  Det* C = A + (int64_t)nmax * nmax * ST;                 // [nmax^2][ST] (inverse)
+  Det* rcp = C + (want_inv ? (int64_t)nmax * nmax * ST : 0);   // [nmax][ST]
+  Det* ld2 = rcp + (int64_t)nmax * ST;                   // [NM]
+  Det* sg2 = ld2 + NM;
+  Det* rho = sg2 + NM;                                   // [K]
+  int* perm = (int*)(rho + K);                           // [nmax][ST]
+  const Det* Phi = (const Det*)a.Phi + (int64_t)w * a.PW;
+  const int64_t blk_off[2] = {0, (int64_t)K * ns[0] * ns[0]};
+  const int64_t per = (int64_t)K * (ns[0] * ns[0] + ns[1] * ns[1]);
+  Det* io = want_inv ? (Det*)a.inv_out + (int64_t)w * per : nullptr;
+  // coalesced staging: block (k, spin) -> thread 2k + spin
+  for (int e = tid; e < per; e += blockDim.x) {
+    const int sp = e < blk_off[1] ? 0 : 1;
+    const int n = ns[sp];
+    const int64_t q = e - blk_off[sp];
+    const int k = (int)(q / (n * n)), idx = (int)(q % (n * n));
+    A[(int64_t)idx * ST + 2 * k + sp] = Phi[e];
+  }
+  __syncthreads();
+  if (tid < NM) {
+    const int k = tid >> 1, sp = tid & 1, n = ns[sp];
+    if (n == 0) {
+      ld2[tid] = 0;
+      sg2[tid] = 1;
+    } else {
+      thread_lu<Det>(A + tid, n, ST, perm + tid, rcp + tid, ld2 + tid, sg2 + tid);
+      if (want_inv) {
+        if (sg2[tid] != 0) thread_inverse<Det>(A + tid, perm + tid, rcp + tid, n, ST, C + tid);
+        else for (int e = 0; e < n * n; ++e) C[(int64_t)e * ST + tid] = 0;
+      }
+    }
+    (void)k;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    Det m = -INFINITY;
+    for (int k = 0; k < K; ++k) {
+      const Det sk = sg2[2 * k] * sg2[2 * k + 1];
+      if (sk != 0 && ld2[2 * k] + ld2[2 * k + 1] > m) m = ld2[2 * k] + ld2[2 * k + 1];
+    }
+    Det S = 0;
+    for (int k = 0; k < K; ++k) {
+      const Det sk = sg2[2 * k] * sg2[2 * k + 1];
+      rho[k] = sk != 0 ? sk * f_exp(ld2[2 * k] + ld2[2 * k + 1] - m) : (Det)0;
+      S += rho[k];
+    }
+    for (int k = 0; k < K; ++k) rho[k] = S != 0 ? rho[k] / S : (Det)0;
+    const double lpsi = (double)(m + f_log(f_abs(S)));
+    const int sgn = S > 0 ? 1 : (S < 0 ? -1 : 0);
+    if (a.log_psi) a.log_psi[w] = lpsi;
+    if (a.sign) a.sign[w] = (int8_t)sgn;
+    if (sgn == 0) atomicOr(a.status, kStatusSingular);
+    else if (!isfinite(lpsi)) atomicOr(a.status, kStatusNonFinite);
+  }
+  if (want_inv) {
+    __syncthreads();
+    for (int e = tid; e < per; e += blockDim.x) {
+      const int sp = e < blk_off[1] ? 0 : 1;
+      const int n = ns[sp];
+      const int64_t q = e - blk_off[sp];
+      const int k = (int)(q / (n * n)), idx = (int)(q % (n * n));
+      const int i = idx / n, j = idx % n;
+      io[e] = rho[k] * C[(int64_t)(j * n + i) * ST + 2 * k + sp];        // rho_k A^{-T}
+    }
   }
 }
 
@@ -296,14 +354,20 @@ void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh,
   a.status = s->ws.status;
   const bool full = sh.T > 1 && e_local != nullptr;
   const int nmax = std::max(s->n_up, s->n_dn), NC = 3 * s->N, K = s->cfg.n_dets;
-  const size_t smem = sizeof(Det) * (4 * nmax * nmax + 4 * K + (full ? K * NC + 4 * NC : 0) + 8 + 128);
   ProfScope ps(s->prof, full ? kProfDetFull : kProfDetValue, st);
   if (full) {
-    cudaFuncSetAttribute(k_det_energy<Det, Wlk, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_det_energy<Det, Wlk, true><<<sh.B, 128, smem, st>>>((const Wlk*)walkers, s->d_nuclei, sh, a);
+    const int ST = (int)round_up(2 * K, 32);
+    const size_t smem = sizeof(Det) * ((size_t)2 * nmax * nmax * ST + (size_t)nmax * ST + 4 * K + 4 * K * NC +
+                                       2 * K + K * NC + 2 * K + 128) + sizeof(int) * (size_t)nmax * ST;
+    cudaFuncSetAttribute(k_det_energy<Det, Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_det_energy<Det, Wlk><<<sh.B, 128, smem, st>>>((const Wlk*)walkers, s->d_nuclei, sh, a);
   } else {
-    cudaFuncSetAttribute(k_det_energy<Det, Wlk, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_det_energy<Det, Wlk, false><<<sh.B, 128, smem, st>>>((const Wlk*)walkers, s->d_nuclei, sh, a);
+    const int threads = (int)round_up(2 * K, 32);
+    const bool inv = keep_inverse;
+    const size_t vsmem = sizeof(Det) * ((size_t)(inv ? 2 : 1) * nmax * nmax * threads + (size_t)nmax * threads +
+                                        5 * K) + sizeof(int) * (size_t)nmax * threads;
+    cudaFuncSetAttribute(k_det_value<Det>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem);
+    k_det_value<Det><<<sh.B, threads, vsmem, st>>>(sh, a);
   }
 }
 

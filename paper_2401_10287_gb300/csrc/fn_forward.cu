@@ -165,7 +165,18 @@ __global__ void k_features_mean(const Wlk* __restrict__ r, const double* __restr
 }
 
 // ---------------------------------------------------------------------------------------
-// two-electron stream: one warp per (walker, electron i), lane = channel
+// two-electron stream.  A pair (i, j) depends only on r_i and r_j, so its jet has 8 rows:
+// value, d/dr_i (3), d/dr_j (3), Laplacian.  Pairs never interact across layers, so a
+// thread carries its pair (and, in the full pass, one jet row) through every layer; the
+// channels live in registers and the layer weights, transposed, in shared memory
+// (every thread reads the same weight at the same time: broadcast).
+//   full pass : one CTA per (walker, electron i), 8 threads per partner j (one per jet
+//               row); the value row's tanh and the tangent rows' sum of squares are
+//               exchanged with shuffles inside the 8-lane group;
+//   value pass: one CTA per walker, one thread per pair.
+// The spin means over j are accumulated with shared-memory atomics and written to the
+// mean-g columns of every layer's input X_l; the derivative of mean_j g_ij along r_j
+// (j != i) is (1/n_spin) d g_ij / d r_j, written directly.
 // ---------------------------------------------------------------------------------------
 struct PairArgs {
   void* X[kMaxLayers];
@@ -178,120 +189,183 @@ struct PairArgs {
   int L, h2;
 };
 
-template <typename Act, typename Cmp, typename Wlk, bool FULL>
-__global__ void k_pair_stream(const Wlk* __restrict__ r, Shape sh, PairArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (gw >= (int64_t)sh.B * sh.N) return;
-  const int w = (int)(gw / sh.N), i = (int)(gw % sh.N);
-  const int64_t row = tile_row(w, i, sh.N, sh.wpt);
-  const Wlk* rw = r + (int64_t)w * sh.N * 3;
-  const double ri[3] = {(double)rw[3 * i], (double)rw[3 * i + 1], (double)rw[3 * i + 2]};
-  const int nsp[2] = {sh.n_up, sh.n_dn};
-  // per layer, per spin: sums of value, Laplacian and derivatives along r_i
-  Cmp acc_v[kMaxLayers][2], acc_l[kMaxLayers][2], acc_d[kMaxLayers][2][3];
-  for (int l = 0; l < a.L; ++l)
-    for (int s = 0; s < 2; ++s) {
-      acc_v[l][s] = acc_l[l][s] = 0;
-      acc_d[l][s][0] = acc_d[l][s][1] = acc_d[l][s][2] = 0;
+constexpr int kMaxH2 = 32;
+
+// Stage W_l^T [d_g][h2] and c_l of every pair layer in shared memory.
+template <typename Cmp>
+__device__ void stage_pair_weights(const PairArgs& a, Cmp* sW, Cmp* sc) {
+  for (int l = 0; l + 1 < a.L; ++l) {
+    const Cmp* W = (const Cmp*)a.W[l];
+    const int dg = a.d_g[l];
+    for (int e = threadIdx.x; e < kMaxH2 * kMaxH2; e += blockDim.x) {
+      const int k = e / kMaxH2, c = e % kMaxH2;
+      sW[l * kMaxH2 * kMaxH2 + e] = (k < dg && c < a.h2) ? W[c * dg + k] : (Cmp)0;
     }
-  for (int j = 0; j < sh.N; ++j) {
-    const int sj = j < sh.n_up ? 0 : 1;
-    const Cmp inv_n = (Cmp)1 / (Cmp)nsp[sj];
-    // jets of g^0_ij in lanes 0..3: v, d/dr_i (3), d/dr_j (3), Laplacian
-    Cmp v = 0, di[3] = {0, 0, 0}, dj[3] = {0, 0, 0}, lp = 0;
-    if (j != i) {
-      const double d[3] = {ri[0] - (double)rw[3 * j], ri[1] - (double)rw[3 * j + 1], ri[2] - (double)rw[3 * j + 2]};
-      const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-      if (lane < 3) {
-        v = (Cmp)d[lane];
-        di[lane] = (Cmp)1;
-        dj[lane] = (Cmp)-1;
-      } else if (lane == 3) {
-        v = (Cmp)dist;
-        for (int c = 0; c < 3; ++c) { di[c] = (Cmp)(d[c] / dist); dj[c] = -di[c]; }
-        lp = (Cmp)(4.0 / dist);
+    for (int c = threadIdx.x; c < kMaxH2; c += blockDim.x) sc[l * kMaxH2 + c] = c < a.h2 ? ((const Cmp*)a.c[l])[c] : (Cmp)0;
+  }
+}
+
+// z[c] = sum_k W^T[k][c] g[k] (+ bias)
+template <typename Cmp>
+__device__ __forceinline__ void pair_matvec(const Cmp* __restrict__ sWl, const Cmp* __restrict__ scl, bool bias,
+                                            int dg, const Cmp (&g)[kMaxH2], Cmp (&z)[kMaxH2]) {
+#pragma unroll
+  for (int c = 0; c < kMaxH2; ++c) z[c] = bias ? scl[c] : (Cmp)0;
+#pragma unroll 4
+  for (int k = 0; k < dg; ++k) {
+    const Cmp gk = g[k];
+    const Cmp* row = sWl + k * kMaxH2;
+#pragma unroll
+    for (int c = 0; c < kMaxH2; ++c) z[c] += row[c] * gk;
+  }
+}
+
+template <typename Act, typename Cmp, typename Wlk>
+__global__ void __launch_bounds__(256) k_pair_full(const Wlk* __restrict__ r, Shape sh, PairArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cmp* sW = (Cmp*)smem_raw;                                  // [L-1][32][32]
+  Cmp* sc = sW + (kMaxLayers - 1) * kMaxH2 * kMaxH2;        // [L-1][32]
+  Cmp* acc = sc + (kMaxLayers - 1) * kMaxH2;                 // [L][2][5][32]: value, Laplacian, d/dr_i
+  const int w = blockIdx.x / sh.N, i = blockIdx.x % sh.N;
+  const int j = threadIdx.x >> 3, rr = threadIdx.x & 7;      // partner, jet row
+  const unsigned gmask = 0xFFu << (threadIdx.x & 24);        // the 8 lanes of this pair
+  stage_pair_weights(a, sW, sc);
+  for (int e = threadIdx.x; e < a.L * 2 * 5 * kMaxH2; e += blockDim.x) acc[e] = (Cmp)0;
+  __syncthreads();
+  const int64_t row = tile_row(w, i, sh.N, sh.wpt);
+  const bool live = j < sh.N;
+  const int sj = j < sh.n_up ? 0 : 1;
+  const int nsj = sj ? sh.n_dn : sh.n_up;
+  const Cmp inv_n = (Cmp)1 / (Cmp)(nsj > 0 ? nsj : 1);
+  // input features of the pair: jet row rr of (r_i - r_j, |r_i - r_j|)
+  Cmp g[kMaxH2];
+#pragma unroll
+  for (int c = 0; c < kMaxH2; ++c) g[c] = 0;
+  if (live && j != i) {
+    const Wlk* rw = r + (int64_t)w * sh.N * 3;
+    double d[3];
+    for (int c = 0; c < 3; ++c) d[c] = (double)rw[3 * i + c] - (double)rw[3 * j + c];
+    const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (rr == 0) {
+      g[0] = (Cmp)d[0]; g[1] = (Cmp)d[1]; g[2] = (Cmp)d[2]; g[3] = (Cmp)dist;
+    } else if (rr < 7) {
+      const int c = (rr - 1) % 3;
+      const Cmp sgn = rr < 4 ? (Cmp)1 : (Cmp)-1;            // d/dr_i or d/dr_j
+      g[c] = sgn;
+      g[3] = sgn * (Cmp)(d[c] / dist);
+    } else {
+      g[3] = (Cmp)(4.0 / dist);
+    }
+  }
+  for (int l = 0; l < a.L; ++l) {
+    const int dg = a.d_g[l];
+    if (live) {
+      Cmp* al = acc + (l * 2 + sj) * 5 * kMaxH2;
+      const int slot = rr == 0 ? 0 : (rr == 7 ? 1 : (rr < 4 ? 1 + rr : -1));
+      if (slot >= 0) {
+#pragma unroll
+        for (int c = 0; c < kMaxH2; ++c)
+          if (c < dg) atomicAdd(al + slot * kMaxH2 + c, g[c]);
+      } else if (j != i) {                                     // d/dr_j row: its own slab
+        const int c3 = rr - 4;
+        Act* X = (Act*)a.X[l];
+        Act* o = X + (1 + 3 * j + c3) * sh.R * a.ldx[l] + row * a.ldx[l] + a.col0[l];
+#pragma unroll
+        for (int c = 0; c < kMaxH2; ++c)
+          if (c < dg) {
+            st(o + sj * dg + c, g[c] * inv_n);
+            st(o + (1 - sj) * dg + c, (Cmp)0);
+          }
       }
+    }
+    if (l == a.L - 1) break;
+    Cmp z[kMaxH2];
+    pair_matvec(sW + l * kMaxH2 * kMaxH2, sc + l * kMaxH2, rr == 0, dg, g, z);
+    // tanh jets: h from the value row, sum of squares of the 6 tangent rows
+    const int base = threadIdx.x & ~7;
+#pragma unroll
+    for (int c = 0; c < kMaxH2; ++c) {
+      const Cmp zv = __shfl_sync(0xffffffffu, z[c], base, 32);
+      const Cmp h = f_tanh(zv);
+      const Cmp dh = (Cmp)1 - h * h;
+      Cmp sq = (rr >= 1 && rr <= 6) ? z[c] * z[c] : (Cmp)0;
+      sq += __shfl_xor_sync(0xffffffffu, sq, 1);
+      sq += __shfl_xor_sync(0xffffffffu, sq, 2);
+      sq += __shfl_xor_sync(0xffffffffu, sq, 4);
+      Cmp out = rr == 0 ? h : (rr == 7 ? dh * z[c] - (Cmp)2 * h * dh * sq : dh * z[c]);
+      if (c >= a.h2) out = 0;
+      g[c] = (l > 0 ? g[c] : (Cmp)0) + out;
+    }
+    (void)gmask;
+  }
+  __syncthreads();
+  // sums over j: value (slab 0), Laplacian (slab T-1), d/dr_i (slabs 1 + 3i + c)
+  for (int l = 0; l < a.L; ++l) {
+    const int dg = a.d_g[l];
+    Act* X = (Act*)a.X[l];
+    const int64_t slab = sh.R * a.ldx[l];
+    for (int e = threadIdx.x; e < 2 * 5 * dg; e += blockDim.x) {
+      const int s = e / (5 * dg), q = (e / dg) % 5, c = e % dg;
+      const int ns = s ? sh.n_dn : sh.n_up;
+      const Cmp v = ns ? acc[((l * 2 + s) * 5 + q) * kMaxH2 + c] / (Cmp)ns : (Cmp)0;
+      const int t = q == 0 ? 0 : (q == 1 ? sh.T - 1 : 1 + 3 * i + (q - 2));
+      st(X + t * slab + row * a.ldx[l] + a.col0[l] + s * dg + c, v);
+    }
+  }
+}
+
+template <typename Act, typename Cmp, typename Wlk>
+__global__ void __launch_bounds__(256) k_pair_value(const Wlk* __restrict__ r, Shape sh, PairArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cmp* sW = (Cmp*)smem_raw;
+  Cmp* sc = sW + (kMaxLayers - 1) * kMaxH2 * kMaxH2;
+  Cmp* acc = sc + (kMaxLayers - 1) * kMaxH2;                 // [L][N][2][32]
+  const int w = blockIdx.x;
+  stage_pair_weights(a, sW, sc);
+  for (int e = threadIdx.x; e < a.L * sh.N * 2 * kMaxH2; e += blockDim.x) acc[e] = (Cmp)0;
+  __syncthreads();
+  const Wlk* rw = r + (int64_t)w * sh.N * 3;
+  for (int p = threadIdx.x; p < sh.N * sh.N; p += blockDim.x) {
+    const int i = p / sh.N, j = p % sh.N;
+    const int sj = j < sh.n_up ? 0 : 1;
+    Cmp g[kMaxH2];
+#pragma unroll
+    for (int c = 0; c < kMaxH2; ++c) g[c] = 0;
+    if (j != i) {
+      double d[3];
+      for (int c = 0; c < 3; ++c) d[c] = (double)rw[3 * i + c] - (double)rw[3 * j + c];
+      g[0] = (Cmp)d[0]; g[1] = (Cmp)d[1]; g[2] = (Cmp)d[2];
+      g[3] = (Cmp)sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     }
     for (int l = 0; l < a.L; ++l) {
       const int dg = a.d_g[l];
-      if (lane < dg) {
-        acc_v[l][sj] += v;
-        acc_l[l][sj] += lp;
-        for (int c = 0; c < 3; ++c) acc_d[l][sj][c] += di[c];
-        if (FULL && j != i) {
-          Act* X = (Act*)a.X[l];
-          const int64_t slab = sh.R * a.ldx[l];
-          for (int c = 0; c < 3; ++c) {
-            Act* o = X + (1 + 3 * j + c) * slab + row * a.ldx[l] + a.col0[l];
-            st(o + sj * dg + lane, dj[c] * inv_n);
-            st(o + (1 - sj) * dg + lane, (Cmp)0);
-          }
-        }
-      }
+      Cmp* al = acc + ((l * sh.N + i) * 2 + sj) * kMaxH2;
+#pragma unroll
+      for (int c = 0; c < kMaxH2; ++c)
+        if (c < dg) atomicAdd(al + c, g[c]);
       if (l == a.L - 1) break;
-      // pair layer l: g <- tanh(W g + c) (+ g for l >= 1)
-      const Cmp* W = (const Cmp*)a.W[l];
-      const Cmp* cb = (const Cmp*)a.c[l];
-      const int h2 = a.h2;
-      Cmp zv = lane < h2 ? cb[lane] : (Cmp)0, zi[3] = {0, 0, 0}, zj[3] = {0, 0, 0}, zl = 0;
-      for (int k = 0; k < dg; ++k) {
-        const Cmp wk = lane < h2 ? W[lane * dg + k] : (Cmp)0;
-        zv += wk * __shfl_sync(0xffffffffu, v, k);
-        if (FULL) {
-          for (int c = 0; c < 3; ++c) {
-            zi[c] += wk * __shfl_sync(0xffffffffu, di[c], k);
-            zj[c] += wk * __shfl_sync(0xffffffffu, dj[c], k);
-          }
-          zl += wk * __shfl_sync(0xffffffffu, lp, k);
-        }
+      Cmp z[kMaxH2];
+      pair_matvec(sW + l * kMaxH2 * kMaxH2, sc + l * kMaxH2, true, dg, g, z);
+#pragma unroll
+      for (int c = 0; c < kMaxH2; ++c) g[c] = (l > 0 ? g[c] : (Cmp)0) + (c < a.h2 ? f_tanh(z[c]) : (Cmp)0);
+      if (a.gstore[l + 1]) {
+        Cmp* gs = (Cmp*)a.gstore[l + 1] + (((int64_t)w * sh.N + i) * sh.N + j) * a.h2;
+#pragma unroll
+        for (int c = 0; c < kMaxH2; ++c)
+          if (c < a.h2) gs[c] = g[c];
       }
-      const Cmp h = f_tanh(zv);
-      const Cmp dh = (Cmp)1 - h * h;
-      Cmp nv = h, ni[3], nj[3], nl = 0;
-      if (FULL) {
-        Cmp sq = 0;
-        for (int c = 0; c < 3; ++c) {
-          ni[c] = dh * zi[c];
-          nj[c] = dh * zj[c];
-          sq += zi[c] * zi[c] + zj[c] * zj[c];
-        }
-        nl = dh * zl - (Cmp)2 * h * dh * sq;
-      }
-      if (l > 0) {
-        nv += v;
-        if (FULL) {
-          for (int c = 0; c < 3; ++c) { ni[c] += di[c]; nj[c] += dj[c]; }
-          nl += lp;
-        }
-      }
-      if (lane >= h2) { nv = 0; nl = 0; }
-      v = nv;
-      if (FULL) {
-        for (int c = 0; c < 3; ++c) {
-          di[c] = lane < h2 ? ni[c] : (Cmp)0;
-          dj[c] = lane < h2 ? nj[c] : (Cmp)0;
-        }
-        lp = nl;
-      }
-      if (a.gstore[l + 1] && lane < h2)
-        ((Cmp*)a.gstore[l + 1])[(((int64_t)w * sh.N + i) * sh.N + j) * h2 + lane] = v;
     }
   }
-  // slabs accumulated over j: value, Laplacian, derivatives along r_i
+  __syncthreads();
   for (int l = 0; l < a.L; ++l) {
     const int dg = a.d_g[l];
-    if (lane >= dg) continue;
     Act* X = (Act*)a.X[l];
-    const int64_t slab = sh.R * a.ldx[l];
-    Act* base = X + row * a.ldx[l] + a.col0[l] + lane;
-    for (int s = 0; s < 2; ++s) {
-      const Cmp inv_n = nsp[s] ? (Cmp)1 / (Cmp)nsp[s] : (Cmp)0;
-      st(base + s * dg, acc_v[l][s] * inv_n);
-      if (FULL) {
-        st(base + (sh.T - 1) * slab + s * dg, acc_l[l][s] * inv_n);
-        for (int c = 0; c < 3; ++c) st(base + (1 + 3 * i + c) * slab + s * dg, acc_d[l][s][c] * inv_n);
-      }
+    for (int e = threadIdx.x; e < sh.N * 2 * dg; e += blockDim.x) {
+      const int i = e / (2 * dg), s = (e / dg) % 2, c = e % dg;
+      const int ns = s ? sh.n_dn : sh.n_up;
+      const int64_t row = tile_row(w, i, sh.N, sh.wpt);
+      const Cmp v = ns ? acc[((l * sh.N + i) * 2 + s) * kMaxH2 + c] / (Cmp)ns : (Cmp)0;
+      st(X + row * a.ldx[l] + a.col0[l] + s * dg + c, v);
     }
   }
 }
@@ -534,11 +608,19 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
       if (l < L - 1) { pa.W[l] = prep + s->prep.W[l]; pa.c[l] = prep + s->prep.c[l]; }
       pa.gstore[l] = (keep && l >= 1) ? ws.gpair[l] : nullptr;
     }
-    const int64_t threads = (int64_t)sh.B * sh.N * 32;
-    const unsigned blocks = (unsigned)((threads + 127) / 128);
+    const size_t wbytes = sizeof(Cmp) * ((kMaxLayers - 1) * kMaxH2 * kMaxH2 + (kMaxLayers - 1) * kMaxH2);
     ProfScope ps(s->prof, kProfPair, st);
-    if (full) k_pair_stream<Act, Cmp, Wlk, true><<<blocks, 128, 0, st>>>(r, sh, pa);
-    else k_pair_stream<Act, Cmp, Wlk, false><<<blocks, 128, 0, st>>>(r, sh, pa);
+    if (full) {
+      const size_t smem = wbytes + sizeof(Cmp) * L * 2 * 5 * kMaxH2;
+      const int threads = (int)round_up(8 * sh.N, 32);
+      cudaFuncSetAttribute(k_pair_full<Act, Cmp, Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_pair_full<Act, Cmp, Wlk><<<(unsigned)((int64_t)sh.B * sh.N), threads, smem, st>>>(r, sh, pa);
+    } else {
+      const size_t smem = wbytes + sizeof(Cmp) * L * sh.N * 2 * kMaxH2;
+      const int threads = (int)std::min<int64_t>(256, round_up((int64_t)sh.N * sh.N, 32));
+      cudaFuncSetAttribute(k_pair_value<Act, Cmp, Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_pair_value<Act, Cmp, Wlk><<<(unsigned)sh.B, threads, smem, st>>>(r, sh, pa);
+    }
   }
   for (int l = 0; l < L; ++l) {
     const LayerDims& d = s->layer[l];
@@ -560,9 +642,16 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     la.Hbar_out = last ? nullptr : ws.Hbar[l + 1];
     la.act_out = keep ? ws.act[l] : nullptr;
     la.h1 = h1;
+    ProfScope ps(s->prof, full ? kProfLayerFull : kProfLayerValue, st);
+    if (Mode::kMode == FN_BF16_MIXED) {
+      const __nv_bfloat16* Vs16 = (const __nv_bfloat16*)ws.prep16 + s->prep.Vs16[l];
+      if (!launch_layer_tc(sh, la.X, la.ldx, la.k_self, Vs16, (const float*)la.Mterm, la.Y, la.ldy, la.residual,
+                           (float*)la.Hbar_out, (float*)la.act_out, h1, ws.status, st))
+        const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
+      continue;
+    }
     const size_t smem = sizeof(Cmp) * (32 * 132 + 32 * 64 + 128 * 65);
     dim3 grid(sh.tiles, (h1 + 63) / 64);
-    ProfScope ps(s->prof, full ? kProfLayerFull : kProfLayerValue, st);
     if (full) {
       cudaFuncSetAttribute(k_layer<Act, Cmp, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_layer<Act, Cmp, true><<<grid, 256, smem, st>>>(sh, la);

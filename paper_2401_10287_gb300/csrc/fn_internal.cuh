@@ -40,6 +40,7 @@ constexpr int kMaxNuclei = 16;
 // Status bits written by kernels into the device status word.
 constexpr int kStatusNonFinite = 1;
 constexpr int kStatusSingular = 2;
+constexpr int kStatusTimeout = 4;
 
 // ---- precision traits ------------------------------------------------------------
 // Act: storage of stream activations; Cmp: elementwise arithmetic; Det: determinant
@@ -157,6 +158,7 @@ struct fn_system {
   void* d_descs = nullptr;       // parameter-preparation copy descriptors
   int n_descs = 0;
   fn::Profiler* prof = nullptr;  // kernel-class timing (fn_profile_enable)
+  fn_status host_error = FN_OK;  // set by a launcher that could not enqueue its kernel
 };
 
 namespace fn {
@@ -165,6 +167,11 @@ void set_error(const std::string& msg);
 fn_status cuda_status(cudaError_t e, const char* what);
 
 fn_status upload_prep_descs(fn_system* s);
+
+// Tensor-core one-electron layer (BF16 mode); false if a TMA tensor map could not be built.
+bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const void* Vs16, const float* Mterm, void* Y,
+                     int ldy, int residual, float* Hbar_out, float* act_out, int h1, int* status, cudaStream_t st);
+bool tc_available();
 
 // Shapes and sizes
 Shape make_shape(const fn_system* s, int B, int T);

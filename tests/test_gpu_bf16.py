@@ -1,0 +1,74 @@
+"""BF16-mixed mode (tcgen05 tensor-core stream layers, FP64 determinants) against the FP64 oracle.
+
+The BF16 mode stores stream activations in BF16 (8 significant bits), so its error is
+not a rounding-order difference: the tests bound it loosely per walker and report the
+mean-energy error, the quantity the precision mode is judged by."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import ansatz, mcmc
+from gpu_helpers import make_pair, need_gpu, oracle_params, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+    yield
+    torch.cuda.synchronize()
+
+
+def _run(sysm, ans, B, seed=0, std=1.0, perturb=0.0, burn_in=150, step=0.3):
+    """Walkers equilibrated on |psi|^2 by the oracle's own Metropolis chain (FP64), so that
+    they are distributed like the walkers a VMC run evaluates."""
+    net, gpu = make_pair(sysm, ans, 2)
+    p = oracle_params(net, seed, perturb).astype(np.float32).astype(np.float64)
+    r, _ = mcmc.init_walkers(sysm.nuclei, sysm.charges, sysm.n_up, sysm.n_down, sysm.partial_charges, B, seed + 1,
+                             std)
+    lp0, _ = ansatz.log_psi(net, p, sysm.nuclei, r)
+    r, _, _ = mcmc.metropolis(net, p, sysm.nuclei, r, lp0, seed + 2, burn_in, step)
+    r = r.astype(np.float32)
+    e, lp, sg = gpu.local_energy(to_dev(p, torch.float32), to_dev(r, torch.float32))
+    gpu.sync()
+    r64 = r.astype(np.float64)
+    e_ref, lp_ref, _ = ansatz.local_energy(net, p, sysm.nuclei, sysm.charges, r64)
+    _, _, grad, lap = ansatz.log_psi_derivatives(net, p, sysm.nuclei, r64)
+    scale = np.maximum(np.maximum(1.0, np.abs(e_ref)), 0.5 * (np.sum(grad * grad, -1) + np.abs(lap)))
+    return e.cpu().numpy(), lp.cpu().numpy(), e_ref, lp_ref, scale
+
+
+@pytest.mark.parametrize("name,make,ans,B", [
+    ("H2", W.h2, W.Ansatz(2, 32, 8, 1, "iso"), 256),
+    ("LiH+", lambda: W.lih(1), W.Ansatz(4, 128, 16, 8, "aniso"), 130),
+    ("N2", W.n2, W.Ansatz(4, 256, 32, 16, "aniso"), 40),
+])
+def test_bf16_local_energy_against_oracle(name, make, ans, B):
+    e, lp, e_ref, lp_ref, scale = _run(make(), ans, B)
+    rel = np.abs(e - e_ref) / scale
+    mean_err = abs(e.mean() - e_ref.mean())
+    worst = int(np.argmax(rel))
+    print(f"{name}: median rel {np.median(rel):.2e} max rel {rel.max():.2e} (E_ref {e_ref[worst]:.3f}, scale "
+          f"{scale[worst]:.1f}) mean-energy error {mean_err * 1e3:.3f} mHa of {e_ref.mean():.4f} Ha;"
+          f" |d log psi| median {np.median(np.abs(lp - lp_ref)):.2e} max {np.abs(lp - lp_ref).max():.2e}")
+    assert np.all(np.isfinite(e))
+    assert np.median(rel) < 1e-2
+
+
+def test_bf16_mcmc_and_grad_run():
+    sysm = W.lih(-1)
+    net, gpu = make_pair(sysm, W.Ansatz(4, 128, 16, 8, "aniso"), 2)
+    params = gpu.init_params(4)
+    walkers, counts = gpu.init_walkers(512, 4, 0.5)
+    assert counts == [4, 1]
+    lp, _ = gpu.log_psi(params, walkers)
+    acc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    gpu.mcmc_steps(params, walkers, lp, 5, 0.05, seed=1, accept_count=acc)
+    e, lp2, _ = gpu.local_energy(params, walkers)
+    g, mean = gpu.energy_grad(params, walkers, e)
+    gpu.sync()
+    assert 0 < acc.item() <= 5 * 512
+    assert torch.isfinite(e).all() and torch.isfinite(g).all()
+    assert (lp - lp2).abs().max().item() < 5e-2 * max(1.0, lp.abs().max().item())
