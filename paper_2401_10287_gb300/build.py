@@ -64,7 +64,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         raise RuntimeError("nvcc failed for " + ", ".join(errors))
     objs = [os.path.join(BUILD, os.path.basename(s) + ".o") for s in _sources()]
     if jobs or not os.path.exists(LIB):
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-lcuda"]
+        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("link failed:\n" + res.stdout + res.stderr)
