@@ -168,6 +168,20 @@ fn_status fn_energy_grad(fn_system_t sys, const void* d_params, const void* d_wa
 fn_status fn_log_psi_vjp(fn_system_t sys, const void* d_params, const void* d_walkers,
                          const double* d_weights, int n_walkers, void* d_grad, void* stream);
 
+/* log|psi| and sign, like fn_log_psi, for callers that cannot let the library allocate
+ * device memory: code enqueuing work during CUDA-graph stream capture, programs whose
+ * device memory belongs to a pool or framework allocator, processes with a fixed
+ * memory budget.  No cudaMalloc or cudaFree happens in this call.  Its scratch is one
+ * static 64 MiB device array that every device loading the library holds until the
+ * process exits; the array's address is looked up on the first call made on each
+ * device (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Calls share the array: two calls whose work overlaps on the GPU race, so order them
+ * on one stream.  A batch whose scratch exceeds 64 MiB returns FN_ERR_ARG, with the
+ * walker count that fits in fn_last_error().  The handle's own workspace is untouched.
+ * The method has no counterpart of this entry point; it is a deployment variant.  */
+fn_status fn_log_psi_noalloc(fn_system_t sys, const void* d_params, const void* d_walkers,
+                             int n_walkers, double* d_log_psi, int8_t* d_sign, void* stream);
+
 /* Kernel timing: while enabled, every kernel the handle launches is bracketed by a
  * CUDA event pair on its stream (adds a few microseconds per launch).  Enabling or
  * disabling clears the counters.  fn_profile_read waits for the recorded events and

@@ -30,6 +30,7 @@ SIGNATURES = {
     "fn_mcmc_steps": (C.c_int, [_P, _P, _P, _P, C.c_int, C.c_int, C.c_double, C.c_uint64, C.c_uint64, _P, _P]),
     "fn_local_energy": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P, _P]),
     "fn_energy_grad": (C.c_int, [_P, _P, _P, _P, C.c_int, _P, _P, _P]),
+    "fn_log_psi_noalloc": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P]),
     "fn_log_psi_vjp": (C.c_int, [_P, _P, _P, _P, C.c_int, _P, _P]),
     "fn_profile_enable": (C.c_int, [_P, C.c_int]),
     "fn_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),

@@ -140,6 +140,17 @@ class System:
         _check(self._lib.fn_log_psi(self._h, _ptr(params), _ptr(walkers), B, _ptr(lp), _ptr(sg), _stream(stream)))
         return lp, sg
 
+    def log_psi_noalloc(self, params, walkers, stream=None) -> Tuple[torch.Tensor, torch.Tensor]:
+        """log|psi| with the library's static scratch (no device allocation inside the call);
+        the output tensors are allocated here, by the caller side."""
+        self._check_walkers(params, walkers)
+        B = walkers.shape[0]
+        lp = torch.empty(B, dtype=torch.float64, device=walkers.device)
+        sg = torch.empty(B, dtype=torch.int8, device=walkers.device)
+        _check(self._lib.fn_log_psi_noalloc(self._h, _ptr(params), _ptr(walkers), B, _ptr(lp), _ptr(sg),
+                                            _stream(stream)))
+        return lp, sg
+
     def mcmc_steps(self, params, walkers, log_psi, n_steps: int, step_size: float, seed: int,
                    step_offset: int = 0, accept_count: Optional[torch.Tensor] = None, stream=None):
         self._check_walkers(params, walkers)
