@@ -129,22 +129,23 @@ static void build_layout(fn_system* s) {
       d.off_W = d.off_c = -1;
     }
   }
-  const int ns[2] = {s->n_up, s->n_dn};
+  const int nsp[2] = {s->n_up, s->n_dn};
   for (int a = 0; a < 2; ++a) {
-    if (!ns[a]) continue;
-    s->off_w[a] = off; off += (int64_t)K * ns[a] * h1;
-    s->off_g[a] = off; off += (int64_t)K * ns[a];
+    if (!nsp[a]) continue;
+    s->off_w[a] = off; off += (int64_t)K * nsp[a] * h1;
+    s->off_g[a] = off; off += (int64_t)K * nsp[a];
   }
   const int sig_sz = s->cfg.envelope == FN_ENV_ANISOTROPIC ? 9 : 1;
   for (int a = 0; a < 2; ++a) {
-    if (!ns[a]) continue;
-    s->off_pi[a] = off; off += (int64_t)K * ns[a] * M;
-    s->off_sig[a] = off; off += (int64_t)K * ns[a] * M * sig_sz;
+    if (!nsp[a]) continue;
+    s->off_pi[a] = off; off += (int64_t)K * nsp[a] * M;
+    s->off_sig[a] = off; off += (int64_t)K * nsp[a] * M * sig_sz;
   }
   s->P = off;
 
   PrepLayout& p = s->prep;
   int64_t q = 0, q16 = 0;
+  const int ns[2] = {s->n_up, s->n_dn};
   for (int l = 0; l < L; ++l) {
     const LayerDims& d = s->layer[l];
     p.VsT[l] = q; q += (int64_t)d.k_self * h1;
@@ -154,10 +155,14 @@ static void build_layout(fn_system* s) {
       p.W[l] = q; q += (int64_t)h2 * d.d_g;
       p.c[l] = q; q += h2;
     }
-    p.Vs16[l] = q16; q16 += (int64_t)h1 * d.ldx;
+    p.Vs16[l] = q16; q16 += (int64_t)h1 * 2 * d.ldx;
+    q16 = round_up(q16, 64);
+    p.U16[l] = q16; q16 += (int64_t)h1 * 4 * d.d_h;
     q = round_up(q, 4);
     q16 = round_up(q16, 64);
   }
+  p.W16 = q16; q16 += (int64_t)K * (ns[0] + ns[1]) * 2 * h1;
+  q16 = round_up(q16, 64);
   for (int a = 0; a < 2; ++a) {
     const int64_t ko = (int64_t)K * ns[a];
     p.wT[a] = q; q += ko * h1;
@@ -184,7 +189,7 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
   int max_ldx = 0, max_dh = 0;
   for (int l = 0; l < L; ++l) {
     o_X[l] = take((size_t)T * sh.R * s->layer[l].ldx * sizeof(Act));
-    o_Hbar[l] = take((size_t)T * B * 2 * s->layer[l].d_h * sizeof(Cmp));
+    o_Hbar[l] = take((size_t)T * B * 2 * s->layer[l].d_h * sizeof(Act));
     o_act[l] = take((size_t)sh.R * h1 * sizeof(Cmp));
     o_gp[l] = take((size_t)B * N * N * h2 * sizeof(Cmp));
     max_ldx = std::max(max_ldx, s->layer[l].ldx);
@@ -192,7 +197,7 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
   }
   const size_t o_HL = take((size_t)T * sh.R * h1 * sizeof(Act));
   const size_t o_M = take((size_t)T * B * h1 * sizeof(Cmp));
-  const size_t o_Phi = take((size_t)B * phi_walker_stride(s, T) * sizeof(Det));
+  const size_t o_Phi = take((size_t)B * phi_walker_stride(s, T) * sizeof(typename Mode::PhiT));
   const size_t o_prep = take((size_t)s->prep.total * sizeof(Cmp));
   const size_t o_prep16 = take((size_t)s->prep.total16 * sizeof(__nv_bfloat16));
   const size_t o_walk2 = take((size_t)B * N * 3 * sizeof(Wlk));
@@ -207,6 +212,7 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
   const size_t o_dPhi = take((size_t)B * phi_walker_stride(s, 1) * sizeof(Det));
   const size_t o_gradc = take((size_t)s->prep.total * sizeof(Cmp));
   const size_t o_dP = take((size_t)sh.R * s->cfg.n_dets * N * sizeof(Cmp));
+  const size_t o_orbP = take(Mode::kMode == FN_BF16_MIXED ? (size_t)sh.R * 4 * s->cfg.n_dets * N * sizeof(float) : 0);
   const size_t o_status = take(sizeof(int) * 4);
   const size_t o_counter = take(sizeof(int64_t) * 4);
   if (ws && ws->base) {
@@ -219,7 +225,7 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
     ws->prep16 = b + o_prep16; ws->walk2 = b + o_walk2; ws->lp2 = (double*)(b + o_lp2);
     ws->scratch_d = (double*)(b + o_scr); ws->dX = b + o_dX; ws->dH = b + o_dH; ws->dZ = b + o_dZ;
     ws->dZw = b + o_dZw; ws->dHbar = b + o_dHbar; ws->dG = b + o_dG; ws->dPhi = b + o_dPhi;
-    ws->gradc = b + o_gradc; ws->dP = b + o_dP; ws->status = (int*)(b + o_status); ws->counter = (int64_t*)(b + o_counter);
+    ws->gradc = b + o_gradc; ws->dP = b + o_dP; ws->orbP = (float*)(b + o_orbP); ws->status = (int*)(b + o_status); ws->counter = (int64_t*)(b + o_counter);
   }
   return off;
 }

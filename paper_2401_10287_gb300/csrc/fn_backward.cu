@@ -348,7 +348,7 @@ void launch_backward(const fn_system* s, const void* walkers, const Shape& sh, c
     const int splitB = (int)std::max(1, std::min(32, sh.B / 256));
     {
       ProfScope ps(s->prof, kProfBwdGemm, st);
-      gemm<Cmp, Cmp, Cmp, Cmp>(st, 2 * d.d_h, h1, sh.B, (const Cmp*)ws.Hbar[l], 1, 2 * d.d_h, dZw, h1, 1,
+      gemm<Act, Cmp, Cmp, Cmp>(st, 2 * d.d_h, h1, sh.B, (const Act*)ws.Hbar[l], 1, 2 * d.d_h, dZw, h1, 1,
                                gradc + pl.UT[l], h1, 1, (const Cmp*)nullptr, 0, splitB, true);
     }
     // dX = dZ V_self^T  ([R][k_self], row stride ldx)

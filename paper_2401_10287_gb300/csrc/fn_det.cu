@@ -108,7 +108,7 @@ __device__ void thread_inverse(const Det* A, const int* perm, const Det* rcp, in
 // (determinant, spin) blocks; then every thread takes (block, coordinate) items
 // g_t = tr(C d_t A), q_t = tr((C d_t A)^2) and tr(C lap A); then the determinant terms
 // are combined and E_L assembled.
-template <typename Det, typename Wlk>
+template <typename Det, typename Wlk, typename PhiT>
 __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, const double* __restrict__ nuc,
                                                     Shape sh, DetArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -130,14 +130,14 @@ __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, c
   Det* rho = lapk + K;                                   // [K]
   Det* red = rho + K;                                    // [128]
   int* perm = (int*)(red + 128);                         // [nmax][ST]
-  const Det* Phi = (const Det*)a.Phi + (int64_t)w * a.PW;
+  const PhiT* Phi = (const PhiT*)a.Phi + (int64_t)w * a.PW;
   const int64_t blk_off[2] = {0, (int64_t)K * T * ns[0] * ns[0]};
   // value slabs of every block, interleaved by block (thread 2k + spin)
   for (int sp = 0; sp < 2; ++sp) {
     const int nn = ns[sp] * ns[sp];
     for (int e = tid; e < K * nn; e += blockDim.x) {
       const int k = e / nn, idx = e % nn;
-      A[(int64_t)idx * ST + 2 * k + sp] = Phi[blk_off[sp] + (int64_t)k * T * nn + idx];
+      A[(int64_t)idx * ST + 2 * k + sp] = (Det)Phi[blk_off[sp] + (int64_t)k * T * nn + idx];
     }
   }
   __syncthreads();
@@ -164,19 +164,19 @@ __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, c
     }
     const Det* Cm = C + p;
     const int t = tr < NC ? 1 + tr : T - 1;
-    const Det* D = Phi + blk_off[sp] + (int64_t)k * T * n * n + (int64_t)t * n * n;
+    const PhiT* D = Phi + blk_off[sp] + (int64_t)k * T * n * n + (int64_t)t * n * n;
     if (tr < NC) {
       Det g = 0, q = 0;
       for (int i = 0; i < n; ++i) {
         for (int j = i; j < n; ++j) {
           Det bij = 0;
-          for (int m = 0; m < n; ++m) bij += Cm[(int64_t)(i * n + m) * ST] * D[m * n + j];
+          for (int m = 0; m < n; ++m) bij += Cm[(int64_t)(i * n + m) * ST] * (Det)D[m * n + j];
           if (j == i) {
             g += bij;
             q += bij * bij;
           } else {
             Det bji = 0;
-            for (int m = 0; m < n; ++m) bji += Cm[(int64_t)(j * n + m) * ST] * D[m * n + i];
+            for (int m = 0; m < n; ++m) bji += Cm[(int64_t)(j * n + m) * ST] * (Det)D[m * n + i];
             q += (Det)2 * bij * bji;
           }
         }
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, c
     } else {
       Det l = 0;
       for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) l += Cm[(int64_t)(j * n + i) * ST] * D[i * n + j];
+        for (int j = 0; j < n; ++j) l += Cm[(int64_t)(j * n + i) * ST] * (Det)D[i * n + j];
       lt[p] = l;
     }
   }
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, c
 
 // Value pass (log|psi|, plus the backward seed rho_k A^{-T} when requested): one CTA per
 // walker, one thread per (determinant, spin) block.
-template <typename Det>
+template <typename Det, typename PhiT>
 __global__ void k_det_value(Shape sh, DetArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int w = blockIdx.x, tid = threadIdx.x;
@@ -276,7 +276,7 @@ __global__ void k_det_value(Shape sh, DetArgs a) {
   Det* sg2 = ld2 + NM;
   Det* rho = sg2 + NM;                                   // [K]
   int* perm = (int*)(rho + K);                           // [nmax][ST]
-  const Det* Phi = (const Det*)a.Phi + (int64_t)w * a.PW;
+  const PhiT* Phi = (const PhiT*)a.Phi + (int64_t)w * a.PW;
   const int64_t blk_off[2] = {0, (int64_t)K * ns[0] * ns[0]};
   const int64_t per = (int64_t)K * (ns[0] * ns[0] + ns[1] * ns[1]);
   Det* io = want_inv ? (Det*)a.inv_out + (int64_t)w * per : nullptr;
@@ -286,7 +286,7 @@ __global__ void k_det_value(Shape sh, DetArgs a) {
     const int n = ns[sp];
     const int64_t q = e - blk_off[sp];
     const int k = (int)(q / (n * n)), idx = (int)(q % (n * n));
-    A[(int64_t)idx * ST + 2 * k + sp] = Phi[e];
+    A[(int64_t)idx * ST + 2 * k + sp] = (Det)Phi[e];
   }
   __syncthreads();
   if (tid < NM) {
@@ -340,7 +340,7 @@ __global__ void k_det_value(Shape sh, DetArgs a) {
 template <class Mode>
 void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh, double* e_local, double* log_psi,
                        int8_t* sign, bool keep_inverse, cudaStream_t st) {
-  using Det = typename Mode::Det; using Wlk = typename Mode::Wlk;
+  using Det = typename Mode::Det; using Wlk = typename Mode::Wlk; using PhiT = typename Mode::PhiT;
   DetArgs a{};
   a.Phi = s->ws.Phi;
   a.PW = phi_walker_stride(s, sh.T);
@@ -359,15 +359,15 @@ void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh,
     const int ST = (int)round_up(2 * K, 32);
     const size_t smem = sizeof(Det) * ((size_t)2 * nmax * nmax * ST + (size_t)nmax * ST + 4 * K + 4 * K * NC +
                                        2 * K + K * NC + 2 * K + 128) + sizeof(int) * (size_t)nmax * ST;
-    cudaFuncSetAttribute(k_det_energy<Det, Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_det_energy<Det, Wlk><<<sh.B, 128, smem, st>>>((const Wlk*)walkers, s->d_nuclei, sh, a);
+    cudaFuncSetAttribute(k_det_energy<Det, Wlk, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_det_energy<Det, Wlk, PhiT><<<sh.B, 128, smem, st>>>((const Wlk*)walkers, s->d_nuclei, sh, a);
   } else {
     const int threads = (int)round_up(2 * K, 32);
     const bool inv = keep_inverse;
     const size_t vsmem = sizeof(Det) * ((size_t)(inv ? 2 : 1) * nmax * nmax * threads + (size_t)nmax * threads +
                                         5 * K) + sizeof(int) * (size_t)nmax * threads;
-    cudaFuncSetAttribute(k_det_value<Det>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem);
-    k_det_value<Det><<<sh.B, threads, vsmem, st>>>(sh, a);
+    cudaFuncSetAttribute(k_det_value<Det, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem);
+    k_det_value<Det, PhiT><<<sh.B, threads, vsmem, st>>>(sh, a);
   }
 }
 

@@ -31,7 +31,11 @@ __global__ void k_prep(const Par* __restrict__ blob, const CopyDesc* __restrict_
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / d.cols, c = e % d.cols;
     const Par v = blob[d.src + r * d.s_rs + c * d.s_cs];
-    if (d.to16) prep16[d.dst + r * d.d_rs + c * d.d_cs] = __float2bfloat16_rn((float)v);
+    if (d.to16) {
+      const __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
+      prep16[d.dst + r * d.d_rs + c * d.d_cs] =
+          d.to16 == 1 ? hi : __float2bfloat16_rn((float)v - __bfloat162float(hi));
+    }
     else prep[d.dst + r * d.d_rs + c * d.d_cs] = (Cmp)v;
   }
 }
@@ -53,12 +57,23 @@ static std::vector<CopyDesc> build_descs(const fn_system* s, bool with16) {
       v.push_back({d.off_c, 0, 1, p.c[l], 0, 1, 1, h2, 0});
     }
     if (with16) {
-      v.push_back({d.off_V, f_in, 1, p.Vs16[l], d.ldx, 1, h1, d.d_h, 1});
-      v.push_back({d.off_V + 3 * d.d_h, f_in, 1, p.Vs16[l] + d.d_h, d.ldx, 1, h1, 2 * d.d_g, 1});
+      // hi part in columns [0, k), residual lo part in [ld, ld + k) of a [rows][2 ld] matrix
+      for (int part = 1; part <= 2; ++part) {
+        const int ox = part == 2 ? d.ldx : 0, ou = part == 2 ? 2 * d.d_h : 0;
+        v.push_back({d.off_V, f_in, 1, p.Vs16[l] + ox, 2 * d.ldx, 1, h1, d.d_h, part});
+        v.push_back({d.off_V + 3 * d.d_h, f_in, 1, p.Vs16[l] + d.d_h + ox, 2 * d.ldx, 1, h1, 2 * d.d_g, part});
+        v.push_back({d.off_V + d.d_h, f_in, 1, p.U16[l] + ou, 4 * d.d_h, 1, h1, 2 * d.d_h, part});
+      }
     }
   }
   const int ns[2] = {s->n_up, s->n_dn};
   const int sig_sz = s->cfg.envelope == FN_ENV_ANISOTROPIC ? 9 : 1;
+  if (with16)
+    for (int a = 0; a < 2; ++a)
+      if (ns[a])
+        for (int part = 1; part <= 2; ++part)
+          v.push_back({s->off_w[a], h1, 1, p.W16 + (a ? (int64_t)K * ns[0] * 2 * h1 : 0) + (part == 2 ? h1 : 0),
+                       2 * h1, 1, K * ns[a], h1, part});
   for (int a = 0; a < 2; ++a) {
     if (!ns[a]) continue;
     const int ko = K * ns[a];
@@ -125,9 +140,9 @@ __global__ void k_features_en(const Wlk* __restrict__ r, const double* __restric
 }
 
 // Hbar0[t][w][spin * 4M + 4m + a]: mean over the electrons of one spin of h0.
-template <typename Cmp, typename Wlk>
+template <typename Act, typename Wlk>
 __global__ void k_features_mean(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh,
-                                Cmp* __restrict__ Hbar) {
+                                Act* __restrict__ Hbar) {
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= (int64_t)sh.B * 2 * sh.M) return;
   const int w = (int)(gid / (2 * sh.M)), spin = (int)((gid / sh.M) % 2), m = (int)(gid % sh.M);
@@ -135,7 +150,7 @@ __global__ void k_features_mean(const Wlk* __restrict__ r, const double* __restr
   const int n_s = hi - lo;
   const int width = 2 * 4 * sh.M;
   const int64_t slab = (int64_t)sh.B * width;
-  Cmp* base = Hbar + (int64_t)w * width + spin * 4 * sh.M + 4 * m;
+  Act* base = Hbar + (int64_t)w * width + spin * 4 * sh.M + 4 * m;
   const double inv = n_s ? 1.0 / n_s : 0.0;
   double v[4] = {0, 0, 0, 0}, lap = 0.0;
   for (int e = lo; e < hi; ++e) {
@@ -146,21 +161,21 @@ __global__ void k_features_mean(const Wlk* __restrict__ r, const double* __restr
     lap += 2.0 / dist;
     if (sh.T > 1)
       for (int c = 0; c < 3; ++c) {
-        Cmp* o = base + (1 + 3 * e + c) * slab;
-        for (int a = 0; a < 3; ++a) o[a] = (Cmp)(a == c ? inv : 0.0);
-        o[3] = (Cmp)(d[c] / dist * inv);
+        Act* o = base + (1 + 3 * e + c) * slab;
+        for (int a = 0; a < 3; ++a) st(o + a, a == c ? inv : 0.0);
+        st(o + 3, d[c] / dist * inv);
       }
   }
-  for (int a = 0; a < 4; ++a) base[a] = (Cmp)(v[a] * inv);
+  for (int a = 0; a < 4; ++a) st(base + a, v[a] * inv);
   if (sh.T == 1) return;
-  Cmp* o = base + (sh.T - 1) * slab;
-  o[0] = o[1] = o[2] = (Cmp)0; o[3] = (Cmp)(lap * inv);
+  Act* o = base + (sh.T - 1) * slab;
+  st(o, 0.0); st(o + 1, 0.0); st(o + 2, 0.0); st(o + 3, lap * inv);
   // slabs of the other spin's electrons are zero
   const int olo = spin ? 0 : sh.n_up, ohi = spin ? sh.n_up : sh.N;
   for (int e = olo; e < ohi; ++e)
     for (int c = 0; c < 3; ++c) {
-      Cmp* q = base + (1 + 3 * e + c) * slab;
-      q[0] = q[1] = q[2] = q[3] = (Cmp)0;
+      Act* q = base + (1 + 3 * e + c) * slab;
+      st(q, 0.0); st(q + 1, 0.0); st(q + 2, 0.0); st(q + 3, 0.0);
     }
 }
 
@@ -205,39 +220,41 @@ __device__ void stage_pair_weights(const PairArgs& a, Cmp* sW, Cmp* sc) {
   }
 }
 
-// z[c] = sum_k W^T[k][c] g[k] (+ bias)
+// z[c] = sum_k W^T[k][c] g[k] (+ bias); the weight row is read as 16-byte vectors that
+// every thread of the block reads at the same time (broadcast).
 template <typename Cmp>
 __device__ __forceinline__ void pair_matvec(const Cmp* __restrict__ sWl, const Cmp* __restrict__ scl, bool bias,
                                             int dg, const Cmp (&g)[kMaxH2], Cmp (&z)[kMaxH2]) {
 #pragma unroll
   for (int c = 0; c < kMaxH2; ++c) z[c] = bias ? scl[c] : (Cmp)0;
-#pragma unroll 4
-  for (int k = 0; k < dg; ++k) {
-    const Cmp gk = g[k];
-    const Cmp* row = sWl + k * kMaxH2;
 #pragma unroll
-    for (int c = 0; c < kMaxH2; ++c) z[c] += row[c] * gk;
+  for (int k = 0; k < kMaxH2; ++k) {
+    if (k < dg) {
+      const Cmp gk = g[k];
+      const Cmp* row = sWl + k * kMaxH2;
+#pragma unroll
+      for (int c = 0; c < kMaxH2; ++c) z[c] += row[c] * gk;
+    }
   }
 }
 
+// Full pass: CTA per (walker, electron i); thread (j, jet row rr).  Per layer the rows
+// that are summed over j (value, Laplacian, d/dr_i) are staged in shared memory and
+// reduced per (spin, row, channel); the d/dr_j rows are written straight to their slab.
 template <typename Act, typename Cmp, typename Wlk>
 __global__ void __launch_bounds__(256) k_pair_full(const Wlk* __restrict__ r, Shape sh, PairArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cmp* sW = (Cmp*)smem_raw;                                  // [L-1][32][32]
-  Cmp* sc = sW + (kMaxLayers - 1) * kMaxH2 * kMaxH2;        // [L-1][32]
-  Cmp* acc = sc + (kMaxLayers - 1) * kMaxH2;                 // [L][2][5][32]: value, Laplacian, d/dr_i
+  Cmp* sc = sW + (a.L - 1) * kMaxH2 * kMaxH2;               // [L-1][32]
+  Cmp* gs = sc + (a.L - 1) * kMaxH2;                        // [N][8][33]
   const int w = blockIdx.x / sh.N, i = blockIdx.x % sh.N;
   const int j = threadIdx.x >> 3, rr = threadIdx.x & 7;      // partner, jet row
-  const unsigned gmask = 0xFFu << (threadIdx.x & 24);        // the 8 lanes of this pair
   stage_pair_weights(a, sW, sc);
-  for (int e = threadIdx.x; e < a.L * 2 * 5 * kMaxH2; e += blockDim.x) acc[e] = (Cmp)0;
-  __syncthreads();
   const int64_t row = tile_row(w, i, sh.N, sh.wpt);
   const bool live = j < sh.N;
   const int sj = j < sh.n_up ? 0 : 1;
   const int nsj = sj ? sh.n_dn : sh.n_up;
   const Cmp inv_n = (Cmp)1 / (Cmp)(nsj > 0 ? nsj : 1);
-  // input features of the pair: jet row rr of (r_i - r_j, |r_i - r_j|)
   Cmp g[kMaxH2];
 #pragma unroll
   for (int c = 0; c < kMaxH2; ++c) g[c] = 0;
@@ -259,17 +276,14 @@ __global__ void __launch_bounds__(256) k_pair_full(const Wlk* __restrict__ r, Sh
   }
   for (int l = 0; l < a.L; ++l) {
     const int dg = a.d_g[l];
+    Act* X = (Act*)a.X[l];
+    const int64_t slab = sh.R * a.ldx[l];
     if (live) {
-      Cmp* al = acc + (l * 2 + sj) * 5 * kMaxH2;
-      const int slot = rr == 0 ? 0 : (rr == 7 ? 1 : (rr < 4 ? 1 + rr : -1));
-      if (slot >= 0) {
 #pragma unroll
-        for (int c = 0; c < kMaxH2; ++c)
-          if (c < dg) atomicAdd(al + slot * kMaxH2 + c, g[c]);
-      } else if (j != i) {                                     // d/dr_j row: its own slab
-        const int c3 = rr - 4;
-        Act* X = (Act*)a.X[l];
-        Act* o = X + (1 + 3 * j + c3) * sh.R * a.ldx[l] + row * a.ldx[l] + a.col0[l];
+      for (int c = 0; c < kMaxH2; ++c)
+        if (c < dg) gs[(j * 8 + rr) * 33 + c] = g[c];
+      if (rr >= 4 && rr <= 6 && j != i) {                    // d/dr_j row: its own slab
+        Act* o = X + (1 + 3 * j + (rr - 4)) * slab + row * a.ldx[l] + a.col0[l];
 #pragma unroll
         for (int c = 0; c < kMaxH2; ++c)
           if (c < dg) {
@@ -278,14 +292,27 @@ __global__ void __launch_bounds__(256) k_pair_full(const Wlk* __restrict__ r, Sh
           }
       }
     }
+    __syncthreads();
+    // sums over j of the value (slab 0), Laplacian (slab T-1) and d/dr_i rows (slabs 1 + 3i + c)
+    for (int e = threadIdx.x; e < 2 * 5 * dg; e += blockDim.x) {
+      const int s2 = e / (5 * dg), q = (e / dg) % 5, c = e % dg;
+      const int lo = s2 ? sh.n_up : 0, hi = s2 ? sh.N : sh.n_up;
+      const int rsrc = q == 0 ? 0 : (q == 1 ? 7 : q - 1);
+      Cmp sum = 0;
+      for (int jj = lo; jj < hi; ++jj) sum += gs[(jj * 8 + rsrc) * 33 + c];
+      const Cmp v = hi > lo ? sum / (Cmp)(hi - lo) : (Cmp)0;
+      const int t = q == 0 ? 0 : (q == 1 ? sh.T - 1 : 1 + 3 * i + (q - 2));
+      st(X + t * slab + row * a.ldx[l] + a.col0[l] + s2 * dg + c, v);
+    }
     if (l == a.L - 1) break;
+    __syncthreads();
     Cmp z[kMaxH2];
     pair_matvec(sW + l * kMaxH2 * kMaxH2, sc + l * kMaxH2, rr == 0, dg, g, z);
     // tanh jets: h from the value row, sum of squares of the 6 tangent rows
-    const int base = threadIdx.x & ~7;
+    const int base = threadIdx.x & 24;
 #pragma unroll
     for (int c = 0; c < kMaxH2; ++c) {
-      const Cmp zv = __shfl_sync(0xffffffffu, z[c], base, 32);
+      const Cmp zv = __shfl_sync(0xffffffffu, z[c], base);
       const Cmp h = f_tanh(zv);
       const Cmp dh = (Cmp)1 - h * h;
       Cmp sq = (rr >= 1 && rr <= 6) ? z[c] * z[c] : (Cmp)0;
@@ -296,76 +323,65 @@ __global__ void __launch_bounds__(256) k_pair_full(const Wlk* __restrict__ r, Sh
       if (c >= a.h2) out = 0;
       g[c] = (l > 0 ? g[c] : (Cmp)0) + out;
     }
-    (void)gmask;
-  }
-  __syncthreads();
-  // sums over j: value (slab 0), Laplacian (slab T-1), d/dr_i (slabs 1 + 3i + c)
-  for (int l = 0; l < a.L; ++l) {
-    const int dg = a.d_g[l];
-    Act* X = (Act*)a.X[l];
-    const int64_t slab = sh.R * a.ldx[l];
-    for (int e = threadIdx.x; e < 2 * 5 * dg; e += blockDim.x) {
-      const int s = e / (5 * dg), q = (e / dg) % 5, c = e % dg;
-      const int ns = s ? sh.n_dn : sh.n_up;
-      const Cmp v = ns ? acc[((l * 2 + s) * 5 + q) * kMaxH2 + c] / (Cmp)ns : (Cmp)0;
-      const int t = q == 0 ? 0 : (q == 1 ? sh.T - 1 : 1 + 3 * i + (q - 2));
-      st(X + t * slab + row * a.ldx[l] + a.col0[l] + s * dg + c, v);
-    }
   }
 }
 
+// Value pass: CTA per walker, threads loop over pairs.  The pair values live in shared
+// memory between layers; per layer the spin means over j are summed per
+// (i, spin, channel), then every pair is advanced through the next pair layer.
 template <typename Act, typename Cmp, typename Wlk>
-__global__ void __launch_bounds__(256) k_pair_value(const Wlk* __restrict__ r, Shape sh, PairArgs a) {
+__global__ void __launch_bounds__(512) k_pair_value(const Wlk* __restrict__ r, Shape sh, PairArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cmp* sW = (Cmp*)smem_raw;
-  Cmp* sc = sW + (kMaxLayers - 1) * kMaxH2 * kMaxH2;
-  Cmp* acc = sc + (kMaxLayers - 1) * kMaxH2;                 // [L][N][2][32]
+  Cmp* sc = sW + (a.L - 1) * kMaxH2 * kMaxH2;
+  Cmp* gs = sc + (a.L - 1) * kMaxH2;                        // [N*N][33]
   const int w = blockIdx.x;
+  const int N = sh.N, NP = N * N;
   stage_pair_weights(a, sW, sc);
-  for (int e = threadIdx.x; e < a.L * sh.N * 2 * kMaxH2; e += blockDim.x) acc[e] = (Cmp)0;
-  __syncthreads();
-  const Wlk* rw = r + (int64_t)w * sh.N * 3;
-  for (int p = threadIdx.x; p < sh.N * sh.N; p += blockDim.x) {
-    const int i = p / sh.N, j = p % sh.N;
-    const int sj = j < sh.n_up ? 0 : 1;
-    Cmp g[kMaxH2];
-#pragma unroll
-    for (int c = 0; c < kMaxH2; ++c) g[c] = 0;
+  const Wlk* rw = r + (int64_t)w * N * 3;
+  for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+    const int i = p / N, j = p % N;
+    Cmp* gp = gs + p * 33;
+    for (int c = 0; c < 4; ++c) gp[c] = 0;
     if (j != i) {
       double d[3];
       for (int c = 0; c < 3; ++c) d[c] = (double)rw[3 * i + c] - (double)rw[3 * j + c];
-      g[0] = (Cmp)d[0]; g[1] = (Cmp)d[1]; g[2] = (Cmp)d[2];
-      g[3] = (Cmp)sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      gp[0] = (Cmp)d[0]; gp[1] = (Cmp)d[1]; gp[2] = (Cmp)d[2];
+      gp[3] = (Cmp)sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     }
-    for (int l = 0; l < a.L; ++l) {
-      const int dg = a.d_g[l];
-      Cmp* al = acc + ((l * sh.N + i) * 2 + sj) * kMaxH2;
+  }
+  for (int l = 0; l < a.L; ++l) {
+    const int dg = a.d_g[l];
+    __syncthreads();
+    Act* X = (Act*)a.X[l];
+    for (int e = threadIdx.x; e < N * 2 * dg; e += blockDim.x) {
+      const int ii = e / (2 * dg), s2 = (e / dg) % 2, c = e % dg;
+      const int lo = s2 ? sh.n_up : 0, hi = s2 ? N : sh.n_up;
+      Cmp sum = 0;
+      for (int jj = lo; jj < hi; ++jj) sum += gs[(ii * N + jj) * 33 + c];
+      const int64_t rowi = tile_row(w, ii, N, sh.wpt);
+      st(X + rowi * a.ldx[l] + a.col0[l] + s2 * dg + c, hi > lo ? sum / (Cmp)(hi - lo) : (Cmp)0);
+    }
+    if (l == a.L - 1) break;
+    __syncthreads();
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+      Cmp* gp = gs + p * 33;
+      Cmp g[kMaxH2], z[kMaxH2];
 #pragma unroll
-      for (int c = 0; c < kMaxH2; ++c)
-        if (c < dg) atomicAdd(al + c, g[c]);
-      if (l == a.L - 1) break;
-      Cmp z[kMaxH2];
+      for (int c = 0; c < kMaxH2; ++c) g[c] = c < dg ? gp[c] : (Cmp)0;
       pair_matvec(sW + l * kMaxH2 * kMaxH2, sc + l * kMaxH2, true, dg, g, z);
 #pragma unroll
       for (int c = 0; c < kMaxH2; ++c) g[c] = (l > 0 ? g[c] : (Cmp)0) + (c < a.h2 ? f_tanh(z[c]) : (Cmp)0);
+#pragma unroll
+      for (int c = 0; c < kMaxH2; ++c)
+        if (c < a.h2) gp[c] = g[c];
       if (a.gstore[l + 1]) {
-        Cmp* gs = (Cmp*)a.gstore[l + 1] + (((int64_t)w * sh.N + i) * sh.N + j) * a.h2;
+        const int i = p / N, j = p % N;
+        Cmp* gsto = (Cmp*)a.gstore[l + 1] + (((int64_t)w * N + i) * N + j) * a.h2;
 #pragma unroll
         for (int c = 0; c < kMaxH2; ++c)
-          if (c < a.h2) gs[c] = g[c];
+          if (c < a.h2) gsto[c] = g[c];
       }
-    }
-  }
-  __syncthreads();
-  for (int l = 0; l < a.L; ++l) {
-    const int dg = a.d_g[l];
-    Act* X = (Act*)a.X[l];
-    for (int e = threadIdx.x; e < sh.N * 2 * dg; e += blockDim.x) {
-      const int i = e / (2 * dg), s = (e / dg) % 2, c = e % dg;
-      const int ns = s ? sh.n_dn : sh.n_up;
-      const int64_t row = tile_row(w, i, sh.N, sh.wpt);
-      const Cmp v = ns ? acc[((l * sh.N + i) * 2 + s) * kMaxH2 + c] / (Cmp)ns : (Cmp)0;
-      st(X + row * a.ldx[l] + a.col0[l] + s * dg + c, v);
     }
   }
 }
@@ -471,7 +487,7 @@ __global__ void __launch_bounds__(256) k_layer(Shape sh, LayerArgs a) {
     }
     if (a.Hbar_out) {
       __syncthreads();
-      Cmp* Hb = (Cmp*)a.Hbar_out;
+      Act* Hb = (Act*)a.Hbar_out;
       for (int e = tid; e < sh.wpt * 2 * 64; e += 256) {
         const int wl = e / 128, s = (e / 64) % 2, cl = e % 64, col = n0 + cl;
         const int w = tile * sh.wpt + wl;
@@ -479,7 +495,7 @@ __global__ void __launch_bounds__(256) k_layer(Shape sh, LayerArgs a) {
         const int lo = s ? sh.n_up : 0, hi = s ? sh.N : sh.n_up;
         Cmp sum = 0;
         for (int i = lo; i < hi; ++i) sum += ys[(wl * sh.N + i) * 65 + cl];
-        Hb[((int64_t)t * sh.B + w) * 2 * a.h1 + s * a.h1 + col] = hi > lo ? sum / (Cmp)(hi - lo) : (Cmp)0;
+        st(Hb + ((int64_t)t * sh.B + w) * 2 * a.h1 + s * a.h1 + col, hi > lo ? sum / (Cmp)(hi - lo) : (Cmp)0);
       }
       __syncthreads();
     }
@@ -498,7 +514,76 @@ struct OrbArgs {
   int h1, K, aniso;
 };
 
-template <typename Act, typename Cmp, typename Det, typename Wlk, bool FULL>
+// Envelope sum_m pi exp(-s_m) of orbital ko at electron position rj (Eq. 4), its gradient
+// along rj and its Laplacian.  Isotropic: s = sigma |d|; anisotropic: s = |Sigma d|, with
+// grad s = Sigma^T u / s and lap s = (|Sigma|_F^2 - |Sigma^T u|^2 / s^2) / s.
+template <typename Cmp, typename Wlk>
+__device__ __forceinline__ void env_jet(const OrbArgs& a, int spin, int ko, const Wlk* rj, const double* nuc, int M,
+                                        Cmp* env_out, Cmp* ge, Cmp* le_out) {
+  const Cmp* pi = (const Cmp*)a.pi[spin] + (int64_t)ko * M;
+  Cmp env = 0, le = 0;
+  ge[0] = ge[1] = ge[2] = 0;
+  for (int m = 0; m < M; ++m) {
+    const Cmp d[3] = {(Cmp)((double)rj[0] - nuc[3 * m]), (Cmp)((double)rj[1] - nuc[3 * m + 1]),
+                      (Cmp)((double)rj[2] - nuc[3 * m + 2])};
+    Cmp s, gs[3], ls;
+    if (!a.aniso) {
+      const Cmp sg = ((const Cmp*)a.sig[spin])[(int64_t)ko * M + m];
+      const Cmp dist = f_sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      s = sg * dist;
+      for (int c = 0; c < 3; ++c) gs[c] = sg * d[c] / dist;
+      ls = (Cmp)2 * sg / dist;
+    } else {
+      const Cmp* S = (const Cmp*)a.sig[spin] + ((int64_t)ko * M + m) * 9;
+      Cmp u[3];
+      for (int x = 0; x < 3; ++x) u[x] = S[3 * x] * d[0] + S[3 * x + 1] * d[1] + S[3 * x + 2] * d[2];
+      s = f_sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      Cmp stu[3], frob = 0, n2 = 0;
+      for (int y = 0; y < 3; ++y) stu[y] = S[y] * u[0] + S[3 + y] * u[1] + S[6 + y] * u[2];
+      for (int q = 0; q < 9; ++q) frob += S[q] * S[q];
+      for (int y = 0; y < 3; ++y) { gs[y] = stu[y] / s; n2 += stu[y] * stu[y]; }
+      ls = (frob - n2 / (s * s)) / s;
+    }
+    const Cmp e = pi[m] * f_exp(-s);
+    env += e;
+    Cmp g2 = 0;
+    for (int c = 0; c < 3; ++c) { ge[c] -= e * gs[c]; g2 += gs[c] * gs[c]; }
+    le += e * (g2 - ls);
+  }
+  *env_out = env;
+  *le_out = le;
+}
+
+// Envelope-derivative terms of the tensor-core orbital pass: on the slabs of the row's own
+// coordinates phi += P_0 d_c env, on the Laplacian slab phi += 2 sum_c P_c d_c env + P_0 lap env.
+template <typename PhiT, typename Wlk>
+__global__ void k_orbital_fixup(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh, OrbArgs a,
+                                const float* __restrict__ orbP) {
+  const int w = blockIdx.x / sh.N, j = blockIdx.x % sh.N;
+  const int spin = j < sh.n_up ? 0 : 1;
+  const int n_s = spin ? sh.n_dn : sh.n_up;
+  const int ko = threadIdx.x;
+  if (ko >= a.K * n_s) return;
+  const int jj = j - (spin ? sh.n_up : 0);
+  const int64_t row = tile_row(w, j, sh.N, sh.wpt);
+  const int ldp = a.K * sh.N, poff = spin ? a.K * sh.n_up : 0;
+  float env, ge[3], le;
+  env_jet<float, Wlk>(a, spin, ko, r + ((int64_t)w * sh.N + j) * 3, nuc, sh.M, &env, ge, &le);
+  const float* pr = orbP + row * 4 * ldp + poff + ko;
+  const float P0 = pr[0];
+  const int k = ko / n_s, i = ko % n_s;
+  const int64_t nn = (int64_t)n_s * n_s;
+  PhiT* base = (PhiT*)a.Phi + (int64_t)w * a.PW + (spin ? (int64_t)a.K * sh.T * sh.n_up * sh.n_up : 0) +
+               (int64_t)k * sh.T * nn + i * n_s + jj;
+  float lap = P0 * le;
+  for (int c = 0; c < 3; ++c) {
+    base[(1 + 3 * j + c) * nn] += (PhiT)(P0 * ge[c]);
+    lap += 2.f * pr[(1 + c) * ldp] * ge[c];
+  }
+  base[(sh.T - 1) * nn] += (PhiT)lap;
+}
+
+template <typename Act, typename Cmp, typename PhiT, typename Wlk, bool FULL>
 __global__ void k_orbitals(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh, OrbArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cmp* hs = (Cmp*)smem_raw;     // [h1]
@@ -514,38 +599,9 @@ __global__ void k_orbitals(const Wlk* __restrict__ r, const double* __restrict__
   // envelope value, gradient along r_j and Laplacian
   Cmp env = 0, ge[3] = {0, 0, 0}, le = 0;
   const Wlk* rj = r + ((int64_t)w * sh.N + j) * 3;
-  if (active) {
-    const Cmp* pi = (const Cmp*)a.pi[spin] + (int64_t)ko * sh.M;
-    for (int m = 0; m < sh.M; ++m) {
-      const Cmp d[3] = {(Cmp)((double)rj[0] - nuc[3 * m]), (Cmp)((double)rj[1] - nuc[3 * m + 1]),
-                        (Cmp)((double)rj[2] - nuc[3 * m + 2])};
-      Cmp s, gs[3], ls;
-      if (!a.aniso) {
-        const Cmp sg = ((const Cmp*)a.sig[spin])[(int64_t)ko * sh.M + m];
-        const Cmp dist = f_sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        s = sg * dist;
-        for (int c = 0; c < 3; ++c) gs[c] = sg * d[c] / dist;
-        ls = (Cmp)2 * sg / dist;
-      } else {
-        const Cmp* S = (const Cmp*)a.sig[spin] + ((int64_t)ko * sh.M + m) * 9;
-        Cmp u[3];
-        for (int x = 0; x < 3; ++x) u[x] = S[3 * x] * d[0] + S[3 * x + 1] * d[1] + S[3 * x + 2] * d[2];
-        s = f_sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        Cmp stu[3], frob = 0, n2 = 0;
-        for (int y = 0; y < 3; ++y) stu[y] = S[y] * u[0] + S[3 + y] * u[1] + S[6 + y] * u[2];
-        for (int q = 0; q < 9; ++q) frob += S[q] * S[q];
-        for (int y = 0; y < 3; ++y) { gs[y] = stu[y] / s; n2 += stu[y] * stu[y]; }
-        ls = (frob - n2 / (s * s)) / s;
-      }
-      const Cmp e = pi[m] * f_exp(-s);
-      env += e;
-      Cmp g2 = 0;
-      for (int c = 0; c < 3; ++c) { ge[c] -= e * gs[c]; g2 += gs[c] * gs[c]; }
-      le += e * (g2 - ls);
-    }
-  }
+  if (active) env_jet<Cmp, Wlk>(a, spin, ko, rj, nuc, sh.M, &env, ge, &le);
   const int k = active ? ko / n_s : 0, i = active ? ko % n_s : 0;
-  Det* out = (Det*)a.Phi + (int64_t)w * a.PW +
+  PhiT* out = (PhiT*)a.Phi + (int64_t)w * a.PW +
              (spin ? (int64_t)a.K * sh.T * sh.n_up * sh.n_up : 0) + (int64_t)k * sh.T * n_s * n_s +
              (int64_t)i * n_s + jj;
   const int64_t tstride = (int64_t)n_s * n_s;
@@ -569,7 +625,7 @@ __global__ void k_orbitals(const Wlk* __restrict__ r, const double* __restrict__
       } else {
         phi = p * env + (Cmp)2 * (pj[0] * ge[0] + pj[1] * ge[1] + pj[2] * ge[2]) + p0 * le;
       }
-      out[t * tstride] = (Det)phi;
+      out[t * tstride] = (PhiT)phi;
     }
     __syncthreads();
   }
@@ -594,7 +650,7 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     k_features_en<Act, Wlk><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(r, s->d_nuclei, sh, (Act*)ws.X[0],
                                                                            s->layer[0].ldx);
     const int64_t m = (int64_t)sh.B * 2 * sh.M;
-    k_features_mean<Cmp, Wlk><<<(unsigned)((m + 127) / 128), 128, 0, st>>>(r, s->d_nuclei, sh, (Cmp*)ws.Hbar[0]);
+    k_features_mean<Act, Wlk><<<(unsigned)((m + 127) / 128), 128, 0, st>>>(r, s->d_nuclei, sh, (Act*)ws.Hbar[0]);
   }
   {
     PairArgs pa{};
@@ -608,16 +664,16 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
       if (l < L - 1) { pa.W[l] = prep + s->prep.W[l]; pa.c[l] = prep + s->prep.c[l]; }
       pa.gstore[l] = (keep && l >= 1) ? ws.gpair[l] : nullptr;
     }
-    const size_t wbytes = sizeof(Cmp) * ((kMaxLayers - 1) * kMaxH2 * kMaxH2 + (kMaxLayers - 1) * kMaxH2);
+    const size_t wbytes = sizeof(Cmp) * ((L - 1) * kMaxH2 * kMaxH2 + (L - 1) * kMaxH2);
     ProfScope ps(s->prof, kProfPair, st);
     if (full) {
-      const size_t smem = wbytes + sizeof(Cmp) * L * 2 * 5 * kMaxH2;
+      const size_t smem = wbytes + sizeof(Cmp) * sh.N * 8 * 33;
       const int threads = (int)round_up(8 * sh.N, 32);
       cudaFuncSetAttribute(k_pair_full<Act, Cmp, Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_pair_full<Act, Cmp, Wlk><<<(unsigned)((int64_t)sh.B * sh.N), threads, smem, st>>>(r, sh, pa);
     } else {
-      const size_t smem = wbytes + sizeof(Cmp) * L * sh.N * 2 * kMaxH2;
-      const int threads = (int)std::min<int64_t>(256, round_up((int64_t)sh.N * sh.N, 32));
+      const size_t smem = wbytes + sizeof(Cmp) * sh.N * sh.N * 33;
+      const int threads = (int)std::min<int64_t>(512, round_up((int64_t)sh.N * sh.N, 32));
       cudaFuncSetAttribute(k_pair_value<Act, Cmp, Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_pair_value<Act, Cmp, Wlk><<<(unsigned)sh.B, threads, smem, st>>>(r, sh, pa);
     }
@@ -625,11 +681,18 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
   for (int l = 0; l < L; ++l) {
     const LayerDims& d = s->layer[l];
     // mean-field term M = Hbar_l U_l^T + b_l (bias on the value slab only)
-    const Cmp* Hb = (const Cmp*)ws.Hbar[l];
+    const Act* Hb = (const Act*)ws.Hbar[l];
     {
-    ProfScope ps(s->prof, kProfMeanGemm, st);
-    gemm<Cmp, Cmp, Cmp, Cmp>(st, sh.T * sh.B, h1, 2 * d.d_h, Hb, 2 * d.d_h, 1, prep + s->prep.UT[l], h1, 1,
-                             (Cmp*)ws.Mterm, h1, 1, prep + s->prep.b[l], sh.B, 1, false);
+      ProfScope ps(s->prof, kProfMeanGemm, st);
+      if (Mode::kMode == FN_BF16_MIXED) {
+        const __nv_bfloat16* U16 = (const __nv_bfloat16*)ws.prep16 + s->prep.U16[l];
+        if (!launch_gemm_tc(sh.T * sh.B, 2 * d.d_h, Hb, 2 * d.d_h, U16, 2 * d.d_h, h1, (float*)ws.Mterm,
+                            (const float*)(prep + s->prep.b[l]), sh.B, ws.status, st))
+          const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
+      } else {
+        gemm<Act, Cmp, Cmp, Cmp>(st, sh.T * sh.B, h1, 2 * d.d_h, Hb, 2 * d.d_h, 1, prep + s->prep.UT[l], h1, 1,
+                                 (Cmp*)ws.Mterm, h1, 1, prep + s->prep.b[l], sh.B, 1, false);
+      }
     }
     LayerArgs la{};
     la.X = ws.X[l]; la.ldx = d.ldx; la.k_self = d.k_self;
@@ -646,7 +709,7 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     if (Mode::kMode == FN_BF16_MIXED) {
       const __nv_bfloat16* Vs16 = (const __nv_bfloat16*)ws.prep16 + s->prep.Vs16[l];
       if (!launch_layer_tc(sh, la.X, la.ldx, la.k_self, Vs16, (const float*)la.Mterm, la.Y, la.ldy, la.residual,
-                           (float*)la.Hbar_out, (float*)la.act_out, h1, ws.status, st))
+                           la.Hbar_out, (float*)la.act_out, h1, ws.status, st))
         const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
       continue;
     }
@@ -672,11 +735,27 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     oa.h1 = h1; oa.K = s->cfg.n_dets; oa.aniso = s->cfg.envelope == FN_ENV_ANISOTROPIC;
     const int ko_max = s->cfg.n_dets * std::max(s->n_up, s->n_dn);
     const int threads = (int)std::min<int64_t>(1024, round_up(ko_max, 32));
+    ProfScope ps(s->prof, full ? kProfOrbFull : kProfOrbValue, st);
+    if (Mode::kMode == FN_BF16_MIXED) {
+      const float* wb[2] = {(const float*)oa.g[0], (const float*)oa.g[1]};
+      const float* pis[2] = {(const float*)oa.pi[0], (const float*)oa.pi[1]};
+      const float* sgs[2] = {(const float*)oa.sig[0], (const float*)oa.sig[1]};
+      if (!launch_orbitals_tc(sh, ws.HL, h1, (const __nv_bfloat16*)ws.prep16 + s->prep.W16, wb, pis, sgs,
+                              s->cfg.n_dets, oa.aniso, (const float*)walkers, s->d_nuclei, ws.Phi, oa.PW, ws.orbP,
+                              ws.status, st))
+        const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
+      if (full) {
+        const int ko_max = s->cfg.n_dets * std::max(s->n_up, s->n_dn);
+        k_orbital_fixup<typename Mode::PhiT, Wlk><<<(unsigned)((int64_t)sh.B * sh.N), (unsigned)round_up(ko_max, 32), 0,
+                                                    st>>>(r, s->d_nuclei, sh, oa, ws.orbP);
+      }
+      return;
+    }
     const size_t smem = sizeof(Cmp) * h1;
     const unsigned blocks = (unsigned)((int64_t)sh.B * sh.N);
-    ProfScope ps(s->prof, full ? kProfOrbFull : kProfOrbValue, st);
-    if (full) k_orbitals<Act, Cmp, Det, Wlk, true><<<blocks, threads, smem, st>>>(r, s->d_nuclei, sh, oa);
-    else k_orbitals<Act, Cmp, Det, Wlk, false><<<blocks, threads, smem, st>>>(r, s->d_nuclei, sh, oa);
+    using PhiT = typename Mode::PhiT;
+    if (full) k_orbitals<Act, Cmp, PhiT, Wlk, true><<<blocks, threads, smem, st>>>(r, s->d_nuclei, sh, oa);
+    else k_orbitals<Act, Cmp, PhiT, Wlk, false><<<blocks, threads, smem, st>>>(r, s->d_nuclei, sh, oa);
   }
 }
 

@@ -47,14 +47,17 @@ constexpr int kStatusTimeout = 4;
 // stage; Wlk: walker coordinates; Par: parameter blob.
 struct ModeF64 {
   using Act = double; using Cmp = double; using Det = double; using Wlk = double; using Par = double;
+  using PhiT = double;
   static constexpr fn_precision kMode = FN_FP64;
 };
 struct ModeF32 {
   using Act = float; using Cmp = float; using Det = float; using Wlk = float; using Par = float;
+  using PhiT = float;
   static constexpr fn_precision kMode = FN_FP32;
 };
 struct ModeBF16 {
   using Act = __nv_bfloat16; using Cmp = float; using Det = double; using Wlk = float; using Par = float;
+  using PhiT = float;          // orbital matrices stored in FP32, factorised in FP64
   static constexpr fn_precision kMode = FN_BF16_MIXED;
 };
 
@@ -91,7 +94,10 @@ struct PrepLayout {
   int64_t pi[2];             // [K n_s][M]
   int64_t sig[2];            // [K n_s][M] or [K n_s][M][9]
   int64_t total;
-  int64_t Vs16[kMaxLayers];  // bf16 [h1][ldx_l] self part of V, K contiguous (BF16 mode)
+  // BF16 mode, each a [rows][2 ld] matrix: bf16(W) in columns [0, k), bf16(W - bf16(W)) from column ld
+  int64_t Vs16[kMaxLayers];  // self part of V, rows h1, ld = ldx_l
+  int64_t U16[kMaxLayers];   // mean-field part of V, rows h1, ld = 2 d_h
+  int64_t W16;               // orbital projections, rows K (n_up + n_dn) (up block first), ld = h1
   int64_t total16;
 };
 
@@ -100,7 +106,7 @@ struct CopyDesc {
   int64_t src, s_rs, s_cs;   // source offset and strides (row, col) in the blob
   int64_t dst, d_rs, d_cs;   // destination offset and strides
   int rows, cols;
-  int to16;                  // 1: destination is the bf16 array
+  int to16;                  // 0: Cmp array; 1: bf16 array, bf16(v); 2: bf16 array, bf16(v - bf16(v))
 };
 
 struct Workspace {
@@ -110,9 +116,9 @@ struct Workspace {
   // carved pointers (valid for cap_B walkers, full T)
   void* X[kMaxLayers] = {};
   void* HL = nullptr;            // last layer output [T][R][h1] (Act)
-  void* Hbar[kMaxLayers] = {};   // [T][B][2 d_h] (Cmp)
+  void* Hbar[kMaxLayers] = {};   // [T][B][2 d_h] (Act)
   void* Mterm = nullptr;         // [T][B][h1] (Cmp)
-  void* Phi = nullptr;           // [B][per-walker orbital block] (Det)
+  void* Phi = nullptr;           // [B][per-walker orbital block] (PhiT)
   void* prep = nullptr;          // prepared params (Cmp)
   void* prep16 = nullptr;        // bf16 weights
   void* walk2 = nullptr;         // proposal walkers [B][N][3] (Wlk)
@@ -130,6 +136,7 @@ struct Workspace {
   void* dPhi = nullptr;          // [B][orbital block, value slab] (Det)
   void* gradc = nullptr;         // prepared-layout gradient accumulator (Cmp)
   void* dP = nullptr;            // [R][K (n_up + n_dn)] gradient wrt orbital projections (Cmp)
+  float* orbP = nullptr;         // [R][4][K N] projections for the orbital envelope fix-up (BF16 mode)
   int* status = nullptr;         // device status word
   int64_t* counter = nullptr;    // scratch counter
 };
@@ -170,7 +177,12 @@ fn_status upload_prep_descs(fn_system* s);
 
 // Tensor-core one-electron layer (BF16 mode); false if a TMA tensor map could not be built.
 bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const void* Vs16, const float* Mterm, void* Y,
-                     int ldy, int residual, float* Hbar_out, float* act_out, int h1, int* status, cudaStream_t st);
+                     int ldy, int residual, void* Hbar_out, float* act_out, int h1, int* status, cudaStream_t st);
+bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int ldb, int h1, float* C,
+                    const float* bias, int bias_rows, int* status, cudaStream_t st);
+bool launch_orbitals_tc(const Shape& sh, const void* HL, int h1, const void* W16, const float* const* wbias,
+                        const float* const* pi, const float* const* sig, int K, int aniso, const float* walkers,
+                        const double* nuclei, void* Phi, int64_t PW, float* orbP, int* status, cudaStream_t st);
 bool tc_available();
 
 // Shapes and sizes

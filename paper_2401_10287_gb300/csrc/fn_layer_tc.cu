@@ -27,7 +27,7 @@
 namespace fn {
 namespace tc {
 
-constexpr int kStages = 4;
+constexpr int kStages = 3;
 constexpr int kBlockK = 64;                     // bf16 elements per 128-byte swizzled row
 constexpr int kThreads = 192;
 constexpr uint64_t kWaitNs = 1000000000ull;     // 1 s per wait
@@ -153,33 +153,268 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+enum { kEpiLayer = 0, kEpiPlain = 1, kEpiOrbital = 2 };
+
 struct TcArgs {
   Shape sh;
   int nkb;               // k-blocks of 64
   int nt;                // output columns per CTA (32, 64 or 128)
   int h1;
+  int* status;
+  uint32_t tmem_cols;
+  // layer epilogue
   const float* Mterm;    // [T][B][h1]
   const __nv_bfloat16* X; int ldx;    // input (residual source)
   __nv_bfloat16* Y; int ldy;          // output
   int residual;
-  float* Hbar_out;       // [T][B][2 h1] or null
+  __nv_bfloat16* Hbar_out;            // [T][B][2 h1] or null
   float* act_out;        // [R][h1] or null
-  int* status;
-  uint32_t tmem_cols;
+  // plain epilogue: C[row][col] = acc + bias[col] (rows < bias_rows)
+  int rows; float* C; int ldc; const float* bias; int bias_rows;
+  // orbital epilogue
+  const float* wbias[2];              // orbital bias g, [K n_s]
+  const float* pi[2]; const float* sig[2];
+  const float* walkers;               // [B][N][3]
+  const double* nuclei;
+  int K, aniso, ctiles_up;            // column tiles of the up block
+  float* Phi; int64_t PW;             // [B][PW] (float)
+  float* orbP;                        // [R][4][K N]: value projection and the row's own-coordinate ones
+  // split weights: columns [0, k) hold bf16(W), columns [bsplit, bsplit + k) hold
+  // bf16(W - bf16(W)); every k-block is multiplied by both (0 = no split)
+  int bsplit;
 };
 
+struct Smem {
+  unsigned char* sA; unsigned char* sB; float* ep;
+  uint64_t *full, *empty, *accf, *acce, *mma_done;
+  uint32_t* tmem_slot; volatile int* abort_flag;
+};
+
+// ---- epilogue: stream layer ------------------------------------------------------------
 template <bool FULL>
+__device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, int r, int ethread, uint32_t tmem,
+                                          uint32_t lane_base, int buf, int n0, int tile, float* ys) {
+  const Shape& sh = a.sh;
+  const int nt = a.nt, T = sh.T;
+  const int64_t row = (int64_t)tile * 128 + r;
+  const int wl = r / sh.N;
+  const int w = tile * sh.wpt + wl;
+  const bool valid = wl < sh.wpt && w < sh.B;
+  const int64_t xslab = sh.R * a.ldx, yslab = sh.R * a.ldy;
+  const int col0 = n0 + cc * 32;
+  uint32_t acc[32], hv[32], sq[32];
+  tmem_ld32(tmem + lane_base + (uint32_t)(buf * nt + cc * 32), acc);
+  if (FULL && t > 0) {
+    tmem_ld32(tmem + lane_base + (uint32_t)(2 * nt + cc * 32), hv);
+    tmem_ld32(tmem + lane_base + (uint32_t)(3 * nt + cc * 32), sq);
+  }
+  const bool live = valid && col0 < a.h1;
+  float out[32];
+  if (live) {
+    const float4* mt = (const float4*)(a.Mterm + ((int64_t)t * sh.B + w) * a.h1 + col0);
+    float mv[32];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const float4 m4 = mt[v];
+      mv[4 * v] = m4.x; mv[4 * v + 1] = m4.y; mv[4 * v + 2] = m4.z; mv[4 * v + 3] = m4.w;
+    }
+    float res[32];
+    if (a.residual) {
+      const uint4* xr = (const uint4*)(a.X + t * xslab + row * a.ldx + col0);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const uint4 u = xr[v];
+        const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = __bfloat1622float2(p2[e]);
+          res[8 * v + 2 * e] = f.x;
+          res[8 * v + 2 * e + 1] = f.y;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float z = __uint_as_float(acc[j]) + mv[j];
+      float o;
+      if (t == 0) {
+        const float h = tanhf(z);
+        hv[j] = __float_as_uint(h);
+        sq[j] = 0u;
+        o = h;
+      } else {
+        const float h = __uint_as_float(hv[j]);
+        const float d = 1.0f - h * h;
+        if (t < T - 1) {
+          o = d * z;
+          sq[j] = __float_as_uint(__uint_as_float(sq[j]) + z * z);
+        } else {
+          o = d * z - 2.0f * h * d * __uint_as_float(sq[j]);
+        }
+      }
+      out[j] = a.residual ? o + res[j] : o;
+    }
+    uint4* yo = (uint4*)(a.Y + t * yslab + row * a.ldy + col0);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      uint4 u;
+      __nv_bfloat162* p2 = (__nv_bfloat162*)&u;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(out[8 * v + 2 * e], out[8 * v + 2 * e + 1]);
+      yo[v] = u;
+    }
+    if (t == 0 && a.act_out) {
+      float4* ao = (float4*)(a.act_out + row * a.h1 + col0);
+#pragma unroll
+      for (int v = 0; v < 8; ++v)
+        ao[v] = make_float4(__uint_as_float(hv[4 * v]), __uint_as_float(hv[4 * v + 1]), __uint_as_float(hv[4 * v + 2]),
+                            __uint_as_float(hv[4 * v + 3]));
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) { out[j] = 0.f; hv[j] = 0u; sq[j] = 0u; }
+  }
+  if (FULL) {
+    if (t == 0) {
+      tmem_st32(tmem + lane_base + (uint32_t)(2 * nt + cc * 32), hv);
+      tmem_st32(tmem + lane_base + (uint32_t)(3 * nt + cc * 32), sq);
+    } else if (t < T - 1) {
+      tmem_st32(tmem + lane_base + (uint32_t)(3 * nt + cc * 32), sq);
+    }
+    tmem_wait_st();
+  }
+  if (a.Hbar_out && col0 < a.h1) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) ys[r * 33 + j] = out[j];
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    for (int e = ethread; e < sh.wpt * 2 * 32; e += 128) {
+      const int wl2 = e / 64, s = (e / 32) & 1, j = e & 31;
+      const int w2 = tile * sh.wpt + wl2;
+      if (w2 >= sh.B) continue;
+      const int lo = s ? sh.n_up : 0, hi = s ? sh.N : sh.n_up;
+      float sum = 0.f;
+      for (int i = lo; i < hi; ++i) sum += ys[(wl2 * sh.N + i) * 33 + j];
+      a.Hbar_out[((int64_t)t * sh.B + w2) * 2 * a.h1 + s * a.h1 + col0 + j] =
+          __float2bfloat16_rn(hi > lo ? sum / (float)(hi - lo) : 0.f);
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+  }
+}
+
+// ---- epilogue: plain GEMM with bias ----------------------------------------------------
+__device__ __forceinline__ void epi_plain(const TcArgs& a, int cc, int r, uint32_t tmem, uint32_t lane_base, int buf,
+                                          int n0, int tile) {
+  const int64_t row = (int64_t)tile * 128 + r;
+  const int col0 = n0 + cc * 32;
+  uint32_t acc[32];
+  tmem_ld32(tmem + lane_base + (uint32_t)(buf * a.nt + cc * 32), acc);
+  if (row >= a.rows || col0 >= a.h1) return;
+  const bool with_bias = a.bias && row < a.bias_rows;
+  float4* co = (float4*)(a.C + row * a.ldc + col0);
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    float o[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) o[e] = __uint_as_float(acc[4 * v + e]) + (with_bias ? a.bias[col0 + 4 * v + e] : 0.f);
+    co[v] = make_float4(o[0], o[1], o[2], o[3]);
+  }
+}
+
+// envelope value sum_m pi exp(-s_m) of orbital ko at r_j (value only, inlined).
+__device__ __forceinline__ float envelope_value(const TcArgs& a, int spin, int ko, float r0, float r1, float r2) {
+  const int M = a.sh.M;
+  const float* pi = a.pi[spin] + (int64_t)ko * M;
+  float e = 0.f;
+  for (int m = 0; m < M; ++m) {
+    const float d0 = (float)((double)r0 - a.nuclei[3 * m]), d1 = (float)((double)r1 - a.nuclei[3 * m + 1]),
+                d2 = (float)((double)r2 - a.nuclei[3 * m + 2]);
+    float s;
+    if (!a.aniso) {
+      s = a.sig[spin][(int64_t)ko * M + m] * sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    } else {
+      const float* S = a.sig[spin] + ((int64_t)ko * M + m) * 9;
+      const float u0 = S[0] * d0 + S[1] * d1 + S[2] * d2;
+      const float u1 = S[3] * d0 + S[4] * d1 + S[5] * d2;
+      const float u2 = S[6] * d0 + S[7] * d1 + S[8] * d2;
+      s = sqrtf(u0 * u0 + u1 * u1 + u2 * u2);
+    }
+    e += pi[m] * __expf(-s);
+  }
+  return e;
+}
+
+// ---- epilogue: orbitals x envelope, common product term ------------------------------------
+// phi_t = P_t env for every slab (P_0 includes the orbital bias).  The envelope-derivative
+// terms (own-coordinate slabs and the Laplacian) are added by k_orbital_fixup from the value
+// projection P_0 and the own-coordinate projections, stored here with predicated stores.
+// TMEM columns: [0, 2 nt) accumulators, [2 nt, 3 nt) envelope value.
+template <bool FULL>
+__device__ __forceinline__ void epi_orbital(const TcArgs& a, int t, int cc, int r, uint32_t tmem, uint32_t lane_base,
+                                            int buf, int spin, int ko0, int tile) {
+  const Shape& sh = a.sh;
+  const int nt = a.nt, T = sh.T;
+  const int wl = r / sh.N, j = r % sh.N;
+  const int w = tile * sh.wpt + wl;
+  const int n_s = spin ? sh.n_dn : sh.n_up;
+  const int n_ko = a.K * n_s;
+  const bool valid = wl < sh.wpt && w < sh.B && (j < sh.n_up ? 0 : 1) == spin;
+  const int jj = j - (spin ? sh.n_up : 0);
+  const int colb = cc * 32;
+  uint32_t acc[32], ev[32];
+  tmem_ld32(tmem + lane_base + (uint32_t)(buf * nt + colb), acc);
+  if (t > 0) tmem_ld32(tmem + lane_base + (uint32_t)(2 * nt + colb), ev);
+  const int own_c = (t >= 1 && t <= 3 * sh.N && (t - 1) / 3 == j) ? (t - 1) % 3 : -1;
+  const int64_t row = (int64_t)tile * 128 + r;
+  const int ldp = a.K * sh.N;
+  float* orbp = a.orbP + row * 4 * ldp + (spin ? a.K * sh.n_up : 0);
+  const int64_t nn = (int64_t)n_s * n_s;
+  float* Phi = a.Phi + (int64_t)w * a.PW + (spin ? (int64_t)a.K * T * sh.n_up * sh.n_up : 0) + t * nn + jj;
+  float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+  if (valid && t == 0) {
+    const float* rp = a.walkers + ((int64_t)w * sh.N + j) * 3;
+    r0 = rp[0]; r1 = rp[1]; r2 = rp[2];
+  }
+  int k = (ko0 + colb) / (n_s ? n_s : 1), i = (ko0 + colb) - k * n_s;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    const int ko = ko0 + colb + q;
+    if (valid && ko < n_ko) {
+      float P = __uint_as_float(acc[q]);
+      float e;
+      if (t == 0) {
+        P += a.wbias[spin][ko];
+        e = envelope_value(a, spin, ko, r0, r1, r2);
+        ev[q] = __float_as_uint(e);
+        if (FULL) orbp[ko] = P;
+      } else {
+        e = __uint_as_float(ev[q]);
+        if (own_c >= 0) orbp[(1 + own_c) * ldp + ko] = P;
+      }
+      Phi[(int64_t)k * T * nn + i * n_s] = P * e;
+    } else if (t == 0) {
+      ev[q] = 0u;
+    }
+    if (++i == n_s) { i = 0; ++k; }
+  }
+  if (t == 0 && FULL) {
+    tmem_st32(tmem + lane_base + (uint32_t)(2 * nt + colb), ev);
+    tmem_wait_st();
+  }
+}
+
+template <int EPI, bool FULL>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_layer_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+    k_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned carve-up
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int nt = a.nt;
+  const int nbparts = a.bsplit ? 2 : 1;                       // B_hi (and B_lo) per stage
   const uint32_t bytesA = 128 * 128, bytesB = (uint32_t)nt * 128;
   unsigned char* sA = base;                                   // kStages x 16 KB
-  unsigned char* sB = sA + kStages * bytesA;                  // kStages x nt*128
-  float* ys = (float*)(sB + kStages * bytesB);                // [128][33]
-  uint64_t* bars = (uint64_t*)(ys + 128 * 33);                // full[S], empty[S], accf[2], acce[2]
+  unsigned char* sB = sA + kStages * bytesA;                  // kStages x nbparts x nt*128
+  float* ep = (float*)(sB + kStages * nbparts * bytesB);      // epilogue staging
+  const size_t ep_floats = EPI == kEpiLayer ? 128 * 33 : 0;
+  uint64_t* bars = (uint64_t*)(ep + ep_floats);
   uint64_t* full = bars;
   uint64_t* empty = bars + kStages;
   uint64_t* accf = bars + 2 * kStages;
@@ -190,8 +425,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Shape& sh = a.sh;
-  const int tile = blockIdx.x, n0 = blockIdx.y * nt;
-  const int T = sh.T, nkb = a.nkb;
+  // blockIdx.x runs over the column tiles (fastest), so the CTAs that share an A tile run together
+  const int tile = blockIdx.y, ctile = blockIdx.x;
+  // column tile: for orbitals it selects (spin, tile within the spin block)
+  int spin = 0, ko0 = 0, brow0 = ctile * nt;
+  if (EPI == kEpiOrbital) {
+    spin = ctile >= a.ctiles_up ? 1 : 0;
+    ko0 = (spin ? ctile - a.ctiles_up : ctile) * nt;
+    brow0 = (spin ? a.K * sh.n_up : 0) + ko0;
+  }
+  const int T = EPI == kEpiPlain ? 1 : sh.T;
+  const int nkb = a.nkb;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
@@ -210,29 +454,31 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint64_t deadline = globaltimer() + kWaitNs * 8;   // whole-CTA budget; each wait checks it
+  const uint64_t deadline = globaltimer() + kWaitNs * 8;
 
   if (warp == 0) {
     if (lane == 0) {
       int issued = 0;
       bool ok = true;
       for (int t = 0; t < T && ok; ++t) {
+        const int arow = EPI == kEpiPlain ? tile * 128 : (int)(t * sh.R + (int64_t)tile * 128);
         for (int kb = 0; kb < nkb; ++kb, ++issued) {
           const int stage = issued % kStages;
           const uint32_t round = (uint32_t)(issued / kStages);
           if (*abort_flag || !mbar_wait(empty + stage, (round & 1u) ^ 1u, deadline)) { ok = false; break; }
-          mbar_expect_tx(full + stage, bytesA + bytesB);
-          tma_load_2d(sA + stage * bytesA, &tmA, full + stage, kb * kBlockK, (int)(t * sh.R + (int64_t)tile * 128));
-          tma_load_2d(sB + stage * bytesB, &tmB, full + stage, kb * kBlockK, n0);
+          mbar_expect_tx(full + stage, bytesA + nbparts * bytesB);
+          tma_load_2d(sA + stage * bytesA, &tmA, full + stage, kb * kBlockK, arow);
+          for (int part = 0; part < nbparts; ++part)
+            tma_load_2d(sB + (stage * nbparts + part) * bytesB, &tmB, full + stage, part * a.bsplit + kb * kBlockK,
+                        brow0);
         }
       }
       if (!ok) {
         *abort_flag = 1;
         atomicOr(a.status, kStatusTimeout);
       }
-      // drain: every armed stage must have received its bytes before shared memory is released
       const uint64_t dl2 = globaltimer() + kWaitNs;
-      for (int q = std::max(0, issued - kStages); q < issued; ++q)
+      for (int q = issued > kStages ? issued - kStages : 0; q < issued; ++q)
         mbar_wait(full + (q % kStages), (uint32_t)((q / kStages) & 1), dl2);
     }
   } else if (warp == 1) {
@@ -252,10 +498,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (*abort_flag || !mbar_wait(full + stage, round & 1u, deadline)) { ok = false; break; }
           fence_after();
           const uint64_t da = sdesc(smem_u32(sA + stage * bytesA));
-          const uint64_t db = sdesc(smem_u32(sB + stage * bytesB));
+          for (int part = 0; part < nbparts; ++part) {
+            const uint64_t db = sdesc(smem_u32(sB + (stage * nbparts + part) * bytesB));
 #pragma unroll
-          for (int k4 = 0; k4 < kBlockK / 16; ++k4)
-            mma_bf16(d, da + (uint64_t)(2 * k4), db + (uint64_t)(2 * k4), idesc, (kb | k4) != 0 ? 1u : 0u);
+            for (int k4 = 0; k4 < kBlockK / 16; ++k4)
+              mma_bf16(d, da + (uint64_t)(2 * k4), db + (uint64_t)(2 * k4), idesc, (kb | k4 | part) != 0 ? 1u : 0u);
+          }
           mma_commit(empty + stage);
         }
         if (ok) mma_commit(accf + buf);
@@ -264,21 +512,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         *abort_flag = 1;
         atomicOr(a.status, kStatusTimeout);
       }
-      // every MMA issued by this thread has completed before tensor memory is released
       mma_commit(mma_done);
       mbar_wait(mma_done, 0u, globaltimer() + kWaitNs);
     }
   } else {
-    // epilogue: thread = TMEM lane = row of the tile
     const int q = warp & 3;
     const int r = q * 32 + lane;
-    const int64_t row = (int64_t)tile * 128 + r;
-    const int wl = r / sh.N;
-    const int w = tile * sh.wpt + wl;
-    const bool valid = wl < sh.wpt && w < sh.B;
-    const int ethread = threadIdx.x - 64;        // 0..127 across the four epilogue warps
+    const int ethread = threadIdx.x - 64;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    const int64_t xslab = sh.R * a.ldx, yslab = sh.R * a.ldy;
     for (int t = 0; t < T; ++t) {
       const int buf = t & 1;
       const uint32_t use = (uint32_t)(t >> 1);
@@ -292,103 +533,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       fence_after();
       for (int cc = 0; cc < nt / 32; ++cc) {
-        const int col0 = n0 + cc * 32;
-        uint32_t acc[32], hv[32], sq[32];
-        tmem_ld32(tmem + lane_base + (uint32_t)(buf * nt + cc * 32), acc);
-        if (FULL && t > 0) {
-          tmem_ld32(tmem + lane_base + (uint32_t)(2 * nt + cc * 32), hv);
-          tmem_ld32(tmem + lane_base + (uint32_t)(3 * nt + cc * 32), sq);
-        }
-        const bool live = valid && col0 < a.h1;
-        float out[32];
-        if (live) {
-          const float4* mt = (const float4*)(a.Mterm + ((int64_t)t * sh.B + w) * a.h1 + col0);
-          float mv[32];
-#pragma unroll
-          for (int v = 0; v < 8; ++v) {
-            const float4 m4 = mt[v];
-            mv[4 * v] = m4.x; mv[4 * v + 1] = m4.y; mv[4 * v + 2] = m4.z; mv[4 * v + 3] = m4.w;
-          }
-          float res[32];
-          if (a.residual) {
-            const uint4* xr = (const uint4*)(a.X + t * xslab + row * a.ldx + col0);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              const uint4 u = xr[v];
-              const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u;
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const float2 f = __bfloat1622float2(p2[e]);
-                res[8 * v + 2 * e] = f.x;
-                res[8 * v + 2 * e + 1] = f.y;
-              }
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float z = __uint_as_float(acc[j]) + mv[j];
-            float o;
-            if (t == 0) {
-              const float h = tanhf(z);
-              hv[j] = __float_as_uint(h);
-              sq[j] = 0u;
-              o = h;
-            } else {
-              const float h = __uint_as_float(hv[j]);
-              const float d = 1.0f - h * h;
-              if (t < T - 1) {
-                o = d * z;
-                sq[j] = __float_as_uint(__uint_as_float(sq[j]) + z * z);
-              } else {
-                o = d * z - 2.0f * h * d * __uint_as_float(sq[j]);
-              }
-            }
-            out[j] = a.residual ? o + res[j] : o;
-          }
-          uint4* yo = (uint4*)(a.Y + t * yslab + row * a.ldy + col0);
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            uint4 u;
-            __nv_bfloat162* p2 = (__nv_bfloat162*)&u;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(out[8 * v + 2 * e], out[8 * v + 2 * e + 1]);
-            yo[v] = u;
-          }
-          if (t == 0 && a.act_out) {
-            float4* ao = (float4*)(a.act_out + row * a.h1 + col0);
-#pragma unroll
-            for (int v = 0; v < 8; ++v)
-              ao[v] = make_float4(__uint_as_float(hv[4 * v]), __uint_as_float(hv[4 * v + 1]),
-                                  __uint_as_float(hv[4 * v + 2]), __uint_as_float(hv[4 * v + 3]));
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) { out[j] = 0.f; hv[j] = 0u; sq[j] = 0u; }
-        }
-        if (FULL) {
-          if (t == 0) {
-            tmem_st32(tmem + lane_base + (uint32_t)(2 * nt + cc * 32), hv);
-            tmem_st32(tmem + lane_base + (uint32_t)(3 * nt + cc * 32), sq);
-          } else if (t < T - 1) {
-            tmem_st32(tmem + lane_base + (uint32_t)(3 * nt + cc * 32), sq);
-          }
-          tmem_wait_st();
-        }
-        if (a.Hbar_out && col0 < a.h1) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) ys[r * 33 + j] = out[j];
-          asm volatile("bar.sync 1, 128;" ::: "memory");
-          for (int e = ethread; e < sh.wpt * 2 * 32; e += 128) {
-            const int wl2 = e / 64, s = (e / 32) & 1, j = e & 31;
-            const int w2 = tile * sh.wpt + wl2;
-            if (w2 >= sh.B) continue;
-            const int lo = s ? sh.n_up : 0, hi = s ? sh.N : sh.n_up;
-            float sum = 0.f;
-            for (int i = lo; i < hi; ++i) sum += ys[(wl2 * sh.N + i) * 33 + j];
-            a.Hbar_out[((int64_t)t * sh.B + w2) * 2 * a.h1 + s * a.h1 + col0 + j] = hi > lo ? sum / (float)(hi - lo) : 0.f;
-          }
-          asm volatile("bar.sync 1, 128;" ::: "memory");
-        }
+        if (EPI == kEpiLayer) epi_layer<FULL>(a, t, cc, r, ethread, tmem, lane_base, buf, ctile * nt, tile, ep);
+        else if (EPI == kEpiPlain) epi_plain(a, cc, r, tmem, lane_base, buf, ctile * nt, tile);
+        else epi_orbital<FULL>(a, t, cc, r, tmem, lane_base, buf, spin, ko0, tile);
       }
       fence_before();
       __syncwarp();
@@ -443,42 +590,111 @@ int tc_columns(int h1) {
   return 32;
 }
 
-size_t tc_smem_bytes(int nt) {
-  return 1024 + tc::kStages * (128 * 128 + (size_t)nt * 128) + 128 * 33 * sizeof(float) + 8 * (2 * tc::kStages + 5) + 16;
+static uint32_t pow2_cols(int c) {
+  uint32_t v = 32;
+  while ((int)v < c) v <<= 1;
+  return v;
 }
 
-// Launches the tensor-core layer; returns false (nothing launched) if a tensor map could not be built.
+static size_t tc_smem_bytes(int nt, int epi, bool split) {
+  const size_t ep = epi == tc::kEpiLayer ? 128 * 33 * 4 : 0;
+  return 1024 + tc::kStages * (128 * 128 + (size_t)nt * 128 * (split ? 2 : 1)) + ep + 8 * (2 * tc::kStages + 5) + 16;
+}
+
+template <int EPI>
+static void launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const tc::TcArgs& a, dim3 grid, bool full,
+                      cudaStream_t st) {
+  const size_t smem = tc_smem_bytes(a.nt, EPI, a.bsplit != 0);
+  if (full) {
+    cudaFuncSetAttribute(tc::k_tc<EPI, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    tc::k_tc<EPI, true><<<grid, tc::kThreads, smem, st>>>(ta, tb, a);
+  } else {
+    cudaFuncSetAttribute(tc::k_tc<EPI, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    tc::k_tc<EPI, false><<<grid, tc::kThreads, smem, st>>>(ta, tb, a);
+  }
+}
+
+// Stream layer on the tensor cores; returns false (nothing launched) if a tensor map could not be built.
 bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const void* Vs16, const float* Mterm, void* Y,
-                     int ldy, int residual, float* Hbar_out, float* act_out, int h1, int* status, cudaStream_t st) {
+                     int ldy, int residual, void* Hbar_out, float* act_out, int h1, int* status, cudaStream_t st) {
   const int nt = tc_columns(h1);
   CUtensorMap ta, tb;
   if (!make_map(&ta, X, k_self, (int64_t)sh.T * sh.R, ldx, 128)) return false;
-  if (!make_map(&tb, Vs16, k_self, h1, ldx, nt)) return false;
+  if (!make_map(&tb, Vs16, ldx + k_self, h1, 2 * ldx, nt)) return false;
   tc::TcArgs a{};
   a.sh = sh;
   a.nkb = (k_self + tc::kBlockK - 1) / tc::kBlockK;
   a.nt = nt;
   a.h1 = h1;
+  a.status = status;
   a.Mterm = Mterm;
   a.X = (const __nv_bfloat16*)X;
   a.ldx = ldx;
   a.Y = (__nv_bfloat16*)Y;
   a.ldy = ldy;
   a.residual = residual;
-  a.Hbar_out = Hbar_out;
+  a.Hbar_out = (__nv_bfloat16*)Hbar_out;
   a.act_out = act_out;
-  a.status = status;
+  a.bsplit = ldx;
   const bool full = sh.T > 1;
-  a.tmem_cols = (uint32_t)(full ? 4 * nt : std::max(32, 2 * nt));
-  const size_t smem = tc_smem_bytes(nt);
-  dim3 grid(sh.tiles, h1 / nt);
-  if (full) {
-    cudaFuncSetAttribute(tc::k_layer_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    tc::k_layer_tc<true><<<grid, tc::kThreads, smem, st>>>(ta, tb, a);
-  } else {
-    cudaFuncSetAttribute(tc::k_layer_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    tc::k_layer_tc<false><<<grid, tc::kThreads, smem, st>>>(ta, tb, a);
-  }
+  a.tmem_cols = pow2_cols(full ? 4 * nt : 2 * nt);
+  launch_tc<tc::kEpiLayer>(ta, tb, a, dim3(h1 / nt, sh.tiles), full, st);
+  return true;
+}
+
+// C[rows][h1] = A[rows][k] B[h1][k]^T + bias (rows < bias_rows); A, B bf16 K-major, C fp32.
+bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int ldb, int h1, float* C,
+                    const float* bias, int bias_rows, int* status, cudaStream_t st) {
+  const int nt = tc_columns(h1);
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, A, k, rows, lda, 128)) return false;
+  if (!make_map(&tb, Bw, ldb + k, h1, 2 * ldb, nt)) return false;
+  tc::TcArgs a{};
+  a.sh.T = 1;
+  a.nkb = (k + tc::kBlockK - 1) / tc::kBlockK;
+  a.nt = nt;
+  a.h1 = h1;
+  a.status = status;
+  a.rows = rows;
+  a.C = C;
+  a.ldc = h1;
+  a.bias = bias;
+  a.bias_rows = bias_rows;
+  a.bsplit = ldb;
+  a.tmem_cols = pow2_cols(2 * nt);
+  launch_tc<tc::kEpiPlain>(ta, tb, a, dim3(h1 / nt, (rows + 127) / 128), false, st);
+  return true;
+}
+
+// Orbitals: Phi (double) from h_L (bf16) and the bf16 orbital weights [K (n_up + n_dn)][h1].
+bool launch_orbitals_tc(const Shape& sh, const void* HL, int h1, const void* W16, const float* const* wbias,
+                        const float* const* pi, const float* const* sig, int K, int aniso, const float* walkers,
+                        const double* nuclei, void* Phi, int64_t PW, float* orbP, int* status, cudaStream_t st) {
+  const int nmax = std::max(sh.n_up, sh.n_dn);
+  const int nt = (int)std::min<int64_t>(128, round_up((int64_t)K * nmax, 32));
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, HL, h1, (int64_t)sh.T * sh.R, h1, 128)) return false;
+  if (!make_map(&tb, W16, 2 * h1, (int64_t)K * sh.N, 2 * h1, nt)) return false;
+  tc::TcArgs a{};
+  a.sh = sh;
+  a.nkb = (h1 + tc::kBlockK - 1) / tc::kBlockK;
+  a.nt = nt;
+  a.h1 = h1;
+  a.status = status;
+  for (int q = 0; q < 2; ++q) { a.wbias[q] = wbias[q]; a.pi[q] = pi[q]; a.sig[q] = sig[q]; }
+  a.walkers = walkers;
+  a.nuclei = nuclei;
+  a.K = K;
+  a.aniso = aniso;
+  a.ctiles_up = (K * sh.n_up + nt - 1) / nt;
+  const int ctiles_dn = (K * sh.n_dn + nt - 1) / nt;
+  a.Phi = (float*)Phi;
+  a.PW = PW;
+  a.orbP = orbP;
+  a.bsplit = h1;
+  const bool full = sh.T > 1;
+  a.tmem_cols = pow2_cols(3 * nt);
+  launch_tc<tc::kEpiOrbital>(ta, tb, a, dim3(a.ctiles_up + ctiles_dn, sh.tiles), full, st);
   return true;
 }
 

@@ -52,7 +52,7 @@ static fn_status scratch_address(void** out) {
 // Carves the value-pass buffers (T = 1) out of `base`; returns the bytes needed.
 template <class Mode>
 static size_t value_pass_layout(const fn_system* s, int B, unsigned char* base, Workspace* ws) {
-  using Act = typename Mode::Act; using Cmp = typename Mode::Cmp; using Det = typename Mode::Det;
+  using Act = typename Mode::Act; using Cmp = typename Mode::Cmp;
   const Shape sh = make_shape(s, B, 1);
   const int L = s->cfg.n_layers, h1 = s->cfg.h1;
   size_t off = 0;
@@ -64,11 +64,11 @@ static size_t value_pass_layout(const fn_system* s, int B, unsigned char* base, 
   size_t o_X[kMaxLayers], o_Hbar[kMaxLayers];
   for (int l = 0; l < L; ++l) {
     o_X[l] = take((size_t)sh.R * s->layer[l].ldx * sizeof(Act));
-    o_Hbar[l] = take((size_t)B * 2 * s->layer[l].d_h * sizeof(Cmp));
+    o_Hbar[l] = take((size_t)B * 2 * s->layer[l].d_h * sizeof(Act));
   }
   const size_t o_HL = take((size_t)sh.R * h1 * sizeof(Act));
   const size_t o_M = take((size_t)B * h1 * sizeof(Cmp));
-  const size_t o_Phi = take((size_t)B * phi_walker_stride(s, 1) * sizeof(Det));
+  const size_t o_Phi = take((size_t)B * phi_walker_stride(s, 1) * sizeof(typename Mode::PhiT));
   const size_t o_prep = take((size_t)s->prep.total * sizeof(Cmp));
   const size_t o_prep16 = take((size_t)s->prep.total16 * sizeof(__nv_bfloat16));
   const size_t o_status = take(sizeof(int) * 4);
