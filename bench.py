@@ -302,6 +302,9 @@ def run_mine(args):
     if not args.no_cpu_baseline and ws == 1:
         cb = cpu_baseline(args.precision)
     launches_total = int(sum(v[0] for v in prof.values()))
+    serving = None
+    if args.serving_jobs > 0 and ws == 1:
+        serving = run_serving(args.serving_jobs, args.serving_budget_gb, args.serving_slots)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -321,12 +324,37 @@ def run_mine(args):
         "roofline": roof,
         "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         "cpu_baseline": cb,
+        "serving": serving,
         "acceptance": float(acc.item()) / max(1, (args.warmup + 2 * args.steps) * cfg["mcmc_steps"] * B),
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_serving(n_jobs: int, budget_gb: float, slots: int):
+    """The serving workload: Poisson arrivals (50/s, seed 4) of atoms Z = 1..14 with charge
+    -1/0/+1 and H2/LiH/N2/CO, 256-4096 walkers, 50 Metropolis steps and one E_L each, on the
+    4/256/32/16 network in BF16-mixed mode, continuous batching with memory admission."""
+    import torch
+
+    import paper_2401_10287_gb300 as P
+    from paper_2401_10287_gb300 import serve
+    jobs = W.serving_jobs(n_jobs=n_jobs, rate_per_s=50.0, seed=4, mcmc_steps=50)
+    reqs = serve.requests_from_jobs(jobs)
+    cfg = P.NetConfig.from_ansatz(W.SERVING_ANSATZ, P.BF16_MIXED)
+    srv = serve.Server(serve.LibraryBackend(cfg), memory_budget=int(budget_gb * (1 << 30)), slots=slots)
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    out = serve.summarize(res, wall)
+    out.update({"stream": f"first {n_jobs} jobs of the 1000-job Poisson stream (50/s, seed 4)",
+                "slots": slots, "memory_budget_gb": budget_gb,
+                "peak_admitted_gb": round(srv.peak_footprint / (1 << 30), 2),
+                "max_concurrent_jobs": srv.max_concurrent, "evictions": srv.evictions})
+    return out
 
 
 def main():
@@ -338,6 +366,10 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
     ap.add_argument("--walkers", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-jobs", type=int, default=150,
+                    help="jobs of the serving stream to replay after the timed steps (0 to skip)")
+    ap.add_argument("--serving-budget-gb", type=float, default=160.0)
+    ap.add_argument("--serving-slots", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
