@@ -179,6 +179,7 @@ def run_mine(args):
     import torch.distributed as dist
 
     import paper_2401_10287_gb300 as P
+    from paper_2401_10287_gb300 import dp
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -207,12 +208,7 @@ def run_mine(args):
                        accept_count=acc)
         e, lp2, _ = gpu.local_energy(params_dev, walkers)
         if ws > 1:
-            tot = torch.stack([e.sum(), torch.tensor(float(B), dtype=torch.float64, device="cuda")])
-            dist.all_reduce(tot)
-            mean = tot[0] / tot[1]
-            wts = 2.0 * (e - mean) / tot[1]
-            g = gpu.log_psi_vjp(params_dev, walkers, wts)
-            dist.all_reduce(g)
+            g = dp.energy_gradient(gpu, params_dev, walkers, e)     # NCCL exchange of Eq. 6
         else:
             g, mean = gpu.energy_grad(params_dev, walkers, e)
         return e, g
