@@ -104,6 +104,79 @@ __device__ void thread_inverse(const Det* A, const int* perm, const Det* rcp, in
   }
 }
 
+// Tangent item for an n x n block with n known at compile time: B = C D row by row with n
+// independent accumulators (no serial dot-product chains), then g = tr B and q = tr(B^2)
+// from the registers.  C is interleaved with stride ST; D is the slab in global memory.
+template <int NN, typename Det, typename PhiT>
+__device__ __forceinline__ void tangent_item_fixed(const Det* __restrict__ Cm, int ST, const PhiT* __restrict__ D,
+                                                   Det* g_out, Det* q_out) {
+  Det B[NN][NN];
+  Det d[NN][NN];
+#pragma unroll
+  for (int m = 0; m < NN; ++m)
+#pragma unroll
+    for (int j = 0; j < NN; ++j) d[m][j] = (Det)D[m * NN + j];
+#pragma unroll
+  for (int i = 0; i < NN; ++i) {
+#pragma unroll
+    for (int j = 0; j < NN; ++j) B[i][j] = 0;
+#pragma unroll
+    for (int m = 0; m < NN; ++m) {
+      const Det c = Cm[(int64_t)(i * NN + m) * ST];
+#pragma unroll
+      for (int j = 0; j < NN; ++j) B[i][j] += c * d[m][j];
+    }
+  }
+  Det g = 0, q = 0;
+#pragma unroll
+  for (int i = 0; i < NN; ++i) {
+    g += B[i][i];
+    q += B[i][i] * B[i][i];
+#pragma unroll
+    for (int j = i + 1; j < NN; ++j) q += (Det)2 * B[i][j] * B[j][i];
+  }
+  *g_out = g;
+  *q_out = q;
+}
+
+// Same for any n (serial dots; used for blocks larger than 8).
+template <typename Det, typename PhiT>
+__device__ void tangent_item_any(const Det* __restrict__ Cm, int ST, const PhiT* __restrict__ D, int n, Det* g_out,
+                                 Det* q_out) {
+  Det g = 0, q = 0;
+  for (int i = 0; i < n; ++i) {
+    for (int j = i; j < n; ++j) {
+      Det bij = 0;
+      for (int m = 0; m < n; ++m) bij += Cm[(int64_t)(i * n + m) * ST] * (Det)D[m * n + j];
+      if (j == i) {
+        g += bij;
+        q += bij * bij;
+      } else {
+        Det bji = 0;
+        for (int m = 0; m < n; ++m) bji += Cm[(int64_t)(j * n + m) * ST] * (Det)D[m * n + i];
+        q += (Det)2 * bij * bji;
+      }
+    }
+  }
+  *g_out = g;
+  *q_out = q;
+}
+
+template <typename Det, typename PhiT>
+__device__ __forceinline__ void tangent_item(const Det* Cm, int ST, const PhiT* D, int n, Det* g, Det* q) {
+  switch (n) {
+    case 1: tangent_item_fixed<1>(Cm, ST, D, g, q); break;
+    case 2: tangent_item_fixed<2>(Cm, ST, D, g, q); break;
+    case 3: tangent_item_fixed<3>(Cm, ST, D, g, q); break;
+    case 4: tangent_item_fixed<4>(Cm, ST, D, g, q); break;
+    case 5: tangent_item_fixed<5>(Cm, ST, D, g, q); break;
+    case 6: tangent_item_fixed<6>(Cm, ST, D, g, q); break;
+    case 7: tangent_item_fixed<7>(Cm, ST, D, g, q); break;
+    case 8: tangent_item_fixed<8>(Cm, ST, D, g, q); break;
+    default: tangent_item_any(Cm, ST, D, n, g, q); break;
+  }
+}
+
 // Local-energy pass: one CTA per walker.  Threads 0..2K-1 factorise and invert the
 // (determinant, spin) blocks; then every thread takes (block, coordinate) items
 // g_t = tr(C d_t A), q_t = tr((C d_t A)^2) and tr(C lap A); then the determinant terms
@@ -166,21 +239,8 @@ __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, c
     const int t = tr < NC ? 1 + tr : T - 1;
     const PhiT* D = Phi + blk_off[sp] + (int64_t)k * T * n * n + (int64_t)t * n * n;
     if (tr < NC) {
-      Det g = 0, q = 0;
-      for (int i = 0; i < n; ++i) {
-        for (int j = i; j < n; ++j) {
-          Det bij = 0;
-          for (int m = 0; m < n; ++m) bij += Cm[(int64_t)(i * n + m) * ST] * (Det)D[m * n + j];
-          if (j == i) {
-            g += bij;
-            q += bij * bij;
-          } else {
-            Det bji = 0;
-            for (int m = 0; m < n; ++m) bji += Cm[(int64_t)(j * n + m) * ST] * (Det)D[m * n + i];
-            q += (Det)2 * bij * bji;
-          }
-        }
-      }
+      Det g, q;
+      tangent_item<Det, PhiT>(Cm, ST, D, n, &g, &q);
       gt[p * NC + tr] = g;
       qt[p * NC + tr] = q;
     } else {

@@ -222,16 +222,37 @@ __device__ void stage_pair_weights(const PairArgs& a, Cmp* sW, Cmp* sc) {
 
 // z[c] = sum_k W^T[k][c] g[k] (+ bias); the weight row is read as 16-byte vectors that
 // every thread of the block reads at the same time (broadcast).
+__device__ __forceinline__ void load_row(const float* p, float (&w)[kMaxH2]) {
+  const float4* q = (const float4*)p;
+#pragma unroll
+  for (int v = 0; v < kMaxH2 / 4; ++v) {
+    const float4 f = q[v];
+    w[4 * v] = f.x; w[4 * v + 1] = f.y; w[4 * v + 2] = f.z; w[4 * v + 3] = f.w;
+  }
+}
+__device__ __forceinline__ void load_row(const double* p, double (&w)[kMaxH2]) {
+  const double2* q = (const double2*)p;
+#pragma unroll
+  for (int v = 0; v < kMaxH2 / 2; ++v) {
+    const double2 f = q[v];
+    w[2 * v] = f.x; w[2 * v + 1] = f.y;
+  }
+}
+
 template <typename Cmp>
 __device__ __forceinline__ void pair_matvec(const Cmp* __restrict__ sWl, const Cmp* __restrict__ scl, bool bias,
                                             int dg, const Cmp (&g)[kMaxH2], Cmp (&z)[kMaxH2]) {
+  if (bias) load_row(scl, z);
+  else {
 #pragma unroll
-  for (int c = 0; c < kMaxH2; ++c) z[c] = bias ? scl[c] : (Cmp)0;
+    for (int c = 0; c < kMaxH2; ++c) z[c] = 0;
+  }
 #pragma unroll
   for (int k = 0; k < kMaxH2; ++k) {
     if (k < dg) {
+      Cmp row[kMaxH2];
+      load_row(sWl + k * kMaxH2, row);
       const Cmp gk = g[k];
-      const Cmp* row = sWl + k * kMaxH2;
 #pragma unroll
       for (int c = 0; c < kMaxH2; ++c) z[c] += row[c] * gk;
     }
@@ -665,7 +686,7 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
       pa.gstore[l] = (keep && l >= 1) ? ws.gpair[l] : nullptr;
     }
     const size_t wbytes = sizeof(Cmp) * ((L - 1) * kMaxH2 * kMaxH2 + (L - 1) * kMaxH2);
-    ProfScope ps(s->prof, kProfPair, st);
+    ProfScope ps(s->prof, full ? kProfPairFull : kProfPair, st);
     if (full) {
       const size_t smem = wbytes + sizeof(Cmp) * sh.N * 8 * 33;
       const int threads = (int)round_up(8 * sh.N, 32);
@@ -735,8 +756,9 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     oa.h1 = h1; oa.K = s->cfg.n_dets; oa.aniso = s->cfg.envelope == FN_ENV_ANISOTROPIC;
     const int ko_max = s->cfg.n_dets * std::max(s->n_up, s->n_dn);
     const int threads = (int)std::min<int64_t>(1024, round_up(ko_max, 32));
-    ProfScope ps(s->prof, full ? kProfOrbFull : kProfOrbValue, st);
     if (Mode::kMode == FN_BF16_MIXED) {
+      {
+      ProfScope ps(s->prof, full ? kProfOrbFull : kProfOrbValue, st);
       const float* wb[2] = {(const float*)oa.g[0], (const float*)oa.g[1]};
       const float* pis[2] = {(const float*)oa.pi[0], (const float*)oa.pi[1]};
       const float* sgs[2] = {(const float*)oa.sig[0], (const float*)oa.sig[1]};
@@ -744,13 +766,16 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
                               s->cfg.n_dets, oa.aniso, (const float*)walkers, s->d_nuclei, ws.Phi, oa.PW, ws.orbP,
                               ws.status, st))
         const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
+      }
       if (full) {
         const int ko_max = s->cfg.n_dets * std::max(s->n_up, s->n_dn);
+        ProfScope ps2(s->prof, kProfOrbFix, st);
         k_orbital_fixup<typename Mode::PhiT, Wlk><<<(unsigned)((int64_t)sh.B * sh.N), (unsigned)round_up(ko_max, 32), 0,
                                                     st>>>(r, s->d_nuclei, sh, oa, ws.orbP);
       }
       return;
     }
+    ProfScope ps(s->prof, full ? kProfOrbFull : kProfOrbValue, st);
     const size_t smem = sizeof(Cmp) * h1;
     const unsigned blocks = (unsigned)((int64_t)sh.B * sh.N);
     using PhiT = typename Mode::PhiT;

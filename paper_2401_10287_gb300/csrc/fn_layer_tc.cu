@@ -29,7 +29,8 @@ namespace tc {
 
 constexpr int kStages = 3;
 constexpr int kBlockK = 64;                     // bf16 elements per 128-byte swizzled row
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;                   // two warps per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint64_t kWaitNs = 1000000000ull;     // 1 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -77,13 +78,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// OR of a predicate over the 128 epilogue threads (named barrier 1).
+// OR of a predicate over the epilogue threads (named barrier 1).
 __device__ __forceinline__ bool epilogue_any(bool v) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.u32 q, %1, 0;\n\t"
-      "bar.red.or.pred p, 1, 128, q;\n\t"
+      "bar.red.or.pred p, 1, 256, q;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(r)
       : "r"(v ? 1u : 0u)
@@ -143,6 +144,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
       : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -191,9 +212,12 @@ struct Smem {
 };
 
 // ---- epilogue: stream layer ------------------------------------------------------------
+// One 32-column chunk, in two 16-column halves (register budget); the spin means of the
+// chunk's outputs are reduced through shared memory by the warps of this column half.
 template <bool FULL>
-__device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, int r, int ethread, uint32_t tmem,
-                                          uint32_t lane_base, int buf, int n0, int tile, float* ys) {
+__device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, bool has_chunk, int r, int ehalf,
+                                          int ethread, uint32_t tmem, uint32_t lane_base, int buf, int n0, int tile,
+                                          float* ys) {
   const Shape& sh = a.sh;
   const int nt = a.nt, T = sh.T;
   const int64_t row = (int64_t)tile * 128 + r;
@@ -202,102 +226,115 @@ __device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, int r,
   const bool valid = wl < sh.wpt && w < sh.B;
   const int64_t xslab = sh.R * a.ldx, yslab = sh.R * a.ldy;
   const int col0 = n0 + cc * 32;
-  uint32_t acc[32], hv[32], sq[32];
-  tmem_ld32(tmem + lane_base + (uint32_t)(buf * nt + cc * 32), acc);
-  if (FULL && t > 0) {
-    tmem_ld32(tmem + lane_base + (uint32_t)(2 * nt + cc * 32), hv);
-    tmem_ld32(tmem + lane_base + (uint32_t)(3 * nt + cc * 32), sq);
-  }
-  const bool live = valid && col0 < a.h1;
-  float out[32];
-  if (live) {
-    const float4* mt = (const float4*)(a.Mterm + ((int64_t)t * sh.B + w) * a.h1 + col0);
-    float mv[32];
-#pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      const float4 m4 = mt[v];
-      mv[4 * v] = m4.x; mv[4 * v + 1] = m4.y; mv[4 * v + 2] = m4.z; mv[4 * v + 3] = m4.w;
-    }
-    float res[32];
-    if (a.residual) {
-      const uint4* xr = (const uint4*)(a.X + t * xslab + row * a.ldx + col0);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const uint4 u = xr[v];
-        const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float2 f = __bfloat1622float2(p2[e]);
-          res[8 * v + 2 * e] = f.x;
-          res[8 * v + 2 * e + 1] = f.y;
-        }
+  const bool live = has_chunk && valid && col0 < a.h1;
+  float* ysh = ys + ehalf * 128 * 33;
+  if (has_chunk) {
+#pragma unroll 1
+    for (int hh = 0; hh < 2; ++hh) {
+      const int cb = cc * 32 + hh * 16;
+      uint32_t acc[16], hv[16], sq[16];
+      tmem_ld16(tmem + lane_base + (uint32_t)(buf * nt + cb), acc);
+      if (FULL && t > 0) {
+        tmem_ld16(tmem + lane_base + (uint32_t)(2 * nt + cb), hv);
+        tmem_ld16(tmem + lane_base + (uint32_t)(3 * nt + cb), sq);
       }
-    }
+      float out[16];
+      if (live) {
+        const int c0 = col0 + hh * 16;
+        const float4* mt = (const float4*)(a.Mterm + ((int64_t)t * sh.B + w) * a.h1 + c0);
+        float res[16];
+        if (a.residual) {
+          const uint4* xr = (const uint4*)(a.X + t * xslab + row * a.ldx + c0);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const float z = __uint_as_float(acc[j]) + mv[j];
-      float o;
-      if (t == 0) {
-        const float h = tanhf(z);
-        hv[j] = __float_as_uint(h);
-        sq[j] = 0u;
-        o = h;
+          for (int v = 0; v < 2; ++v) {
+            const uint4 u = xr[v];
+            const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float2 f = __bfloat1622float2(p2[e]);
+              res[8 * v + 2 * e] = f.x;
+              res[8 * v + 2 * e + 1] = f.y;
+            }
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float4 m4 = mt[v];
+          const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int j = 4 * v + e;
+            const float z = __uint_as_float(acc[j]) + mv[e];
+            float o;
+            if (t == 0) {
+              const float h = tanhf(z);
+              hv[j] = __float_as_uint(h);
+              sq[j] = 0u;
+              o = h;
+            } else {
+              const float h = __uint_as_float(hv[j]);
+              const float d = 1.0f - h * h;
+              if (t < T - 1) {
+                o = d * z;
+                sq[j] = __float_as_uint(__uint_as_float(sq[j]) + z * z);
+              } else {
+                o = d * z - 2.0f * h * d * __uint_as_float(sq[j]);
+              }
+            }
+            out[j] = a.residual ? o + res[j] : o;
+          }
+        }
+        uint4* yo = (uint4*)(a.Y + t * yslab + row * a.ldy + c0);
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          uint4 u;
+          __nv_bfloat162* p2 = (__nv_bfloat162*)&u;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(out[8 * v + 2 * e], out[8 * v + 2 * e + 1]);
+          yo[v] = u;
+        }
+        if (t == 0 && a.act_out) {
+          float4* ao = (float4*)(a.act_out + row * a.h1 + c0);
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            ao[v] = make_float4(__uint_as_float(hv[4 * v]), __uint_as_float(hv[4 * v + 1]),
+                                __uint_as_float(hv[4 * v + 2]), __uint_as_float(hv[4 * v + 3]));
+        }
       } else {
-        const float h = __uint_as_float(hv[j]);
-        const float d = 1.0f - h * h;
-        if (t < T - 1) {
-          o = d * z;
-          sq[j] = __float_as_uint(__uint_as_float(sq[j]) + z * z);
-        } else {
-          o = d * z - 2.0f * h * d * __uint_as_float(sq[j]);
-        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) { out[j] = 0.f; hv[j] = 0u; sq[j] = 0u; }
       }
-      out[j] = a.residual ? o + res[j] : o;
+      if (FULL) {
+        if (t == 0) {
+          tmem_st16(tmem + lane_base + (uint32_t)(2 * nt + cb), hv);
+          tmem_st16(tmem + lane_base + (uint32_t)(3 * nt + cb), sq);
+        } else if (t < T - 1) {
+          tmem_st16(tmem + lane_base + (uint32_t)(3 * nt + cb), sq);
+        }
+        tmem_wait_st();
+      }
+      if (a.Hbar_out) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) ysh[r * 33 + hh * 16 + j] = out[j];
+      }
     }
-    uint4* yo = (uint4*)(a.Y + t * yslab + row * a.ldy + col0);
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      uint4 u;
-      __nv_bfloat162* p2 = (__nv_bfloat162*)&u;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(out[8 * v + 2 * e], out[8 * v + 2 * e + 1]);
-      yo[v] = u;
-    }
-    if (t == 0 && a.act_out) {
-      float4* ao = (float4*)(a.act_out + row * a.h1 + col0);
-#pragma unroll
-      for (int v = 0; v < 8; ++v)
-        ao[v] = make_float4(__uint_as_float(hv[4 * v]), __uint_as_float(hv[4 * v + 1]), __uint_as_float(hv[4 * v + 2]),
-                            __uint_as_float(hv[4 * v + 3]));
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) { out[j] = 0.f; hv[j] = 0u; sq[j] = 0u; }
   }
-  if (FULL) {
-    if (t == 0) {
-      tmem_st32(tmem + lane_base + (uint32_t)(2 * nt + cc * 32), hv);
-      tmem_st32(tmem + lane_base + (uint32_t)(3 * nt + cc * 32), sq);
-    } else if (t < T - 1) {
-      tmem_st32(tmem + lane_base + (uint32_t)(3 * nt + cc * 32), sq);
+  if (a.Hbar_out) {
+    // both column halves take part in both barriers, with or without a chunk
+    asm volatile("bar.sync 2, 256;" ::: "memory");
+    if (has_chunk && col0 < a.h1) {
+      for (int e = ethread & 127; e < sh.wpt * 2 * 32; e += 128) {
+        const int wl2 = e / 64, s2 = (e / 32) & 1, j = e & 31;
+        const int w2 = tile * sh.wpt + wl2;
+        if (w2 >= sh.B) continue;
+        const int lo = s2 ? sh.n_up : 0, hi = s2 ? sh.N : sh.n_up;
+        float sum = 0.f;
+        for (int i = lo; i < hi; ++i) sum += ysh[(wl2 * sh.N + i) * 33 + j];
+        a.Hbar_out[((int64_t)t * sh.B + w2) * 2 * a.h1 + s2 * a.h1 + col0 + j] =
+            __float2bfloat16_rn(hi > lo ? sum / (float)(hi - lo) : 0.f);
+      }
     }
-    tmem_wait_st();
-  }
-  if (a.Hbar_out && col0 < a.h1) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) ys[r * 33 + j] = out[j];
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    for (int e = ethread; e < sh.wpt * 2 * 32; e += 128) {
-      const int wl2 = e / 64, s = (e / 32) & 1, j = e & 31;
-      const int w2 = tile * sh.wpt + wl2;
-      if (w2 >= sh.B) continue;
-      const int lo = s ? sh.n_up : 0, hi = s ? sh.N : sh.n_up;
-      float sum = 0.f;
-      for (int i = lo; i < hi; ++i) sum += ys[(wl2 * sh.N + i) * 33 + j];
-      a.Hbar_out[((int64_t)t * sh.B + w2) * 2 * a.h1 + s * a.h1 + col0 + j] =
-          __float2bfloat16_rn(hi > lo ? sum / (float)(hi - lo) : 0.f);
-    }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 2, 256;" ::: "memory");
   }
 }
 
@@ -413,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* sA = base;                                   // kStages x 16 KB
   unsigned char* sB = sA + kStages * bytesA;                  // kStages x nbparts x nt*128
   float* ep = (float*)(sB + kStages * nbparts * bytesB);      // epilogue staging
-  const size_t ep_floats = EPI == kEpiLayer ? 128 * 33 : 0;
+  const size_t ep_floats = EPI == kEpiLayer ? 2 * 128 * 33 : 0;
   uint64_t* bars = (uint64_t*)(ep + ep_floats);
   uint64_t* full = bars;
   uint64_t* empty = bars + kStages;
@@ -439,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(accf + b, 1); mbar_init(acce + b, 4); }
+    for (int b = 0; b < 2; ++b) { mbar_init(accf + b, 1); mbar_init(acce + b, kEpiWarps); }
     mbar_init(mma_done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -516,10 +553,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(mma_done, 0u, globaltimer() + kWaitNs);
     }
   } else {
-    const int q = warp & 3;
+    const int q = warp & 3;                       // TMEM lane quarter this warp may access
     const int r = q * 32 + lane;
-    const int ethread = threadIdx.x - 64;
+    const int ethread = threadIdx.x - 64;         // 0..255
+    const int ehalf = (warp - 2) >> 2;            // column half: chunks cc with cc % 2 == ehalf
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const int nchunks = nt / 32;
     for (int t = 0; t < T; ++t) {
       const int buf = t & 1;
       const uint32_t use = (uint32_t)(t >> 1);
@@ -532,10 +571,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       fence_after();
-      for (int cc = 0; cc < nt / 32; ++cc) {
-        if (EPI == kEpiLayer) epi_layer<FULL>(a, t, cc, r, ethread, tmem, lane_base, buf, ctile * nt, tile, ep);
-        else if (EPI == kEpiPlain) epi_plain(a, cc, r, tmem, lane_base, buf, ctile * nt, tile);
-        else epi_orbital<FULL>(a, t, cc, r, tmem, lane_base, buf, spin, ko0, tile);
+      for (int it = 0; it < (nchunks + 1) / 2; ++it) {
+        const int cc = 2 * it + ehalf;
+        const bool has = cc < nchunks;
+        if (EPI == kEpiLayer) {
+          epi_layer<FULL>(a, t, has ? cc : 0, has, r, ehalf, ethread, tmem, lane_base, buf, ctile * nt, tile, ep);
+        } else if (has) {
+          if (EPI == kEpiPlain) epi_plain(a, cc, r, tmem, lane_base, buf, ctile * nt, tile);
+          else epi_orbital<FULL>(a, t, cc, r, tmem, lane_base, buf, spin, ko0, tile);
+        }
       }
       fence_before();
       __syncwarp();
@@ -597,7 +641,7 @@ static uint32_t pow2_cols(int c) {
 }
 
 static size_t tc_smem_bytes(int nt, int epi, bool split) {
-  const size_t ep = epi == tc::kEpiLayer ? 128 * 33 * 4 : 0;
+  const size_t ep = epi == tc::kEpiLayer ? 2 * 128 * 33 * 4 : 0;
   return 1024 + tc::kStages * (128 * 128 + (size_t)nt * 128 * (split ? 2 : 1)) + ep + 8 * (2 * tc::kStages + 5) + 16;
 }
 
