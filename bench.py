@@ -153,25 +153,30 @@ def run_reference(args):
     return 0
 
 
-def _algorithmic(cls, B, N, a, T_full):
-    """(work per launch, unit, bound) of a kernel class at this workload (Sec. d of the design)."""
+def _algorithmic(cls, B, N, a, T_full, act_bytes):
+    """Algorithmic work of one launch of a kernel class at this workload:
+    returns (amount, kind) with kind "bytes" (HBM-bound), "flop" (FP32/tensor) or "flop64"."""
     M = 2
     h1, h2, K = a.h1, a.h2, a.n_dets
     n = N // 2
+    L = a.n_layers
+    R = int(np.ceil(B / (128 // N))) * 128
+    k_self = [4 * M + 8] + [h1 + 2 * h2] * (L - 1)
     if cls in ("layer_full", "layer_value"):
         T = T_full if cls == "layer_full" else 1
-        # average over the L layers: layer 0 has k_self = 4M + 8, the others h1 + 2 h2
-        k_self = [4 * M + 8] + [h1 + 2 * h2] * (a.n_layers - 1)
-        flops = np.mean([2.0 * B * N * T * k * h1 for k in k_self])
-        return flops, "flop", "alu"
-    if cls in ("det_full",):
-        # per walker, determinant k, spin: 3N tangent items x 2 n^3 flops + Laplacian trace 2 n^2
-        flops = B * K * 2 * (3 * N * 2 * n ** 3 + 2 * n * n + 3 * n ** 3)
-        return flops, "flop64", "alu"
-    if cls in ("orbitals_full",):
-        flops = 2.0 * B * N * T_full * h1 * K * n
-        return flops, "flop", "alu"
-    return None, None, None
+        # per layer: X_l read, h_{l+1} written, mean-field term read, spin means written;
+        # averaged over the L launches of one pass
+        per = [T * R * (k + h1) * act_bytes + T * B * h1 * 4 + T * B * 2 * h1 * act_bytes for k in k_self]
+        return float(np.mean(per)), "bytes"
+    if cls == "det_full":
+        # per walker, determinant k, spin: 3N tangent items x 2 n^3 + Laplacian trace + LU/inverse
+        return float(B * K * 2 * (3 * N * 2 * n ** 3 + 2 * n * n + 3 * n ** 3)), "flop64"
+    if cls == "pair_full":
+        # 8 jet rows per ordered pair, L-1 layers of h2 x d_g
+        return float(B * N * N * 8 * 2 * (4 * h2 + (L - 2) * h2 * h2)), "flop"
+    if cls == "orbitals_full":
+        return float(2.0 * B * N * T_full * h1 * K * n), "flop"
+    return None, None
 
 
 def run_mine(args):
@@ -274,26 +279,27 @@ def run_mine(args):
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     cls, (launches, total_ms) = dom
     T_full = 3 * N + 2
-    work, kind, bound = _algorithmic(cls, B, N, a, T_full)
+    act_bytes = 2 if prec == P.BF16_MIXED else (8 if prec == P.FP64 else 4)
+    work, kind = _algorithmic(cls, B, N, a, T_full, act_bytes)
     roof = None
     if work is not None:
         avg_s = total_ms / launches / 1000.0
-        if kind == "flop64":
+        if kind == "bytes":
+            achieved = work / avg_s / 1e9
+            pk = peaks["hbm_gbs"]
+            roof = {"kernel": cls, "bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
+                    "frac": achieved / pk, "traffic": args.traffic, "algorithmic_bytes_per_launch": work,
+                    "peak_source": f"{peak_src} HBM copy bandwidth"}
+        elif kind == "flop64":
             achieved = work / avg_s / 1e12
             roof = {"kernel": cls, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s (FP64)", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "unit": "TFLOP/s (FP64)", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": args.traffic,
                     "peak_source": "nominal FP64 rate of the part (measured DFMA probe: 1.20)"}
-        elif prec == P.BF16_MIXED and cls.startswith("layer"):
-            achieved = work / avg_s / 1e12
-            pk = peaks["bf16_tflops_sustained"]
-            roof = {"kernel": cls, "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                    "frac": achieved / pk, "traffic": None, "peak_source": f"{peak_src} bf16 sustained"}
         else:
             achieved = work / avg_s / 1e12
-            pk = FP64_PEAK_TFLOPS if prec == P.FP64 else FP32_PEAK_TFLOPS
-            roof = {"kernel": cls, "bound": "alu", "achieved": achieved, "peak": pk,
-                    "unit": "TFLOP/s (FP64)" if prec == P.FP64 else "TFLOP/s (FP32)", "frac": achieved / pk,
-                    "traffic": None, "peak_source": "derived from unit counts and the 2.07 GHz clock"}
+            roof = {"kernel": cls, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s (FP32)", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": args.traffic,
+                    "peak_source": "derived from unit counts and the 2.07 GHz clock"}
     cb = None
     if not args.no_cpu_baseline and ws == 1:
         cb = cpu_baseline(args.precision)
@@ -366,6 +372,8 @@ def main():
                     help="jobs of the serving stream to replay after the timed steps (0 to skip)")
     ap.add_argument("--serving-budget-gb", type=float, default=160.0)
     ap.add_argument("--serving-slots", type=int, default=8)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -213,6 +213,7 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
   const size_t o_gradc = take((size_t)s->prep.total * sizeof(Cmp));
   const size_t o_dP = take((size_t)sh.R * s->cfg.n_dets * N * sizeof(Cmp));
   const size_t o_orbP = take(Mode::kMode == FN_BF16_MIXED ? (size_t)sh.R * 4 * s->cfg.n_dets * N * sizeof(float) : 0);
+  const size_t o_envv = take(Mode::kMode == FN_BF16_MIXED ? (size_t)sh.R * s->cfg.n_dets * N * sizeof(float) : 0);
   const size_t o_status = take(sizeof(int) * 4);
   const size_t o_counter = take(sizeof(int64_t) * 4);
   if (ws && ws->base) {
@@ -225,7 +226,7 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
     ws->prep16 = b + o_prep16; ws->walk2 = b + o_walk2; ws->lp2 = (double*)(b + o_lp2);
     ws->scratch_d = (double*)(b + o_scr); ws->dX = b + o_dX; ws->dH = b + o_dH; ws->dZ = b + o_dZ;
     ws->dZw = b + o_dZw; ws->dHbar = b + o_dHbar; ws->dG = b + o_dG; ws->dPhi = b + o_dPhi;
-    ws->gradc = b + o_gradc; ws->dP = b + o_dP; ws->orbP = (float*)(b + o_orbP); ws->status = (int*)(b + o_status); ws->counter = (int64_t*)(b + o_counter);
+    ws->gradc = b + o_gradc; ws->dP = b + o_dP; ws->orbP = (float*)(b + o_orbP); ws->envv = (float*)(b + o_envv); ws->status = (int*)(b + o_status); ws->counter = (int64_t*)(b + o_counter);
   }
   return off;
 }

@@ -397,6 +397,133 @@ __global__ void k_det_value(Shape sh, DetArgs a) {
   }
 }
 
+// Register-resident LU of one n x n block (n <= 8 known at compile time): one elimination
+// step per template instance, so every matrix index is a compile-time constant and the block
+// stays in registers; partial pivoting by predicated row swaps; log|det| and sign by
+// mantissa/exponent tracking.
+template <int NN, int C, typename Det>
+struct LuStep {
+  static __device__ __forceinline__ void run(Det (&a)[NN][NN], Det& sgn, Det& mant, int& expo, bool& singular) {
+    Det best = f_abs(a[C][C]);
+    int piv = C;
+#pragma unroll
+    for (int r = C + 1; r < NN; ++r) {
+      const Det v = f_abs(a[r][C]);
+      if (v > best) { best = v; piv = r; }
+    }
+    if (!(best > (Det)0)) singular = true;
+#pragma unroll
+    for (int r = C + 1; r < NN; ++r) {
+      const bool sw = r == piv;
+#pragma unroll
+      for (int j = 0; j < NN; ++j) {
+        const Det t = a[C][j];
+        a[C][j] = sw ? a[r][j] : t;
+        a[r][j] = sw ? t : a[r][j];
+      }
+    }
+    if (piv != C) sgn = -sgn;
+    const Det p = a[C][C];
+    const Det rp = (Det)1 / p;
+    int e;
+    mant *= frexp(p, &e);
+    expo += e;
+    int e2;
+    mant = frexp(mant, &e2);
+    expo += e2;
+#pragma unroll
+    for (int r = C + 1; r < NN; ++r) {
+      const Det f = a[r][C] * rp;
+#pragma unroll
+      for (int j = C + 1; j < NN; ++j) a[r][j] -= f * a[C][j];
+    }
+    LuStep<NN, C + 1, Det>::run(a, sgn, mant, expo, singular);
+  }
+};
+template <int NN, typename Det>
+struct LuStep<NN, NN, Det> {
+  static __device__ __forceinline__ void run(Det (&)[NN][NN], Det&, Det&, int&, bool&) {}
+};
+
+template <int NN, typename Det, typename PhiT>
+__device__ __forceinline__ void lu_regs(const PhiT* __restrict__ Ag, Det* ld_out, Det* sign_out) {
+  Det a[NN][NN];
+#pragma unroll
+  for (int i = 0; i < NN; ++i)
+#pragma unroll
+    for (int j = 0; j < NN; ++j) a[i][j] = (Det)Ag[i * NN + j];
+  Det sgn = 1, mant = 1;
+  int expo = 0;
+  bool singular = false;
+  LuStep<NN, 0, Det>::run(a, sgn, mant, expo, singular);
+  if (singular) {
+    *ld_out = 0;
+    *sign_out = 0;
+    return;
+  }
+  *sign_out = mant < 0 ? -sgn : sgn;
+  *ld_out = f_log(f_abs(mant)) + (Det)expo * (Det)0.6931471805599453;
+}
+
+template <typename Det, typename PhiT>
+__device__ __forceinline__ void lu_regs_any(const PhiT* Ag, int n, Det* ld, Det* sg) {
+  switch (n) {
+    case 1: lu_regs<1, Det, PhiT>(Ag, ld, sg); break;
+    case 2: lu_regs<2, Det, PhiT>(Ag, ld, sg); break;
+    case 3: lu_regs<3, Det, PhiT>(Ag, ld, sg); break;
+    case 4: lu_regs<4, Det, PhiT>(Ag, ld, sg); break;
+    case 5: lu_regs<5, Det, PhiT>(Ag, ld, sg); break;
+    case 6: lu_regs<6, Det, PhiT>(Ag, ld, sg); break;
+    case 7: lu_regs<7, Det, PhiT>(Ag, ld, sg); break;
+    default: lu_regs<8, Det, PhiT>(Ag, ld, sg); break;
+  }
+}
+
+// Value pass without the backward seed, blocks of at most 8 x 8: one thread per
+// (determinant, spin) block, 128 / (2K) walkers per CTA, no shared-memory staging.
+template <typename Det, typename PhiT>
+__global__ void __launch_bounds__(128) k_det_value_small(Shape sh, DetArgs a) {
+  __shared__ Det ld2[128], sg2[128];
+  const int K = a.K, NM = 2 * K;
+  const int per_cta = 128 / NM;
+  const int wl = threadIdx.x / NM, p = threadIdx.x % NM;
+  const int w = blockIdx.x * per_cta + wl;
+  const int ns[2] = {sh.n_up, sh.n_dn};
+  if (wl < per_cta && w < sh.B) {
+    const int k = p >> 1, sp = p & 1, n = ns[sp];
+    if (n == 0) {
+      ld2[threadIdx.x] = 0;
+      sg2[threadIdx.x] = 1;
+    } else {
+      const PhiT* A = (const PhiT*)a.Phi + (int64_t)w * a.PW + (sp ? (int64_t)K * ns[0] * ns[0] : 0) +
+                      (int64_t)k * n * n;
+      lu_regs_any<Det, PhiT>(A, n, ld2 + threadIdx.x, sg2 + threadIdx.x);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < per_cta) {
+    const int w2 = blockIdx.x * per_cta + threadIdx.x;
+    if (w2 < sh.B) {
+      const Det* l = ld2 + threadIdx.x * NM;
+      const Det* g = sg2 + threadIdx.x * NM;
+      Det m = -INFINITY;
+      for (int k = 0; k < K; ++k)
+        if (g[2 * k] * g[2 * k + 1] != 0 && l[2 * k] + l[2 * k + 1] > m) m = l[2 * k] + l[2 * k + 1];
+      Det S = 0;
+      for (int k = 0; k < K; ++k) {
+        const Det sk = g[2 * k] * g[2 * k + 1];
+        if (sk != 0) S += sk * f_exp(l[2 * k] + l[2 * k + 1] - m);
+      }
+      const double lpsi = (double)(m + f_log(f_abs(S)));
+      const int sgn = S > 0 ? 1 : (S < 0 ? -1 : 0);
+      if (a.log_psi) a.log_psi[w2] = lpsi;
+      if (a.sign) a.sign[w2] = (int8_t)sgn;
+      if (sgn == 0) atomicOr(a.status, kStatusSingular);
+      else if (!isfinite(lpsi)) atomicOr(a.status, kStatusNonFinite);
+    }
+  }
+}
+
 template <class Mode>
 void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh, double* e_local, double* log_psi,
                        int8_t* sign, bool keep_inverse, cudaStream_t st) {
@@ -421,6 +548,9 @@ void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh,
                                        2 * K + K * NC + 2 * K + 128) + sizeof(int) * (size_t)nmax * ST;
     cudaFuncSetAttribute(k_det_energy<Det, Wlk, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_det_energy<Det, Wlk, PhiT><<<sh.B, 128, smem, st>>>((const Wlk*)walkers, s->d_nuclei, sh, a);
+  } else if (!keep_inverse && nmax <= 8) {
+    const int per_cta = 128 / (2 * K);
+    k_det_value_small<Det, PhiT><<<(unsigned)((sh.B + per_cta - 1) / per_cta), 128, 0, st>>>(sh, a);
   } else {
     const int threads = (int)round_up(2 * K, 32);
     const bool inv = keep_inverse;

@@ -604,6 +604,38 @@ __global__ void k_orbital_fixup(const Wlk* __restrict__ r, const double* __restr
   base[(sh.T - 1) * nn] += (PhiT)lap;
 }
 
+// Envelope values of every (electron, own-spin orbital), one thread each (tensor-core pass).
+template <typename Wlk>
+__global__ void k_envelope_values(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh, OrbArgs a,
+                                  float* __restrict__ envv) {
+  const int w = blockIdx.x / sh.N, j = blockIdx.x % sh.N;
+  const int spin = j < sh.n_up ? 0 : 1;
+  const int n_s = spin ? sh.n_dn : sh.n_up;
+  const int ko = threadIdx.x;
+  if (ko >= a.K * n_s) return;
+  const int64_t row = tile_row(w, j, sh.N, sh.wpt);
+  const Wlk* rj = r + ((int64_t)w * sh.N + j) * 3;
+  const float* pi = (const float*)a.pi[spin] + (int64_t)ko * sh.M;
+  float env = 0.f;
+  for (int m = 0; m < sh.M; ++m) {
+    const float d0 = (float)((double)rj[0] - nuc[3 * m]), d1 = (float)((double)rj[1] - nuc[3 * m + 1]),
+                d2 = (float)((double)rj[2] - nuc[3 * m + 2]);
+    float s2;
+    if (!a.aniso) {
+      const float sg = ((const float*)a.sig[spin])[(int64_t)ko * sh.M + m];
+      s2 = sg * sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    } else {
+      const float* S = (const float*)a.sig[spin] + ((int64_t)ko * sh.M + m) * 9;
+      const float u0 = S[0] * d0 + S[1] * d1 + S[2] * d2;
+      const float u1 = S[3] * d0 + S[4] * d1 + S[5] * d2;
+      const float u2 = S[6] * d0 + S[7] * d1 + S[8] * d2;
+      s2 = sqrtf(u0 * u0 + u1 * u1 + u2 * u2);
+    }
+    env += pi[m] * __expf(-s2);
+  }
+  envv[row * a.K * sh.N + (spin ? a.K * sh.n_up : 0) + ko] = env;
+}
+
 template <typename Act, typename Cmp, typename PhiT, typename Wlk, bool FULL>
 __global__ void k_orbitals(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh, OrbArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -759,12 +791,15 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     if (Mode::kMode == FN_BF16_MIXED) {
       {
       ProfScope ps(s->prof, full ? kProfOrbFull : kProfOrbValue, st);
+      const int ko_env = s->cfg.n_dets * std::max(s->n_up, s->n_dn);
+      k_envelope_values<Wlk><<<(unsigned)((int64_t)sh.B * sh.N), (unsigned)round_up(ko_env, 32), 0, st>>>(
+          r, s->d_nuclei, sh, oa, ws.envv);
       const float* wb[2] = {(const float*)oa.g[0], (const float*)oa.g[1]};
       const float* pis[2] = {(const float*)oa.pi[0], (const float*)oa.pi[1]};
       const float* sgs[2] = {(const float*)oa.sig[0], (const float*)oa.sig[1]};
       if (!launch_orbitals_tc(sh, ws.HL, h1, (const __nv_bfloat16*)ws.prep16 + s->prep.W16, wb, pis, sgs,
                               s->cfg.n_dets, oa.aniso, (const float*)walkers, s->d_nuclei, ws.Phi, oa.PW, ws.orbP,
-                              ws.status, st))
+                              ws.envv, ws.status, st))
         const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
       }
       if (full) {

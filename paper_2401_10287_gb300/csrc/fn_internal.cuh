@@ -137,6 +137,7 @@ struct Workspace {
   void* gradc = nullptr;         // prepared-layout gradient accumulator (Cmp)
   void* dP = nullptr;            // [R][K (n_up + n_dn)] gradient wrt orbital projections (Cmp)
   float* orbP = nullptr;         // [R][4][K N] projections for the orbital envelope fix-up (BF16 mode)
+  float* envv = nullptr;         // [R][K N] envelope values (BF16 mode)
   int* status = nullptr;         // device status word
   int64_t* counter = nullptr;    // scratch counter
 };
@@ -182,7 +183,8 @@ bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int
                     const float* bias, int bias_rows, int* status, cudaStream_t st);
 bool launch_orbitals_tc(const Shape& sh, const void* HL, int h1, const void* W16, const float* const* wbias,
                         const float* const* pi, const float* const* sig, int K, int aniso, const float* walkers,
-                        const double* nuclei, void* Phi, int64_t PW, float* orbP, int* status, cudaStream_t st);
+                        const double* nuclei, void* Phi, int64_t PW, float* orbP, const float* envv, int* status,
+                        cudaStream_t st);
 bool tc_available();
 
 // Shapes and sizes

@@ -28,6 +28,7 @@ namespace fn {
 namespace tc {
 
 constexpr int kStages = 3;
+constexpr int kMaxNucleiTc = 16;
 constexpr int kBlockK = 64;                     // bf16 elements per 128-byte swizzled row
 constexpr int kEpiWarps = 8;                   // two warps per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
@@ -200,6 +201,7 @@ struct TcArgs {
   int K, aniso, ctiles_up;            // column tiles of the up block
   float* Phi; int64_t PW;             // [B][PW] (float)
   float* orbP;                        // [R][4][K N]: value projection and the row's own-coordinate ones
+  const float* envv;                  // [R][K N]: envelope values (k_envelope_values)
   // split weights: columns [0, k) hold bf16(W), columns [bsplit, bsplit + k) hold
   // bf16(W - bf16(W)); every k-block is multiplied by both (0 = no split)
   int bsplit;
@@ -357,29 +359,6 @@ __device__ __forceinline__ void epi_plain(const TcArgs& a, int cc, int r, uint32
   }
 }
 
-// envelope value sum_m pi exp(-s_m) of orbital ko at r_j (value only, inlined).
-__device__ __forceinline__ float envelope_value(const TcArgs& a, int spin, int ko, float r0, float r1, float r2) {
-  const int M = a.sh.M;
-  const float* pi = a.pi[spin] + (int64_t)ko * M;
-  float e = 0.f;
-  for (int m = 0; m < M; ++m) {
-    const float d0 = (float)((double)r0 - a.nuclei[3 * m]), d1 = (float)((double)r1 - a.nuclei[3 * m + 1]),
-                d2 = (float)((double)r2 - a.nuclei[3 * m + 2]);
-    float s;
-    if (!a.aniso) {
-      s = a.sig[spin][(int64_t)ko * M + m] * sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-    } else {
-      const float* S = a.sig[spin] + ((int64_t)ko * M + m) * 9;
-      const float u0 = S[0] * d0 + S[1] * d1 + S[2] * d2;
-      const float u1 = S[3] * d0 + S[4] * d1 + S[5] * d2;
-      const float u2 = S[6] * d0 + S[7] * d1 + S[8] * d2;
-      s = sqrtf(u0 * u0 + u1 * u1 + u2 * u2);
-    }
-    e += pi[m] * __expf(-s);
-  }
-  return e;
-}
-
 // ---- epilogue: orbitals x envelope, common product term ------------------------------------
 // phi_t = P_t env for every slab (P_0 includes the orbital bias).  The envelope-derivative
 // terms (own-coordinate slabs and the Laplacian) are added by k_orbital_fixup from the value
@@ -406,11 +385,7 @@ __device__ __forceinline__ void epi_orbital(const TcArgs& a, int t, int cc, int 
   float* orbp = a.orbP + row * 4 * ldp + (spin ? a.K * sh.n_up : 0);
   const int64_t nn = (int64_t)n_s * n_s;
   float* Phi = a.Phi + (int64_t)w * a.PW + (spin ? (int64_t)a.K * T * sh.n_up * sh.n_up : 0) + t * nn + jj;
-  float r0 = 0.f, r1 = 0.f, r2 = 0.f;
-  if (valid && t == 0) {
-    const float* rp = a.walkers + ((int64_t)w * sh.N + j) * 3;
-    r0 = rp[0]; r1 = rp[1]; r2 = rp[2];
-  }
+  const float* envrow = a.envv + row * ldp + (spin ? a.K * sh.n_up : 0);
   int k = (ko0 + colb) / (n_s ? n_s : 1), i = (ko0 + colb) - k * n_s;
 #pragma unroll
   for (int q = 0; q < 32; ++q) {
@@ -420,7 +395,7 @@ __device__ __forceinline__ void epi_orbital(const TcArgs& a, int t, int cc, int 
       float e;
       if (t == 0) {
         P += a.wbias[spin][ko];
-        e = envelope_value(a, spin, ko, r0, r1, r2);
+        e = envrow[ko];
         ev[q] = __float_as_uint(e);
         if (FULL) orbp[ko] = P;
       } else {
@@ -713,7 +688,8 @@ bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int
 // Orbitals: Phi (double) from h_L (bf16) and the bf16 orbital weights [K (n_up + n_dn)][h1].
 bool launch_orbitals_tc(const Shape& sh, const void* HL, int h1, const void* W16, const float* const* wbias,
                         const float* const* pi, const float* const* sig, int K, int aniso, const float* walkers,
-                        const double* nuclei, void* Phi, int64_t PW, float* orbP, int* status, cudaStream_t st) {
+                        const double* nuclei, void* Phi, int64_t PW, float* orbP, const float* envv, int* status,
+                        cudaStream_t st) {
   const int nmax = std::max(sh.n_up, sh.n_dn);
   const int nt = (int)std::min<int64_t>(128, round_up((int64_t)K * nmax, 32));
   CUtensorMap ta, tb;
@@ -736,6 +712,7 @@ bool launch_orbitals_tc(const Shape& sh, const void* HL, int h1, const void* W16
   a.PW = PW;
   a.orbP = orbP;
   a.bsplit = h1;
+  a.envv = envv;
   const bool full = sh.T > 1;
   a.tmem_cols = pow2_cols(3 * nt);
   launch_tc<tc::kEpiOrbital>(ta, tb, a, dim3(a.ctiles_up + ctiles_dn, sh.tiles), full, st);

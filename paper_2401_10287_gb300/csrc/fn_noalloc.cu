@@ -71,6 +71,7 @@ static size_t value_pass_layout(const fn_system* s, int B, unsigned char* base, 
   const size_t o_Phi = take((size_t)B * phi_walker_stride(s, 1) * sizeof(typename Mode::PhiT));
   const size_t o_prep = take((size_t)s->prep.total * sizeof(Cmp));
   const size_t o_prep16 = take((size_t)s->prep.total16 * sizeof(__nv_bfloat16));
+  const size_t o_envv = take(Mode::kMode == FN_BF16_MIXED ? (size_t)sh.R * s->cfg.n_dets * s->N * sizeof(float) : 0);
   const size_t o_status = take(sizeof(int) * 4);
   if (base && ws) {
     *ws = Workspace();
@@ -84,6 +85,7 @@ static size_t value_pass_layout(const fn_system* s, int B, unsigned char* base, 
     ws->prep = base + o_prep;
     ws->prep16 = base + o_prep16;
     ws->status = (int*)(base + o_status);
+    ws->envv = (float*)(base + o_envv);
     ws->base = base;
     ws->bytes = off;
     ws->cap_B = B;
