@@ -179,6 +179,7 @@ enum { kEpiLayer = 0, kEpiPlain = 1, kEpiOrbital = 2 };
 
 struct TcArgs {
   Shape sh;
+  int tiles;             // row tiles of 128; CTA y index strides over them (persistent)
   int nkb;               // k-blocks of 64
   int nt;                // output columns per CTA (32, 64 or 128)
   int h1;
@@ -437,8 +438,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Shape& sh = a.sh;
-  // blockIdx.x runs over the column tiles (fastest), so the CTAs that share an A tile run together
-  const int tile = blockIdx.y, ctile = blockIdx.x;
+  // blockIdx.x runs over the column tiles (fastest), so the CTAs that share an A tile run together;
+  // blockIdx.y strides over the row tiles (persistent CTAs, one per SM)
+  const int ctile = blockIdx.x;
+  const int my_tiles = a.tiles > (int)blockIdx.y ? (a.tiles - 1 - (int)blockIdx.y) / (int)gridDim.y + 1 : 0;
   // column tile: for orbitals it selects (spin, tile within the spin block)
   int spin = 0, ko0 = 0, brow0 = ctile * nt;
   if (EPI == kEpiOrbital) {
@@ -466,13 +469,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint64_t deadline = globaltimer() + kWaitNs * 8;
+  const uint64_t deadline = globaltimer() + kWaitNs * 8 * (uint64_t)(my_tiles > 0 ? my_tiles : 1);
 
   if (warp == 0) {
     if (lane == 0) {
       int issued = 0;
       bool ok = true;
-      for (int t = 0; t < T && ok; ++t) {
+      for (int item = 0; item < my_tiles * T && ok; ++item) {
+        const int tile = (int)blockIdx.y + (item / T) * (int)gridDim.y, t = item % T;
         const int arow = EPI == kEpiPlain ? tile * 128 : (int)(t * sh.R + (int64_t)tile * 128);
         for (int kb = 0; kb < nkb; ++kb, ++issued) {
           const int stage = issued % kStages;
@@ -498,9 +502,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = idesc_bf16(128, nt);
       int consumed = 0;
       bool ok = true;
-      for (int t = 0; t < T && ok; ++t) {
-        const int buf = t & 1;
-        const uint32_t use = (uint32_t)(t >> 1);
+      for (int item = 0; item < my_tiles * T && ok; ++item) {
+        const int buf = item & 1;
+        const uint32_t use = (uint32_t)(item >> 1);
         if (*abort_flag || !mbar_wait(acce + buf, (use & 1u) ^ 1u, deadline)) { ok = false; break; }
         fence_after();
         const uint32_t d = tmem + (uint32_t)(buf * nt);
@@ -534,9 +538,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ehalf = (warp - 2) >> 2;            // column half: chunks cc with cc % 2 == ehalf
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const int nchunks = nt / 32;
-    for (int t = 0; t < T; ++t) {
-      const int buf = t & 1;
-      const uint32_t use = (uint32_t)(t >> 1);
+    for (int item = 0; item < my_tiles * T; ++item) {
+      const int tile = (int)blockIdx.y + (item / T) * (int)gridDim.y, t = item % T;
+      const int buf = item & 1;
+      const uint32_t use = (uint32_t)(item >> 1);
       const bool ok = !*abort_flag && mbar_wait(accf + buf, use & 1u, deadline);
       if (epilogue_any(!ok)) {
         if (ethread == 0) {
@@ -620,6 +625,23 @@ static size_t tc_smem_bytes(int nt, int epi, bool split) {
   return 1024 + tc::kStages * (128 * 128 + (size_t)nt * 128 * (split ? 2 : 1)) + ep + 8 * (2 * tc::kStages + 5) + 16;
 }
 
+static int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+// Grid of column tiles x enough row-tile strides to give every SM one CTA.
+static dim3 persistent_grid(int ctiles, int tiles) {
+  const int per_col = std::max(1, sm_count() / std::max(1, ctiles));
+  return dim3(ctiles, std::min(tiles, per_col));
+}
+
 template <int EPI>
 static void launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const tc::TcArgs& a, dim3 grid, bool full,
                       cudaStream_t st) {
@@ -657,7 +679,8 @@ bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const 
   a.bsplit = ldx;
   const bool full = sh.T > 1;
   a.tmem_cols = pow2_cols(full ? 4 * nt : 2 * nt);
-  launch_tc<tc::kEpiLayer>(ta, tb, a, dim3(h1 / nt, sh.tiles), full, st);
+  a.tiles = sh.tiles;
+  launch_tc<tc::kEpiLayer>(ta, tb, a, persistent_grid(h1 / nt, sh.tiles), full, st);
   return true;
 }
 
@@ -681,7 +704,8 @@ bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int
   a.bias_rows = bias_rows;
   a.bsplit = ldb;
   a.tmem_cols = pow2_cols(2 * nt);
-  launch_tc<tc::kEpiPlain>(ta, tb, a, dim3(h1 / nt, (rows + 127) / 128), false, st);
+  a.tiles = (rows + 127) / 128;
+  launch_tc<tc::kEpiPlain>(ta, tb, a, persistent_grid(h1 / nt, a.tiles), false, st);
   return true;
 }
 
@@ -715,7 +739,8 @@ bool launch_orbitals_tc(const Shape& sh, const void* HL, int h1, const void* W16
   a.envv = envv;
   const bool full = sh.T > 1;
   a.tmem_cols = pow2_cols(3 * nt);
-  launch_tc<tc::kEpiOrbital>(ta, tb, a, dim3(a.ctiles_up + ctiles_dn, sh.tiles), full, st);
+  a.tiles = sh.tiles;
+  launch_tc<tc::kEpiOrbital>(ta, tb, a, persistent_grid(a.ctiles_up + ctiles_dn, sh.tiles), full, st);
   return true;
 }
 
