@@ -74,83 +74,99 @@ struct OrbBwdArgs {
   int h1, K, aniso, chunk;
 };
 
-template <typename Act, typename Cmp, typename Det, typename Wlk>
+// Thread per orbital (k, i) of one spin, looping over a chunk of walkers and that spin's
+// electrons j.  dP holds the projections P = h_L w + g on entry (written by a GEMM over
+// all rows); the kernel replaces P by dphi env in the spin's own columns of row (w, j),
+// zeroes the other spin's columns there, and accumulates the envelope gradients in
+// registers (MM >= the number of nuclei bounds the unrolled per-nucleus arrays).
+template <typename Cmp, typename Det, typename Wlk, int MM>
 __global__ void k_orb_bwd(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh, OrbBwdArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Cmp* hs = (Cmp*)smem_raw;
   const int spin = blockIdx.y;
-  const int n = spin ? sh.n_dn : sh.n_up;
+  const int n = spin ? sh.n_dn : sh.n_up, n_o = spin ? sh.n_up : sh.n_dn;
   if (n == 0) return;
   const int n_ko = a.K * n, ko = threadIdx.x;
   const bool active = ko < n_ko;
   const int k = active ? ko / n : 0, i = active ? ko % n : 0;
-  const int sig_sz = a.aniso ? 9 : 1;
-  const Cmp* wT = (const Cmp*)a.wT[spin];
   const Cmp* pi = (const Cmp*)a.pi[spin] + (int64_t)(active ? ko : 0) * sh.M;
-  const Cmp* sg = (const Cmp*)a.sig[spin] + (int64_t)(active ? ko : 0) * sh.M * sig_sz;
+  const Cmp* sg = (const Cmp*)a.sig[spin] + (int64_t)(active ? ko : 0) * sh.M * (a.aniso ? 9 : 1);
+  Cmp pim[MM], S[MM][9], acc_pi[MM], acc_sig[MM][9];
+#pragma unroll
+  for (int m = 0; m < MM; ++m) {
+    pim[m] = m < sh.M ? pi[m] : (Cmp)0;
+    acc_pi[m] = 0;
+#pragma unroll
+    for (int x = 0; x < 9; ++x) {
+      S[m][x] = m < sh.M ? (a.aniso ? sg[m * 9 + x] : (x == 0 ? sg[m] : (Cmp)0)) : (Cmp)0;
+      acc_sig[m][x] = 0;
+    }
+  }
   const int64_t PW1 = (int64_t)a.K * (sh.n_up * sh.n_up + sh.n_dn * sh.n_dn);
   const int64_t inv_off = spin ? (int64_t)a.K * sh.n_up * sh.n_up : 0;
-  const int ldp = a.K * sh.N, poff = spin ? a.K * sh.n_up : 0;
-  Cmp acc_pi[kMaxNuclei], acc_sig[kMaxNuclei * 9], em[kMaxNuclei];
-  for (int q = 0; q < sh.M; ++q) acc_pi[q] = 0;
-  for (int q = 0; q < sh.M * sig_sz; ++q) acc_sig[q] = 0;
+  const int ldp = a.K * sh.N, poff = spin ? a.K * sh.n_up : 0, poff_o = spin ? 0 : a.K * sh.n_up;
   const int w0 = blockIdx.x * a.chunk, w1 = min(sh.B, w0 + a.chunk);
+  Cmp* dP = (Cmp*)a.dP;
   for (int w = w0; w < w1; ++w) {
+    const Cmp cw = (Cmp)a.cw[w];
     for (int jj = 0; jj < n; ++jj) {
       const int j = jj + (spin ? sh.n_up : 0);
       const int64_t row = tile_row(w, j, sh.N, sh.wpt);
-      for (int c = threadIdx.x; c < a.h1; c += blockDim.x) hs[c] = (Cmp)ld((const Act*)a.HL + row * a.h1 + c);
-      __syncthreads();
-      if (active) {
-        Cmp P = ((const Cmp*)a.g[spin])[ko];
-        for (int c = 0; c < a.h1; ++c) P += hs[c] * wT[(int64_t)c * n_ko + ko];
-        const Wlk* rj = r + ((int64_t)w * sh.N + j) * 3;
-        Cmp env = 0;
-        Cmp dv[kMaxNuclei][3];
-        Cmp sv[kMaxNuclei];
-        for (int m = 0; m < sh.M; ++m) {
-          for (int c = 0; c < 3; ++c) dv[m][c] = (Cmp)((double)rj[c] - nuc[3 * m + c]);
-          Cmp s;
-          if (!a.aniso) {
-            s = sg[m] * f_sqrt(dv[m][0] * dv[m][0] + dv[m][1] * dv[m][1] + dv[m][2] * dv[m][2]);
-          } else {
-            const Cmp* S = sg + m * 9;
-            Cmp u2 = 0;
-            for (int x = 0; x < 3; ++x) {
-              const Cmp u = S[3 * x] * dv[m][0] + S[3 * x + 1] * dv[m][1] + S[3 * x + 2] * dv[m][2];
-              u2 += u * u;
-            }
-            s = f_sqrt(u2);
+      if (ko < a.K * n_o) dP[row * ldp + poff_o + ko] = (Cmp)0;
+      if (!active) continue;
+      const Cmp P = dP[row * ldp + poff + ko] + ((const Cmp*)a.g[spin])[ko];
+      const Wlk* rj = r + ((int64_t)w * sh.N + j) * 3;
+      Cmp dv[MM][3], sv[MM], em[MM];
+      Cmp env = 0;
+#pragma unroll
+      for (int m = 0; m < MM; ++m) {
+        if (m >= sh.M) break;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dv[m][c] = (Cmp)((double)rj[c] - nuc[3 * m + c]);
+        if (!a.aniso) {
+          sv[m] = S[m][0] * f_sqrt(dv[m][0] * dv[m][0] + dv[m][1] * dv[m][1] + dv[m][2] * dv[m][2]);
+        } else {
+          Cmp u2 = 0;
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            const Cmp u = S[m][3 * x] * dv[m][0] + S[m][3 * x + 1] * dv[m][1] + S[m][3 * x + 2] * dv[m][2];
+            u2 += u * u;
           }
-          sv[m] = s;
-          em[m] = f_exp(-s);
-          env += pi[m] * em[m];
+          sv[m] = f_sqrt(u2);
         }
-        const Cmp dphi = (Cmp)(a.cw[w] * (double)((const Det*)a.dPhi)[(int64_t)w * PW1 + inv_off +
-                                                                     (int64_t)k * n * n + i * n + jj]);
-        const Cmp dPv = dphi * env, denv = dphi * P;
-        ((Cmp*)a.dP)[row * ldp + poff + ko] = dPv;
-        for (int m = 0; m < sh.M; ++m) {
-          acc_pi[m] += denv * em[m];
-          const Cmp f = -denv * pi[m] * em[m];
-          if (!a.aniso) {
-            acc_sig[m] += f * f_sqrt(dv[m][0] * dv[m][0] + dv[m][1] * dv[m][1] + dv[m][2] * dv[m][2]);
-          } else {
-            const Cmp* S = sg + m * 9;
-            for (int x = 0; x < 3; ++x) {
-              const Cmp u = S[3 * x] * dv[m][0] + S[3 * x + 1] * dv[m][1] + S[3 * x + 2] * dv[m][2];
-              for (int y = 0; y < 3; ++y) acc_sig[m * 9 + 3 * x + y] += f * u * dv[m][y] / sv[m];
-            }
+        em[m] = f_exp(-sv[m]);
+        env += pim[m] * em[m];
+      }
+      const Cmp dphi = cw * (Cmp)((const Det*)a.dPhi)[(int64_t)w * PW1 + inv_off + (int64_t)k * n * n + i * n + jj];
+      const Cmp denv = dphi * P;
+      dP[row * ldp + poff + ko] = dphi * env;
+#pragma unroll
+      for (int m = 0; m < MM; ++m) {
+        if (m >= sh.M) break;
+        acc_pi[m] += denv * em[m];
+        const Cmp f = -denv * pim[m] * em[m];
+        if (!a.aniso) {
+          acc_sig[m][0] += f * f_sqrt(dv[m][0] * dv[m][0] + dv[m][1] * dv[m][1] + dv[m][2] * dv[m][2]);
+        } else {
+          const Cmp inv_s = (Cmp)1 / sv[m];
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            const Cmp u = S[m][3 * x] * dv[m][0] + S[m][3 * x + 1] * dv[m][1] + S[m][3 * x + 2] * dv[m][2];
+#pragma unroll
+            for (int y = 0; y < 3; ++y) acc_sig[m][3 * x + y] += f * u * dv[m][y] * inv_s;
           }
         }
       }
-      __syncthreads();
     }
   }
   if (active) {
-    for (int m = 0; m < sh.M; ++m) atomicAdd((Cmp*)a.gpi[spin] + (int64_t)ko * sh.M + m, acc_pi[m]);
-    for (int q = 0; q < sh.M * sig_sz; ++q)
-      atomicAdd((Cmp*)a.gsig[spin] + (int64_t)ko * sh.M * sig_sz + q, acc_sig[q]);
+#pragma unroll
+    for (int m = 0; m < MM; ++m) {
+      if (m >= sh.M) break;
+      atomicAdd((Cmp*)a.gpi[spin] + (int64_t)ko * sh.M + m, acc_pi[m]);
+      if (!a.aniso) atomicAdd((Cmp*)a.gsig[spin] + (int64_t)ko * sh.M + m, acc_sig[m][0]);
+      else
+#pragma unroll
+        for (int x = 0; x < 9; ++x) atomicAdd((Cmp*)a.gsig[spin] + ((int64_t)ko * sh.M + m) * 9 + x, acc_sig[m][x]);
+    }
   }
 }
 
@@ -200,15 +216,24 @@ struct PairBwdArgs {
 template <typename Cmp, typename Wlk>
 __global__ void __launch_bounds__(128) k_pair_bwd(const Wlk* __restrict__ r, Shape sh, PairBwdArgs a) {
   __shared__ Cmp red[4][32][33];
+  __shared__ Cmp sW[32][33];                                   // W_l[q][c], zero outside [h2][d_g]
   const int w = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = sh.N;
   const bool has_layer = a.l < a.L - 1;
+  if (has_layer)
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+      const int q = e >> 5, c = e & 31;
+      sW[q][c] = (q < a.h2 && c < a.d_g) ? ((const Cmp*)a.W)[q * a.d_g + c] : (Cmp)0;
+    }
+  __syncthreads();
+  // dW[q][lane] and dc[lane] of this warp's pairs, in registers (the q loop is unrolled)
   Cmp accW[32];
+#pragma unroll
   for (int q = 0; q < 32; ++q) accW[q] = 0;
   Cmp accc = 0;
   const Wlk* rw = r + (int64_t)w * N * 3;
   for (int p = warp; p < N * N; p += 4) {
-    const int i = p / N, j = p % N;
+    const int i = p / N, j = p - (p / N) * N;
     const int64_t pidx = ((int64_t)w * N + i) * N + j;
     // input g^l of this lane's channel
     Cmp gin = 0;
@@ -217,7 +242,8 @@ __global__ void __launch_bounds__(128) k_pair_bwd(const Wlk* __restrict__ r, Sha
     } else if (i != j && lane < 4) {
       const double d[3] = {(double)rw[3 * i] - (double)rw[3 * j], (double)rw[3 * i + 1] - (double)rw[3 * j + 1],
                            (double)rw[3 * i + 2] - (double)rw[3 * j + 2]};
-      gin = lane < 3 ? (Cmp)d[lane] : (Cmp)sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      gin = lane == 0 ? (Cmp)d[0] : lane == 1 ? (Cmp)d[1] : lane == 2 ? (Cmp)d[2]
+                                                : (Cmp)sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     }
     Cmp dgl = 0;
     if (has_layer) {
@@ -226,11 +252,11 @@ __global__ void __launch_bounds__(128) k_pair_bwd(const Wlk* __restrict__ r, Sha
       const Cmp t = a.l >= 1 ? gout - gin : gout;
       const Cmp dz = lane < a.h2 ? dgn * ((Cmp)1 - t * t) : (Cmp)0;
       accc += dz;
-      const Cmp* W = (const Cmp*)a.W;
-      for (int q = 0; q < a.h2; ++q) {
-        const Cmp dzq = __shfl_sync(0xffffffffu, dz, q);
-        accW[q] += dzq * gin;                                   // dW[q][lane]
-        if (lane < a.d_g) dgl += W[q * a.d_g + lane] * dzq;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const Cmp dzq = __shfl_sync(0xffffffffu, dz, q);      // zero for q >= h2
+        accW[q] += dzq * gin;                                  // dW[q][lane]
+        dgl += sW[q][lane] * dzq;
       }
       if (a.l >= 1) dgl += dgn;
     }
@@ -244,6 +270,7 @@ __global__ void __launch_bounds__(128) k_pair_bwd(const Wlk* __restrict__ r, Sha
   }
   if (!has_layer) return;
   // block reduction of dW (lane = column, q = row) and dc
+#pragma unroll
   for (int q = 0; q < 32; ++q) red[warp][q][lane] = accW[q];
   __syncthreads();
   for (int e = threadIdx.x; e < a.h2 * a.d_g; e += blockDim.x) {
@@ -286,9 +313,29 @@ void launch_backward(const fn_system* s, const void* walkers, const Shape& sh, c
   const int ldp = K * N;
   const int split = (int)std::max<int64_t>(1, std::min<int64_t>(64, R / 1024));
   cudaMemsetAsync(gradc, 0, sizeof(Cmp) * pl.total, st);
-  cudaMemsetAsync(ws.dP, 0, sizeof(Cmp) * R * ldp, st);
   cudaMemsetAsync(ws.dH, 0, sizeof(Cmp) * R * h1, st);
-  // orbitals + envelopes
+  // orbitals + envelopes: P = h_L w (both spins, every row), then the envelope kernel turns
+  // it into dP in place; rows that hold no electron are zeroed for the weight GEMMs below
+  {
+    ProfScope ps(s->prof, kProfBwdGemm, st);
+    for (int q = 0; q < 2; ++q) {
+      const int n_q = q ? s->n_dn : s->n_up;
+      if (!n_q) continue;
+      gemm<Act, Cmp, Cmp, Cmp>(st, (int)R, K * n_q, h1, (const Act*)ws.HL, h1, 1, prep + pl.wT[q], K * n_q, 1,
+                               (Cmp*)ws.dP + (q ? K * s->n_up : 0), ldp, 1, (const Cmp*)nullptr, 0, 1, false);
+    }
+  }
+  {
+    const size_t row_bytes = sizeof(Cmp) * ldp;
+    const int used = sh.wpt * N;
+    if (used < kTileRows)
+      cudaMemset2DAsync((char*)ws.dP + used * row_bytes, kTileRows * row_bytes, 0, (kTileRows - used) * row_bytes,
+                        sh.tiles, st);
+    const int last = sh.B - (sh.tiles - 1) * sh.wpt;
+    if (last < sh.wpt)
+      cudaMemsetAsync((char*)ws.dP + ((int64_t)(sh.tiles - 1) * kTileRows + (int64_t)last * N) * row_bytes, 0,
+                      (size_t)(sh.wpt - last) * N * row_bytes, st);
+  }
   {
     OrbBwdArgs a{};
     a.HL = ws.HL;
@@ -298,11 +345,14 @@ void launch_backward(const fn_system* s, const void* walkers, const Shape& sh, c
     }
     a.dPhi = ws.dPhi; a.cw = weights; a.dP = ws.dP;
     a.h1 = h1; a.K = K; a.aniso = s->cfg.envelope == FN_ENV_ANISOTROPIC;
-    a.chunk = std::max(1, sh.B / (2 * s->sm_count));
+    a.chunk = std::max(1, sh.B / (4 * s->sm_count));
     const int threads = (int)std::min<int64_t>(1024, round_up((int64_t)K * std::max(s->n_up, s->n_dn), 32));
     dim3 grid((sh.B + a.chunk - 1) / a.chunk, 2);
     ProfScope ps(s->prof, kProfBwdOrb, st);
-    k_orb_bwd<Act, Cmp, Det, Wlk><<<grid, threads, sizeof(Cmp) * h1, st>>>(r, s->d_nuclei, sh, a);
+    if (s->M <= 2) k_orb_bwd<Cmp, Det, Wlk, 2><<<grid, threads, 0, st>>>(r, s->d_nuclei, sh, a);
+    else if (s->M <= 4) k_orb_bwd<Cmp, Det, Wlk, 4><<<grid, threads, 0, st>>>(r, s->d_nuclei, sh, a);
+    else if (s->M <= 8) k_orb_bwd<Cmp, Det, Wlk, 8><<<grid, threads, 0, st>>>(r, s->d_nuclei, sh, a);
+    else k_orb_bwd<Cmp, Det, Wlk, kMaxNuclei><<<grid, threads, 0, st>>>(r, s->d_nuclei, sh, a);
   }
   const int ns[2] = {s->n_up, s->n_dn};
   for (int q = 0; q < 2; ++q) {

@@ -15,9 +15,23 @@ __device__ __forceinline__ void st(float* p, double v) { *p = (float)v; }
 __device__ __forceinline__ void st(double* p, float v) { *p = (double)v; }
 __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ void st(__nv_bfloat16* p, double v) { *p = __float2bfloat16_rn((float)v); }
+// two adjacent elements at an even element offset from an aligned base
+__device__ __forceinline__ void st2(double* p, double a, double b) { *(double2*)p = make_double2(a, b); }
+__device__ __forceinline__ void st2(float* p, float a, float b) { *(float2*)p = make_float2(a, b); }
+__device__ __forceinline__ void st2(__nv_bfloat16* p, float a, float b) { *(__nv_bfloat162*)p = __floats2bfloat162_rn(a, b); }
 
 __device__ __forceinline__ float f_tanh(float x) { return tanhf(x); }
 __device__ __forceinline__ double f_tanh(double x) { return tanh(x); }
+// tanh for the BF16-storage mode, whose activations are rounded to 8 mantissa bits:
+// tanh x = 1 - 2 / (e^{2x} + 1) with the fast exponential and division intrinsics.  Its
+// absolute error is a few 1e-7 (cancellation near x = 0 costs relative, not absolute,
+// accuracy); e^{2x} overflowing to inf gives exactly 1, underflowing to 0 gives -1.
+__device__ __forceinline__ float tanh_fast(float x) { return 1.0f - __fdividef(2.0f, __expf(2.0f * x) + 1.0f); }
+template <typename Act> __device__ __forceinline__ float act_tanh(float x) {
+  if constexpr (std::is_same<Act, __nv_bfloat16>::value) return tanh_fast(x);
+  else return tanhf(x);
+}
+template <typename Act> __device__ __forceinline__ double act_tanh(double x) { return tanh(x); }
 __device__ __forceinline__ float f_exp(float x) { return expf(x); }
 __device__ __forceinline__ double f_exp(double x) { return exp(x); }
 __device__ __forceinline__ float f_sqrt(float x) { return sqrtf(x); }

@@ -180,18 +180,18 @@ __global__ void k_features_mean(const Wlk* __restrict__ r, const double* __restr
 }
 
 // ---------------------------------------------------------------------------------------
-// two-electron stream.  A pair (i, j) depends only on r_i and r_j, so its jet has 8 rows:
-// value, d/dr_i (3), d/dr_j (3), Laplacian.  Pairs never interact across layers, so a
-// thread carries its pair (and, in the full pass, one jet row) through every layer; the
-// channels live in registers and the layer weights, transposed, in shared memory
+// two-electron stream.  A pair (i, j) depends only on r_i - r_j, so d/dr_j = -d/dr_i and
+// its jet reduces to 5 rows: value, d/dr_i (3), Laplacian.  Pairs never interact across
+// layers, so a thread carries its pair (and, in the full pass, one jet row) through every
+// layer; the channels live in registers and the layer weights, transposed, in shared memory
 // (every thread reads the same weight at the same time: broadcast).
-//   full pass : one CTA per (walker, electron i), 8 threads per partner j (one per jet
-//               row); the value row's tanh and the tangent rows' sum of squares are
-//               exchanged with shuffles inside the 8-lane group;
+//   full pass : a CTA per (walker, run of electrons i), 5 lanes per pair (one per jet row);
+//               the value row's tanh and the tangent rows' squares are exchanged with
+//               shuffles inside the group;
 //   value pass: one CTA per walker, one thread per pair.
-// The spin means over j are accumulated with shared-memory atomics and written to the
-// mean-g columns of every layer's input X_l; the derivative of mean_j g_ij along r_j
-// (j != i) is (1/n_spin) d g_ij / d r_j, written directly.
+// The spin means over j are reduced in shared memory and written to the mean-g columns of
+// every layer's input X_l; the derivative of mean_j g_ij along r_j (j != i) is
+// (1/n_spin) d g_ij / d r_j, written directly.
 // ---------------------------------------------------------------------------------------
 struct PairArgs {
   void* X[kMaxLayers];
@@ -259,23 +259,32 @@ __device__ __forceinline__ void pair_matvec(const Cmp* __restrict__ sWl, const C
   }
 }
 
-// Full pass: CTA per (walker, electron i); thread (j, jet row rr).  Per layer the rows
-// that are summed over j (value, Laplacian, d/dr_i) are staged in shared memory and
-// reduced per (spin, row, channel); the d/dr_j rows are written straight to their slab.
+// Full pass.  The pair features depend only on r_i - r_j, so at every layer
+// d g / d r_j = -d g / d r_i and the Laplacian over both electrons is 2 d^2 g / d r_i^2: a
+// pair's jet has 5 rows (value, d/dr_i along x, y, z, Laplacian), carried by a group of 5
+// lanes, 6 groups per warp.  A CTA covers walker w and `ib` consecutive electrons i, all
+// their partners j.  Per layer every pair's rows are staged in shared memory; from there
+// the CTA writes the spin means over j (value, Laplacian, d/dr_i) and the d/dr_j slabs
+// (-d/dr_i / n_spin) to the layer input, adjacent columns from adjacent threads.
+constexpr int kPairLanes = 5, kPairGroups = 6;
+
 template <typename Act, typename Cmp, typename Wlk>
-__global__ void __launch_bounds__(256) k_pair_full(const Wlk* __restrict__ r, Shape sh, PairArgs a) {
+__global__ void __launch_bounds__(256) k_pair_full(const Wlk* __restrict__ r, Shape sh, PairArgs a, int ib) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cmp* sW = (Cmp*)smem_raw;                                  // [L-1][32][32]
   Cmp* sc = sW + (a.L - 1) * kMaxH2 * kMaxH2;               // [L-1][32]
-  Cmp* gs = sc + (a.L - 1) * kMaxH2;                        // [N][8][33]
-  const int w = blockIdx.x / sh.N, i = blockIdx.x % sh.N;
-  const int j = threadIdx.x >> 3, rr = threadIdx.x & 7;      // partner, jet row
+  Cmp* gs = sc + (a.L - 1) * kMaxH2;                        // [ib][N][5][33]: value, lap, d/dr_i x, y, z
+  const int blocks_per_walker = (sh.N + ib - 1) / ib;
+  const int w = blockIdx.x / blocks_per_walker, i0 = (blockIdx.x % blocks_per_walker) * ib;
+  const int n_i = min(ib, sh.N - i0);
+  const int lane = threadIdx.x & 31, grp = lane / kPairLanes;
+  const int q = lane - grp * kPairLanes;
+  const int p = (threadIdx.x >> 5) * kPairGroups + grp;      // pair index within the CTA
+  const bool live = grp < kPairGroups && p < n_i * sh.N;
+  const int ii = live ? p / sh.N : 0, j = live ? p % sh.N : 0, i = i0 + ii;
+  const int base = grp < kPairGroups ? grp * kPairLanes : 0;  // value lane of this group
   stage_pair_weights(a, sW, sc);
-  const int64_t row = tile_row(w, i, sh.N, sh.wpt);
-  const bool live = j < sh.N;
-  const int sj = j < sh.n_up ? 0 : 1;
-  const int nsj = sj ? sh.n_dn : sh.n_up;
-  const Cmp inv_n = (Cmp)1 / (Cmp)(nsj > 0 ? nsj : 1);
+  const int srow = q == 0 ? 0 : (q == 4 ? 1 : q + 1);       // this lane's row in the staging area
   Cmp g[kMaxH2];
 #pragma unroll
   for (int c = 0; c < kMaxH2; ++c) g[c] = 0;
@@ -284,15 +293,17 @@ __global__ void __launch_bounds__(256) k_pair_full(const Wlk* __restrict__ r, Sh
     double d[3];
     for (int c = 0; c < 3; ++c) d[c] = (double)rw[3 * i + c] - (double)rw[3 * j + c];
     const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    if (rr == 0) {
+    if (q == 0) {
       g[0] = (Cmp)d[0]; g[1] = (Cmp)d[1]; g[2] = (Cmp)d[2]; g[3] = (Cmp)dist;
-    } else if (rr < 7) {
-      const int c = (rr - 1) % 3;
-      const Cmp sgn = rr < 4 ? (Cmp)1 : (Cmp)-1;            // d/dr_i or d/dr_j
-      g[c] = sgn;
-      g[3] = sgn * (Cmp)(d[c] / dist);
+    } else if (q == 4) {
+      g[3] = (Cmp)(4.0 / dist);                              // Laplacian of |r_i - r_j| over both electrons
     } else {
-      g[3] = (Cmp)(4.0 / dist);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)                            // static indices keep g and d in registers
+        if (c == q - 1) {
+          g[c] = (Cmp)1;
+          g[3] = (Cmp)(d[c] / dist);
+        }
     }
   }
   for (int l = 0; l < a.L; ++l) {
@@ -300,47 +311,62 @@ __global__ void __launch_bounds__(256) k_pair_full(const Wlk* __restrict__ r, Sh
     Act* X = (Act*)a.X[l];
     const int64_t slab = sh.R * a.ldx[l];
     if (live) {
+      Cmp* gr = gs + (p * 5 + srow) * 33;
 #pragma unroll
       for (int c = 0; c < kMaxH2; ++c)
-        if (c < dg) gs[(j * 8 + rr) * 33 + c] = g[c];
-      if (rr >= 4 && rr <= 6 && j != i) {                    // d/dr_j row: its own slab
-        Act* o = X + (1 + 3 * j + (rr - 4)) * slab + row * a.ldx[l] + a.col0[l];
-#pragma unroll
-        for (int c = 0; c < kMaxH2; ++c)
-          if (c < dg) {
-            st(o + sj * dg + c, g[c] * inv_n);
-            st(o + (1 - sj) * dg + c, (Cmp)0);
-          }
-      }
+        if (c < dg) gr[c] = g[c];
     }
     __syncthreads();
-    // sums over j of the value (slab 0), Laplacian (slab T-1) and d/dr_i rows (slabs 1 + 3i + c)
-    for (int e = threadIdx.x; e < 2 * 5 * dg; e += blockDim.x) {
-      const int s2 = e / (5 * dg), q = (e / dg) % 5, c = e % dg;
-      const int lo = s2 ? sh.n_up : 0, hi = s2 ? sh.N : sh.n_up;
-      const int rsrc = q == 0 ? 0 : (q == 1 ? 7 : q - 1);
-      Cmp sum = 0;
-      for (int jj = lo; jj < hi; ++jj) sum += gs[(jj * 8 + rsrc) * 33 + c];
-      const Cmp v = hi > lo ? sum / (Cmp)(hi - lo) : (Cmp)0;
-      const int t = q == 0 ? 0 : (q == 1 ? sh.T - 1 : 1 + 3 * i + (q - 2));
-      st(X + t * slab + row * a.ldx[l] + a.col0[l] + s2 * dg + c, v);
+    // The layer input row of electron i holds [mean over up partners, mean over down
+    // partners], 2 d_g columns from col0.  A warp writes one row at a time, lane c the
+    // column pair (2c, 2c + 1); all loop bounds and row indices are warp-uniform.
+    const int64_t ldx = a.ldx[l];
+    Act* Xc = X + a.col0[l];
+    const int warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    const int col = 2 * lane, half0 = col < dg ? 0 : 1, half1 = col + 1 < dg ? 0 : 1;
+    const int c0 = col - half0 * dg, c1 = col + 1 - half1 * dg;
+    // d/dr_j slabs (j != i): -d g_ij / d r_i / n_spin(j) in j's spin half, 0 in the other
+    for (int pp = warp; pp < n_i * sh.N; pp += n_warps) {
+      const int e_i = pp / sh.N, jj = pp - e_i * sh.N;
+      if (jj == i0 + e_i || lane >= dg) continue;
+      const int sjj = jj < sh.n_up ? 0 : 1;
+      const Cmp scale = -(Cmp)1 / (Cmp)(sjj ? sh.n_dn : sh.n_up);
+      const int64_t row = tile_row(w, i0 + e_i, sh.N, sh.wpt) * ldx;
+#pragma unroll
+      for (int axis = 0; axis < 3; ++axis) {
+        const Cmp* src = gs + (pp * 5 + 2 + axis) * 33;
+        st2(Xc + (1 + 3 * jj + axis) * slab + row + col, half0 == sjj ? src[c0] * scale : (Cmp)0,
+            half1 == sjj ? src[c1] * scale : (Cmp)0);
+      }
+    }
+    // value, Laplacian and d/dr_i rows: spin means over partners
+    for (int rr = warp; rr < n_i * 5; rr += n_warps) {
+      if (lane >= dg) continue;
+      const int e_i = rr / 5, qq = rr - 5 * e_i, ie = i0 + e_i;
+      const Cmp* src = gs + (e_i * sh.N * 5 + qq) * 33;
+      Cmp up0 = 0, up1 = 0, dn0 = 0, dn1 = 0;
+      for (int jj = 0; jj < sh.n_up; ++jj) { up0 += src[jj * 165 + c0]; up1 += src[jj * 165 + c1]; }
+      for (int jj = sh.n_up; jj < sh.N; ++jj) { dn0 += src[jj * 165 + c0]; dn1 += src[jj * 165 + c1]; }
+      const Cmp iu = sh.n_up ? (Cmp)1 / (Cmp)sh.n_up : (Cmp)0, id = sh.n_dn ? (Cmp)1 / (Cmp)sh.n_dn : (Cmp)0;
+      const int t = qq == 0 ? 0 : (qq == 1 ? sh.T - 1 : 1 + 3 * ie + (qq - 2));
+      st2(Xc + t * slab + tile_row(w, ie, sh.N, sh.wpt) * ldx + col, half0 ? dn0 * id : up0 * iu,
+          half1 ? dn1 * id : up1 * iu);
     }
     if (l == a.L - 1) break;
     __syncthreads();
     Cmp z[kMaxH2];
-    pair_matvec(sW + l * kMaxH2 * kMaxH2, sc + l * kMaxH2, rr == 0, dg, g, z);
-    // tanh jets: h from the value row, sum of squares of the 6 tangent rows
-    const int base = threadIdx.x & 24;
+    pair_matvec(sW + l * kMaxH2 * kMaxH2, sc + l * kMaxH2, q == 0, dg, g, z);
 #pragma unroll
     for (int c = 0; c < kMaxH2; ++c) {
+      // h and 1 - h^2 from the value lane; the 6 tangent rows give 2 (z_x^2 + z_y^2 + z_z^2)
       const Cmp zv = __shfl_sync(0xffffffffu, z[c], base);
-      const Cmp h = f_tanh(zv);
+      const Cmp zx = __shfl_sync(0xffffffffu, z[c], base + 1);
+      const Cmp zy = __shfl_sync(0xffffffffu, z[c], base + 2);
+      const Cmp zz = __shfl_sync(0xffffffffu, z[c], base + 3);
+      const Cmp h = act_tanh<Act>(zv);
       const Cmp dh = (Cmp)1 - h * h;
-      Cmp sq = (rr >= 1 && rr <= 6) ? z[c] * z[c] : (Cmp)0;
-      sq += __shfl_xor_sync(0xffffffffu, sq, 1);
-      sq += __shfl_xor_sync(0xffffffffu, sq, 2);
-      sq += __shfl_xor_sync(0xffffffffu, sq, 4);
-      Cmp out = rr == 0 ? h : (rr == 7 ? dh * z[c] - (Cmp)2 * h * dh * sq : dh * z[c]);
+      Cmp out = q == 0 ? h : dh * z[c];
+      if (q == 4) out -= (Cmp)4 * h * dh * (zx * zx + zy * zy + zz * zz);
       if (c >= a.h2) out = 0;
       g[c] = (l > 0 ? g[c] : (Cmp)0) + out;
     }
@@ -392,7 +418,7 @@ __global__ void __launch_bounds__(512) k_pair_value(const Wlk* __restrict__ r, S
       for (int c = 0; c < kMaxH2; ++c) g[c] = c < dg ? gp[c] : (Cmp)0;
       pair_matvec(sW + l * kMaxH2 * kMaxH2, sc + l * kMaxH2, true, dg, g, z);
 #pragma unroll
-      for (int c = 0; c < kMaxH2; ++c) g[c] = (l > 0 ? g[c] : (Cmp)0) + (c < a.h2 ? f_tanh(z[c]) : (Cmp)0);
+      for (int c = 0; c < kMaxH2; ++c) g[c] = (l > 0 ? g[c] : (Cmp)0) + (c < a.h2 ? act_tanh<Act>(z[c]) : (Cmp)0);
 #pragma unroll
       for (int c = 0; c < kMaxH2; ++c)
         if (c < a.h2) gp[c] = g[c];
@@ -608,11 +634,18 @@ __global__ void k_orbital_fixup(const Wlk* __restrict__ r, const double* __restr
 template <typename Wlk>
 __global__ void k_envelope_values(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh, OrbArgs a,
                                   float* __restrict__ envv) {
-  const int w = blockIdx.x / sh.N, j = blockIdx.x % sh.N;
-  const int spin = j < sh.n_up ? 0 : 1;
+  // one thread per (walker, electron j, orbital of j's spin); K n_s orbitals per electron
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int per_walker = a.K * (sh.n_up * sh.n_up + sh.n_dn * sh.n_dn);
+  if (gid >= (int64_t)sh.B * per_walker) return;
+  const int w = (int)(gid / per_walker);
+  int rem = (int)(gid % per_walker);
+  const int up_block = a.K * sh.n_up * sh.n_up;
+  const int spin = rem < up_block ? 0 : 1;
+  if (spin) rem -= up_block;
   const int n_s = spin ? sh.n_dn : sh.n_up;
-  const int ko = threadIdx.x;
-  if (ko >= a.K * n_s) return;
+  const int j = (spin ? sh.n_up : 0) + rem / (a.K * n_s);
+  const int ko = rem % (a.K * n_s);
   const int64_t row = tile_row(w, j, sh.N, sh.wpt);
   const Wlk* rj = r + ((int64_t)w * sh.N + j) * 3;
   const float* pi = (const float*)a.pi[spin] + (int64_t)ko * sh.M;
@@ -720,10 +753,19 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     const size_t wbytes = sizeof(Cmp) * ((L - 1) * kMaxH2 * kMaxH2 + (L - 1) * kMaxH2);
     ProfScope ps(s->prof, full ? kProfPairFull : kProfPair, st);
     if (full) {
-      const size_t smem = wbytes + sizeof(Cmp) * sh.N * 8 * 33;
-      const int threads = (int)round_up(8 * sh.N, 32);
+      // electrons per CTA: the fewest warps per walker with at most 8 warps per CTA
+      const int per_warp = kPairGroups;
+      int ib = 1, best = INT32_MAX;
+      for (int c = 1; c <= sh.N && c * sh.N <= 8 * per_warp; ++c) {
+        const int full = sh.N / c, rem = sh.N % c;
+        const int warps = full * ((c * sh.N + per_warp - 1) / per_warp) + (rem ? (rem * sh.N + per_warp - 1) / per_warp : 0);
+        if (warps <= best) { best = warps; ib = c; }
+      }
+      const int warps = (ib * sh.N + per_warp - 1) / per_warp;
+      const size_t smem = wbytes + sizeof(Cmp) * ib * sh.N * 5 * 33;
+      const int64_t blocks = (int64_t)sh.B * ((sh.N + ib - 1) / ib);
       cudaFuncSetAttribute(k_pair_full<Act, Cmp, Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_pair_full<Act, Cmp, Wlk><<<(unsigned)((int64_t)sh.B * sh.N), threads, smem, st>>>(r, sh, pa);
+      k_pair_full<Act, Cmp, Wlk><<<(unsigned)blocks, 32 * warps, smem, st>>>(r, sh, pa, ib);
     } else {
       const size_t smem = wbytes + sizeof(Cmp) * sh.N * sh.N * 33;
       const int threads = (int)std::min<int64_t>(512, round_up((int64_t)sh.N * sh.N, 32));
@@ -791,9 +833,8 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     if (Mode::kMode == FN_BF16_MIXED) {
       {
       ProfScope ps(s->prof, full ? kProfOrbFull : kProfOrbValue, st);
-      const int ko_env = s->cfg.n_dets * std::max(s->n_up, s->n_dn);
-      k_envelope_values<Wlk><<<(unsigned)((int64_t)sh.B * sh.N), (unsigned)round_up(ko_env, 32), 0, st>>>(
-          r, s->d_nuclei, sh, oa, ws.envv);
+      const int64_t n_env = (int64_t)sh.B * s->cfg.n_dets * (s->n_up * s->n_up + s->n_dn * s->n_dn);
+      k_envelope_values<Wlk><<<(unsigned)((n_env + 255) / 256), 256, 0, st>>>(r, s->d_nuclei, sh, oa, ws.envv);
       const float* wb[2] = {(const float*)oa.g[0], (const float*)oa.g[1]};
       const float* pis[2] = {(const float*)oa.pi[0], (const float*)oa.pi[1]};
       const float* sgs[2] = {(const float*)oa.sig[0], (const float*)oa.sig[1]};
