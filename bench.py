@@ -153,7 +153,7 @@ def run_reference(args):
     return 0
 
 
-def _algorithmic(cls, B, N, a, T_full, act_bytes):
+def _algorithmic(cls, B, N, a, T_full, act_bytes, launches=1):
     """Algorithmic work of one launch of a kernel class at this workload:
     returns (amount, kind) with kind "bytes" (HBM-bound), "flop" (FP32/tensor) or "flop64"."""
     M = 2
@@ -162,18 +162,31 @@ def _algorithmic(cls, B, N, a, T_full, act_bytes):
     L = a.n_layers
     R = int(np.ceil(B / (128 // N))) * 128
     k_self = [4 * M + 8] + [h1 + 2 * h2] * (L - 1)
+    d_h = [4 * M] + [h1] * (L - 1)
+    if cls == "bwd_gemm":
+        # every backward GEMM of one gradient pass over the B N electron rows, averaged
+        # over the class's launches: orbital projections, their weight gradient and input
+        # gradient, then per layer dV_self, dU, dX and (l >= 1) dHbar
+        rows = B * N
+        fl = 3 * 2.0 * rows * K * N * h1
+        for l in range(L):
+            fl += 2 * 2.0 * rows * k_self[l] * h1 + 2.0 * (2 * d_h[l]) * h1 * B
+            if l >= 1:
+                fl += 2.0 * B * (2 * d_h[l]) * h1
+        return fl / max(1, launches), "flop"
     if cls in ("layer_full", "layer_value"):
         T = T_full if cls == "layer_full" else 1
-        # per layer: X_l read, h_{l+1} written, mean-field term read, spin means written;
-        # averaged over the L launches of one pass
-        per = [T * R * (k + h1) * act_bytes + T * B * h1 * 4 + T * B * 2 * h1 * act_bytes for k in k_self]
+        # per layer: X_l read, h_{l+1} written, mean-field term read; averaged over the L
+        # launches of one pass (the spin means of h_{l+1} are a separate pass)
+        per = [T * R * (k + h1) * act_bytes + T * B * h1 * 4 for k in k_self]
         return float(np.mean(per)), "bytes"
     if cls == "det_full":
         # per walker, determinant k, spin: 3N tangent items x 2 n^3 + Laplacian trace + LU/inverse
         return float(B * K * 2 * (3 * N * 2 * n ** 3 + 2 * n * n + 3 * n ** 3)), "flop64"
     if cls == "pair_full":
-        # 8 jet rows per ordered pair, L-1 layers of h2 x d_g
-        return float(B * N * N * 8 * 2 * (4 * h2 + (L - 2) * h2 * h2)), "flop"
+        # 5 jet rows per ordered pair (value, d/dr_i, Laplacian; d/dr_j = -d/dr_i),
+        # L-1 layers of h2 x d_g
+        return float(B * N * N * 5 * 2 * (4 * h2 + (L - 2) * h2 * h2)), "flop"
     if cls == "orbitals_full":
         return float(2.0 * B * N * T_full * h1 * K * n), "flop"
     return None, None
@@ -280,7 +293,7 @@ def run_mine(args):
     cls, (launches, total_ms) = dom
     T_full = 3 * N + 2
     act_bytes = 2 if prec == P.BF16_MIXED else (8 if prec == P.FP64 else 4)
-    work, kind = _algorithmic(cls, B, N, a, T_full, act_bytes)
+    work, kind = _algorithmic(cls, B, N, a, T_full, act_bytes, launches)
     roof = None
     if work is not None:
         avg_s = total_ms / launches / 1000.0

@@ -433,6 +433,43 @@ __global__ void __launch_bounds__(512) k_pair_value(const Wlk* __restrict__ r, S
   }
 }
 
+// Spin means of a BF16 stream-layer output, the next layer's mean-field input:
+// Hbar[t][w][s h1 + c] = mean over the electrons i of spin s of Y[t][row(w, i)][c].
+// One thread per (slab, walker, spin, 8 columns); a warp reads 512 contiguous bytes of a row.
+__global__ void k_spin_means_bf16(Shape sh, const __nv_bfloat16* __restrict__ Y, int ldy, int h1,
+                                  __nv_bfloat16* __restrict__ Hbar) {
+  const int g8 = h1 >> 3;
+  const int64_t n = (int64_t)sh.T * sh.B * 2 * g8;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c8 = (int)(e % g8);
+    const int64_t rest = e / g8;
+    const int s2 = (int)(rest & 1);
+    const int64_t tw = rest >> 1;
+    const int w = (int)(tw % sh.B), t = (int)(tw / sh.B);
+    const int lo = s2 ? sh.n_up : 0, hi = s2 ? sh.N : sh.n_up;
+    float acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+    const __nv_bfloat16* base = Y + (int64_t)t * sh.R * ldy + 8 * c8;
+    for (int i = lo; i < hi; ++i) {
+      const uint4 u = *(const uint4*)(base + tile_row(w, i, sh.N, sh.wpt) * ldy);
+      const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 f = __bfloat1622float2(p2[k]);
+        acc[2 * k] += f.x;
+        acc[2 * k + 1] += f.y;
+      }
+    }
+    const float sc = hi > lo ? 1.0f / (float)(hi - lo) : 0.f;
+    uint4 o;
+    __nv_bfloat162* q = (__nv_bfloat162*)&o;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = __floats2bfloat162_rn(acc[2 * k] * sc, acc[2 * k + 1] * sc);
+    *(uint4*)(Hbar + ((int64_t)t * sh.B + w) * 2 * h1 + s2 * h1 + 8 * c8) = o;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // one-electron layer: for every 128-row walker tile and 64 output columns, loop over
 // the tangent slabs: value first (h = tanh z), then every gradient slab
@@ -804,8 +841,15 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     if (Mode::kMode == FN_BF16_MIXED) {
       const __nv_bfloat16* Vs16 = (const __nv_bfloat16*)ws.prep16 + s->prep.Vs16[l];
       if (!launch_layer_tc(sh, la.X, la.ldx, la.k_self, Vs16, (const float*)la.Mterm, la.Y, la.ldy, la.residual,
-                           la.Hbar_out, (float*)la.act_out, h1, ws.status, st))
+                           (float*)la.act_out, h1, ws.status, st))
         const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
+      if (!last) {
+        ProfScope pm(s->prof, kProfSpinMeans, st);
+        const int64_t n = (int64_t)sh.T * sh.B * 2 * (h1 / 8);
+        const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)s->sm_count * 64);
+        k_spin_means_bf16<<<blocks, 256, 0, st>>>(sh, (const __nv_bfloat16*)la.Y, la.ldy, h1,
+                                                  (__nv_bfloat16*)la.Hbar_out);
+      }
       continue;
     }
     const size_t smem = sizeof(Cmp) * (32 * 132 + 32 * 64 + 128 * 65);

@@ -178,7 +178,7 @@ fn_status upload_prep_descs(fn_system* s);
 
 // Tensor-core one-electron layer (BF16 mode); false if a TMA tensor map could not be built.
 bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const void* Vs16, const float* Mterm, void* Y,
-                     int ldy, int residual, void* Hbar_out, float* act_out, int h1, int* status, cudaStream_t st);
+                     int ldy, int residual, float* act_out, int h1, int* status, cudaStream_t st);
 bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int ldb, int h1, float* C,
                     const float* bias, int bias_rows, int* status, cudaStream_t st);
 bool launch_orbitals_tc(const Shape& sh, const void* HL, int h1, const void* W16, const float* const* wbias,

@@ -3,14 +3,17 @@
 //
 // Per CTA: 128 electron rows (one walker-aligned tile) x N_t output columns, looping
 // over every tangent slab t (value, 3N gradient slabs, Laplacian):
-//   warp 0      TMA producer: X_l[t] tile (128 x 64 bf16) and V_self tile (N_t x 64) per
-//               k-block into a 4-stage shared-memory ring (128B swizzle);
+//   warp 0      TMA producer: X_l[t] tile (128 x 64 bf16) and the V_self tiles (N_t x 64,
+//               high and low BF16 parts) per k-block into a kStages-deep shared-memory
+//               ring (128B swizzle);
 //   warp 1      allocates tensor memory; one lane issues tcgen05.mma (M=128, N=N_t, K=16)
 //               into a double-buffered accumulator and commits to mbarriers;
-//   warps 2..5  epilogue, one TMEM lane (= row) per thread: z = acc + M[t][walker];
-//               slab 0: h = tanh z (kept in TMEM), slabs 1..3N: (1 - h^2) z and the running
-//               sum of z^2 (kept in TMEM), Laplacian slab: (1 - h^2) z - 2 h (1 - h^2) sum;
-//               plus the residual, the BF16 store and the spin means of the output.
+//   warps 2..9  epilogue, one TMEM lane (= row) per thread, two warps per lane quarter
+//               (column halves): z = acc + M[t][walker] (M[t] staged in shared memory by
+//               cp.async one slab ahead); slab 0: h = tanh z (kept in TMEM), slabs 1..3N:
+//               (1 - h^2) z and the running sum of z^2 (kept in TMEM), Laplacian slab:
+//               (1 - h^2) z - 2 h (1 - h^2) sum; plus the residual (loaded before the
+//               accumulator wait) and the BF16 store.
 // Tensor memory columns: [0, 2 N_t) accumulators, [2 N_t, 3 N_t) h, [3 N_t, 4 N_t) sum z^2.
 //
 // Every wait is bounded (1 s of %globaltimer); on expiry the CTA records a timeout bit in
@@ -27,7 +30,7 @@
 namespace fn {
 namespace tc {
 
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 constexpr int kMaxNucleiTc = 16;
 constexpr int kBlockK = 64;                     // bf16 elements per 128-byte swizzled row
 constexpr int kEpiWarps = 8;                   // two warps per TMEM lane quarter
@@ -156,6 +159,34 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
       : "memory");
 }
 
+// Three 16-column loads (accumulator, h, sum of squares) under one completion wait.
+__device__ __forceinline__ void tmem_ld16x3(uint32_t ta, uint32_t tb, uint32_t tc_, uint32_t (&a)[16],
+                                            uint32_t (&b)[16], uint32_t (&c)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%48];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, "
+      "%29, %30, %31}, [%49];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, "
+      "%45, %46, %47}, [%50];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]),
+        "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(b[0]),
+        "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]), "=r"(b[8]), "=r"(b[9]),
+        "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15]), "=r"(c[0]), "=r"(c[1]),
+        "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7]), "=r"(c[8]), "=r"(c[9]), "=r"(c[10]),
+        "=r"(c[11]), "=r"(c[12]), "=r"(c[13]), "=r"(c[14]), "=r"(c[15])
+      : "r"(ta), "r"(tb), "r"(tc_)
+      : "memory");
+}
+
+// 16-byte asynchronous global -> shared copy (no register staging), grouped per thread.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -190,8 +221,8 @@ struct TcArgs {
   const __nv_bfloat16* X; int ldx;    // input (residual source)
   __nv_bfloat16* Y; int ldy;          // output
   int residual;
-  __nv_bfloat16* Hbar_out;            // [T][B][2 h1] or null
   float* act_out;        // [R][h1] or null
+  int mt_stage;          // 1: the epilogue stages M[t] rows of the tile in shared memory
   // plain epilogue: C[row][col] = acc + bias[col] (rows < bias_rows)
   int rows; float* C; int ldc; const float* bias; int bias_rows;
   // orbital epilogue
@@ -208,86 +239,86 @@ struct TcArgs {
   int bsplit;
 };
 
-struct Smem {
-  unsigned char* sA; unsigned char* sB; float* ep;
-  uint64_t *full, *empty, *accf, *acce, *mma_done;
-  uint32_t* tmem_slot; volatile int* abort_flag;
-};
 
 // ---- epilogue: stream layer ------------------------------------------------------------
-// One 32-column chunk, in two 16-column halves (register budget); the spin means of the
-// chunk's outputs are reduced through shared memory by the warps of this column half.
+// One 32-column chunk, in two 16-column halves (register budget).  `res` holds the
+// chunk's residual (8 bf16 per uint4), loaded before the accumulator wait; `mrow` is the
+// walker's mean-field row for this tile's columns (shared memory or global).  The spin
+// means of the output, the next layer's mean-field input, are taken by a separate pass.
 template <bool FULL>
-__device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, bool has_chunk, int r, int ehalf,
-                                          int ethread, uint32_t tmem, uint32_t lane_base, int buf, int n0, int tile,
-                                          float* ys) {
+__device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, bool has_chunk, int r, uint32_t tmem,
+                                          uint32_t lane_base, int buf, int n0, int tile, const uint4 (&res)[4],
+                                          const float* mrow) {
   const Shape& sh = a.sh;
   const int nt = a.nt, T = sh.T;
   const int64_t row = (int64_t)tile * 128 + r;
   const int wl = r / sh.N;
   const int w = tile * sh.wpt + wl;
   const bool valid = wl < sh.wpt && w < sh.B;
-  const int64_t xslab = sh.R * a.ldx, yslab = sh.R * a.ldy;
+  const int64_t yslab = sh.R * a.ldy;
   const int col0 = n0 + cc * 32;
   const bool live = has_chunk && valid && col0 < a.h1;
-  float* ysh = ys + ehalf * 128 * 33;
+  const int kind = t == 0 ? 0 : (t < T - 1 ? 1 : 2);           // value, gradient, Laplacian slab
   if (has_chunk) {
-#pragma unroll 1
+#pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
       const int cb = cc * 32 + hh * 16;
       uint32_t acc[16], hv[16], sq[16];
-      tmem_ld16(tmem + lane_base + (uint32_t)(buf * nt + cb), acc);
       if (FULL && t > 0) {
-        tmem_ld16(tmem + lane_base + (uint32_t)(2 * nt + cb), hv);
-        tmem_ld16(tmem + lane_base + (uint32_t)(3 * nt + cb), sq);
+        tmem_ld16x3(tmem + lane_base + (uint32_t)(buf * nt + cb), tmem + lane_base + (uint32_t)(2 * nt + cb),
+                    tmem + lane_base + (uint32_t)(3 * nt + cb), acc, hv, sq);
+      } else {
+        tmem_ld16(tmem + lane_base + (uint32_t)(buf * nt + cb), acc);
       }
       float out[16];
       if (live) {
-        const int c0 = col0 + hh * 16;
-        const float4* mt = (const float4*)(a.Mterm + ((int64_t)t * sh.B + w) * a.h1 + c0);
-        float res[16];
+        float z[16];
+        const float4* mt = (const float4*)(mrow + cc * 32 + hh * 16);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float4 m4 = mt[v];
+          z[4 * v] = __uint_as_float(acc[4 * v]) + m4.x;
+          z[4 * v + 1] = __uint_as_float(acc[4 * v + 1]) + m4.y;
+          z[4 * v + 2] = __uint_as_float(acc[4 * v + 2]) + m4.z;
+          z[4 * v + 3] = __uint_as_float(acc[4 * v + 3]) + m4.w;
+        }
+        if (kind == 0) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float h = tanh_fast(z[j]);
+            hv[j] = __float_as_uint(h);
+            sq[j] = 0u;
+            out[j] = h;
+          }
+        } else if (kind == 1) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float h = __uint_as_float(hv[j]);
+            out[j] = (1.0f - h * h) * z[j];
+            sq[j] = __float_as_uint(fmaf(z[j], z[j], __uint_as_float(sq[j])));
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float h = __uint_as_float(hv[j]);
+            const float d = 1.0f - h * h;
+            out[j] = d * (z[j] - 2.0f * h * __uint_as_float(sq[j]));
+          }
+        }
         if (a.residual) {
-          const uint4* xr = (const uint4*)(a.X + t * xslab + row * a.ldx + c0);
 #pragma unroll
           for (int v = 0; v < 2; ++v) {
-            const uint4 u = xr[v];
+            const uint4 u = res[2 * hh + v];
             const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const float2 f = __bfloat1622float2(p2[e]);
-              res[8 * v + 2 * e] = f.x;
-              res[8 * v + 2 * e + 1] = f.y;
+              out[8 * v + 2 * e] += f.x;
+              out[8 * v + 2 * e + 1] += f.y;
             }
           }
         }
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const float4 m4 = mt[v];
-          const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int j = 4 * v + e;
-            const float z = __uint_as_float(acc[j]) + mv[e];
-            float o;
-            if (t == 0) {
-              const float h = tanhf(z);
-              hv[j] = __float_as_uint(h);
-              sq[j] = 0u;
-              o = h;
-            } else {
-              const float h = __uint_as_float(hv[j]);
-              const float d = 1.0f - h * h;
-              if (t < T - 1) {
-                o = d * z;
-                sq[j] = __float_as_uint(__uint_as_float(sq[j]) + z * z);
-              } else {
-                o = d * z - 2.0f * h * d * __uint_as_float(sq[j]);
-              }
-            }
-            out[j] = a.residual ? o + res[j] : o;
-          }
-        }
-        uint4* yo = (uint4*)(a.Y + t * yslab + row * a.ldy + c0);
+        uint4* yo = (uint4*)(a.Y + t * yslab + row * a.ldy + col0 + hh * 16);
 #pragma unroll
         for (int v = 0; v < 2; ++v) {
           uint4 u;
@@ -296,8 +327,8 @@ __device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, bool h
           for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(out[8 * v + 2 * e], out[8 * v + 2 * e + 1]);
           yo[v] = u;
         }
-        if (t == 0 && a.act_out) {
-          float4* ao = (float4*)(a.act_out + row * a.h1 + c0);
+        if (kind == 0 && a.act_out) {
+          float4* ao = (float4*)(a.act_out + row * a.h1 + col0 + hh * 16);
 #pragma unroll
           for (int v = 0; v < 4; ++v)
             ao[v] = make_float4(__uint_as_float(hv[4 * v]), __uint_as_float(hv[4 * v + 1]),
@@ -308,37 +339,30 @@ __device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, bool h
         for (int j = 0; j < 16; ++j) { out[j] = 0.f; hv[j] = 0u; sq[j] = 0u; }
       }
       if (FULL) {
-        if (t == 0) {
+        if (kind == 0) {
           tmem_st16(tmem + lane_base + (uint32_t)(2 * nt + cb), hv);
           tmem_st16(tmem + lane_base + (uint32_t)(3 * nt + cb), sq);
-        } else if (t < T - 1) {
+        } else if (kind == 1) {
           tmem_st16(tmem + lane_base + (uint32_t)(3 * nt + cb), sq);
         }
-        tmem_wait_st();
-      }
-      if (a.Hbar_out) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) ysh[r * 33 + hh * 16 + j] = out[j];
       }
     }
+    if (FULL) tmem_wait_st();
   }
-  if (a.Hbar_out) {
-    // both column halves take part in both barriers, with or without a chunk
-    asm volatile("bar.sync 2, 256;" ::: "memory");
-    if (has_chunk && col0 < a.h1) {
-      for (int e = ethread & 127; e < sh.wpt * 2 * 32; e += 128) {
-        const int wl2 = e / 64, s2 = (e / 32) & 1, j = e & 31;
-        const int w2 = tile * sh.wpt + wl2;
-        if (w2 >= sh.B) continue;
-        const int lo = s2 ? sh.n_up : 0, hi = s2 ? sh.N : sh.n_up;
-        float sum = 0.f;
-        for (int i = lo; i < hi; ++i) sum += ysh[(wl2 * sh.N + i) * 33 + j];
-        a.Hbar_out[((int64_t)t * sh.B + w2) * 2 * a.h1 + s2 * a.h1 + col0 + j] =
-            __float2bfloat16_rn(hi > lo ? sum / (float)(hi - lo) : 0.f);
-      }
-    }
-    asm volatile("bar.sync 2, 256;" ::: "memory");
+}
+
+// Issues the copies of M[t] (the tile's walkers, this CTA's nt columns) into a staging
+// buffer of rows nt + 4 floats; one commit group per call and thread.
+__device__ __forceinline__ void stage_mterm(const TcArgs& a, int t, int tile, int n0, float* dst, int ethread) {
+  const Shape& sh = a.sh;
+  const int q4 = a.nt >> 2;                                   // 16-byte pieces per walker row
+  const int w0 = tile * sh.wpt;
+  const int nw = min(sh.wpt, sh.B - w0);
+  for (int e = ethread; e < nw * q4; e += 32 * kEpiWarps) {
+    const int wl = e / q4, c4 = e - wl * q4;
+    cp_async16(dst + wl * (a.nt + 4) + 4 * c4, a.Mterm + ((int64_t)t * sh.B + w0 + wl) * a.h1 + n0 + 4 * c4);
   }
+  cp_async_commit();
 }
 
 // ---- epilogue: plain GEMM with bias ----------------------------------------------------
@@ -425,9 +449,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t bytesA = 128 * 128, bytesB = (uint32_t)nt * 128;
   unsigned char* sA = base;                                   // kStages x 16 KB
   unsigned char* sB = sA + kStages * bytesA;                  // kStages x nbparts x nt*128
-  float* ep = (float*)(sB + kStages * nbparts * bytesB);      // epilogue staging
-  const size_t ep_floats = EPI == kEpiLayer ? 2 * 128 * 33 : 0;
-  uint64_t* bars = (uint64_t*)(ep + ep_floats);
+  float* mts = (float*)(sB + kStages * nbparts * bytesB);     // [2][wpt][nt + 4] M[t] staging (layer)
+  const size_t mt_floats = (EPI == kEpiLayer && a.mt_stage) ? (size_t)2 * a.sh.wpt * (nt + 4) : 0;
+  uint64_t* bars = (uint64_t*)(mts + mt_floats);
   uint64_t* full = bars;
   uint64_t* empty = bars + kStages;
   uint64_t* accf = bars + 2 * kStages;
@@ -538,11 +562,32 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ehalf = (warp - 2) >> 2;            // column half: chunks cc with cc % 2 == ehalf
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const int nchunks = nt / 32;
-    for (int item = 0; item < my_tiles * T; ++item) {
+    const int n_items = my_tiles * T;
+    const int64_t xslab = sh.R * a.ldx;
+    if (EPI == kEpiLayer && a.mt_stage && n_items > 0) stage_mterm(a, 0, (int)blockIdx.y, ctile * nt, mts, ethread);
+    for (int item = 0; item < n_items; ++item) {
       const int tile = (int)blockIdx.y + (item / T) * (int)gridDim.y, t = item % T;
       const int buf = item & 1;
       const uint32_t use = (uint32_t)(item >> 1);
+      // residual of this slab, both chunks, loaded before the accumulator is ready
+      uint4 res[2][4];
+      if (EPI == kEpiLayer && a.residual) {
+        const int wl = r / sh.N;
+        const bool valid = wl < sh.wpt && tile * sh.wpt + wl < sh.B;
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
+          const int cc = 2 * it + ehalf;
+          if (valid && cc < nchunks) {
+            const uint4* xr =
+                (const uint4*)(a.X + t * xslab + ((int64_t)tile * 128 + r) * a.ldx + ctile * nt + cc * 32);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) res[it][v] = xr[v];
+          }
+        }
+      }
+      if (EPI == kEpiLayer && a.mt_stage) cp_async_wait_all();
       const bool ok = !*abort_flag && mbar_wait(accf + buf, use & 1u, deadline);
+      // (the barrier also publishes every thread's staged M[t] copies)
       if (epilogue_any(!ok)) {
         if (ethread == 0) {
           *abort_flag = 1;
@@ -551,11 +596,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       fence_after();
-      for (int it = 0; it < (nchunks + 1) / 2; ++it) {
+      const float* mrow = nullptr;
+      if (EPI == kEpiLayer) {
+        if (a.mt_stage) {
+          // prefetch the next slab's M[t] into the other buffer (its readers passed the barrier)
+          if (item + 1 < n_items) {
+            const int tile1 = (int)blockIdx.y + ((item + 1) / T) * (int)gridDim.y, t1 = (item + 1) % T;
+            stage_mterm(a, t1, tile1, ctile * nt, mts + ((item + 1) & 1) * sh.wpt * (nt + 4), ethread);
+          }
+          const int wl = min(r / sh.N, sh.wpt - 1);
+          mrow = mts + ((item & 1) * sh.wpt + wl) * (nt + 4);
+        } else {
+          const int w = min(tile * sh.wpt + r / sh.N, sh.B - 1);
+          mrow = a.Mterm + ((int64_t)t * sh.B + w) * a.h1 + ctile * nt;
+        }
+      }
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        if (it >= (nchunks + 1) / 2) break;
         const int cc = 2 * it + ehalf;
         const bool has = cc < nchunks;
         if (EPI == kEpiLayer) {
-          epi_layer<FULL>(a, t, has ? cc : 0, has, r, ehalf, ethread, tmem, lane_base, buf, ctile * nt, tile, ep);
+          epi_layer<FULL>(a, t, has ? cc : 0, has, r, tmem, lane_base, buf, ctile * nt, tile, res[it], mrow);
         } else if (has) {
           if (EPI == kEpiPlain) epi_plain(a, cc, r, tmem, lane_base, buf, ctile * nt, tile);
           else epi_orbital<FULL>(a, t, cc, r, tmem, lane_base, buf, spin, ko0, tile);
@@ -566,6 +628,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) mbar_arrive(acce + buf);
     }
   }
+  if (EPI == kEpiLayer) cp_async_wait_all();
   fence_before();
   __syncthreads();
   fence_after();
@@ -620,10 +683,14 @@ static uint32_t pow2_cols(int c) {
   return v;
 }
 
-static size_t tc_smem_bytes(int nt, int epi, bool split) {
-  const size_t ep = epi == tc::kEpiLayer ? 2 * 128 * 33 * 4 : 0;
-  return 1024 + tc::kStages * (128 * 128 + (size_t)nt * 128 * (split ? 2 : 1)) + ep + 8 * (2 * tc::kStages + 5) + 16;
+// Dynamic shared memory of a launch: alignment slack, the A/B ring, the layer epilogue's
+// M[t] staging (mt_rows walkers, double-buffered), barriers.
+static size_t tc_smem_bytes(int nt, int epi, bool split, int mt_rows = 0) {
+  (void)epi;
+  const size_t mt = (size_t)2 * mt_rows * (nt + 4) * 4;
+  return 1024 + tc::kStages * (128 * 128 + (size_t)nt * 128 * (split ? 2 : 1)) + mt + 8 * (2 * tc::kStages + 5) + 16;
 }
+constexpr size_t kMaxDynamicSmem = 227 * 1024;
 
 static int sm_count() {
   static int n = 0;
@@ -645,7 +712,7 @@ static dim3 persistent_grid(int ctiles, int tiles) {
 template <int EPI>
 static void launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const tc::TcArgs& a, dim3 grid, bool full,
                       cudaStream_t st) {
-  const size_t smem = tc_smem_bytes(a.nt, EPI, a.bsplit != 0);
+  const size_t smem = tc_smem_bytes(a.nt, EPI, a.bsplit != 0, (EPI == tc::kEpiLayer && a.mt_stage) ? a.sh.wpt : 0);
   if (full) {
     cudaFuncSetAttribute(tc::k_tc<EPI, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     tc::k_tc<EPI, true><<<grid, tc::kThreads, smem, st>>>(ta, tb, a);
@@ -657,7 +724,7 @@ static void launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const tc::Tc
 
 // Stream layer on the tensor cores; returns false (nothing launched) if a tensor map could not be built.
 bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const void* Vs16, const float* Mterm, void* Y,
-                     int ldy, int residual, void* Hbar_out, float* act_out, int h1, int* status, cudaStream_t st) {
+                     int ldy, int residual, float* act_out, int h1, int* status, cudaStream_t st) {
   const int nt = tc_columns(h1);
   CUtensorMap ta, tb;
   if (!make_map(&ta, X, k_self, (int64_t)sh.T * sh.R, ldx, 128)) return false;
@@ -674,9 +741,10 @@ bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const 
   a.Y = (__nv_bfloat16*)Y;
   a.ldy = ldy;
   a.residual = residual;
-  a.Hbar_out = (__nv_bfloat16*)Hbar_out;
   a.act_out = act_out;
   a.bsplit = ldx;
+  // stage M[t] in shared memory when the tile's walkers fit beside the ring
+  a.mt_stage = tc_smem_bytes(nt, tc::kEpiLayer, true, sh.wpt) <= kMaxDynamicSmem ? 1 : 0;
   const bool full = sh.T > 1;
   a.tmem_cols = pow2_cols(full ? 4 * nt : 2 * nt);
   a.tiles = sh.tiles;
