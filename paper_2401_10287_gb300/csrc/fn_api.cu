@@ -163,6 +163,13 @@ static void build_layout(fn_system* s) {
   }
   p.W16 = q16; q16 += (int64_t)K * (ns[0] + ns[1]) * 2 * h1;
   q16 = round_up(q16, 64);
+  for (int l = 0; l < L; ++l) {
+    p.VsT16[l] = q16; q16 += (int64_t)s->layer[l].k_self * 2 * h1;
+    q16 = round_up(q16, 64);
+  }
+  p.ldWT = (int)round_up((int64_t)K * (ns[0] + ns[1]), 64);
+  p.W16T = q16; q16 += (int64_t)h1 * 2 * p.ldWT;
+  q16 = round_up(q16, 64);
   for (int a = 0; a < 2; ++a) {
     const int64_t ko = (int64_t)K * ns[a];
     p.wT[a] = q; q += ko * h1;
@@ -214,6 +221,13 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
   const size_t o_dP = take((size_t)sh.R * s->cfg.n_dets * N * sizeof(Cmp));
   const size_t o_orbP = take(Mode::kMode == FN_BF16_MIXED ? (size_t)sh.R * 4 * s->cfg.n_dets * N * sizeof(float) : 0);
   const size_t o_envv = take(Mode::kMode == FN_BF16_MIXED ? (size_t)sh.R * s->cfg.n_dets * N * sizeof(float) : 0);
+  const bool bf16 = Mode::kMode == FN_BF16_MIXED;
+  int max_k = 0;
+  for (int l = 0; l < L; ++l) max_k = std::max(max_k, s->layer[l].k_self);
+  const int64_t KN = (int64_t)s->cfg.n_dets * N;
+  const size_t o_g16 = take(bf16 ? (size_t)sh.R * std::max<int64_t>(h1, s->prep.ldWT) * 2 : 0);
+  const size_t o_t16a = take(bf16 ? (size_t)std::max(max_k, h1) * sh.R * 2 : 0);
+  const size_t o_t16b = take(bf16 ? (size_t)std::max<int64_t>(h1, KN) * sh.R * 2 : 0);
   const size_t o_status = take(sizeof(int) * 4);
   const size_t o_counter = take(sizeof(int64_t) * 4);
   if (ws && ws->base) {
@@ -227,6 +241,7 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
     ws->scratch_d = (double*)(b + o_scr); ws->dX = b + o_dX; ws->dH = b + o_dH; ws->dZ = b + o_dZ;
     ws->dZw = b + o_dZw; ws->dHbar = b + o_dHbar; ws->dG = b + o_dG; ws->dPhi = b + o_dPhi;
     ws->gradc = b + o_gradc; ws->dP = b + o_dP; ws->orbP = (float*)(b + o_orbP); ws->envv = (float*)(b + o_envv); ws->status = (int*)(b + o_status); ws->counter = (int64_t*)(b + o_counter);
+    ws->g16 = b + o_g16; ws->t16a = b + o_t16a; ws->t16b = b + o_t16b;
   }
   return off;
 }

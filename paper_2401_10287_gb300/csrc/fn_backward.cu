@@ -63,6 +63,55 @@ static void colsum(const fn_system* s, cudaStream_t st, const T* src, int64_t ro
   k_colsum<T, Cmp><<<grid, 128, 0, st>>>(src, rows, ld, cols, dst);
 }
 
+// ---- BF16 operands of the tensor-core backward GEMMs (BF16 mode) ---------------------
+// out[r][c] = bf16(in[r][c]) (when out is given) and outT[c][r] = bf16(in[r][c]) (when outT
+// is given) over the R tile rows and `cols` columns; rows that hold no electron are written
+// as zero.  32 x 32 tiles pass through shared memory, so the row-major reads and the
+// transposed writes are both coalesced.
+template <typename Tin>
+__global__ void k_bf16_copy_T(Shape sh, const Tin* __restrict__ in, int64_t ld_in, int cols,
+                              __nv_bfloat16* __restrict__ out, int64_t ld_out, __nv_bfloat16* __restrict__ outT) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32;
+  const int64_t r0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t r = r0 + k;
+    const int c = c0 + tx;
+    const int rr = (int)(r % kTileRows), q = (int)(r / kTileRows);
+    const bool valid = rr / sh.N < sh.wpt && q * sh.wpt + rr / sh.N < sh.B;
+    const float v = (c < cols && valid) ? (float)ld(in + r * ld_in + c) : 0.f;
+    tile[k][tx] = v;
+    if (out && c < cols) out[r * ld_out + c] = __float2bfloat16_rn(v);
+  }
+  if (!outT) return;
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int c = c0 + k;
+    if (c < cols) outT[(int64_t)c * sh.R + r0 + tx] = __float2bfloat16_rn(tile[tx][k]);
+  }
+}
+
+template <typename Tin>
+static void bf16_copy_T(const fn_system* s, cudaStream_t st, const Shape& sh, const Tin* in, int64_t ld_in, int cols,
+                        __nv_bfloat16* out, int64_t ld_out, __nv_bfloat16* outT) {
+  ProfScope ps(s->prof, kProfBwdMisc, st);
+  dim3 grid((cols + 31) / 32, (unsigned)(sh.R / 32));
+  k_bf16_copy_T<Tin><<<grid, dim3(32, 8), 0, st>>>(sh, in, ld_in, cols, out, ld_out, outT);
+}
+
+// K splits of a weight-gradient GEMM (K = all rows): about two CTAs per SM, >= 4 k-blocks each.
+static int ksplit_for(const fn_system* s, int rows, int ncols, int64_t k) {
+  const int tiles = (rows + 127) / 128, ctiles = (ncols + 127) / 128;
+  const int64_t nkb = (k + 63) / 64;
+  const int want = std::max(1, 2 * s->sm_count / std::max(1, tiles * ctiles));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, nkb / 4));
+}
+
+static void tc_or_flag(const fn_system* s, bool ok) {
+  if (!ok) const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
+}
+
 // ---- orbitals and envelopes ----------------------------------------------------------
 struct OrbBwdArgs {
   const void* HL;            // [R][h1] value slab
@@ -316,13 +365,20 @@ void launch_backward(const fn_system* s, const void* walkers, const Shape& sh, c
   cudaMemsetAsync(ws.dH, 0, sizeof(Cmp) * R * h1, st);
   // orbitals + envelopes: P = h_L w (both spins, every row), then the envelope kernel turns
   // it into dP in place; rows that hold no electron are zeroed for the weight GEMMs below
+  constexpr bool kTc = Mode::kMode == FN_BF16_MIXED;
+  const __nv_bfloat16* prep16 = (const __nv_bfloat16*)ws.prep16;
   {
     ProfScope ps(s->prof, kProfBwdGemm, st);
-    for (int q = 0; q < 2; ++q) {
-      const int n_q = q ? s->n_dn : s->n_up;
-      if (!n_q) continue;
-      gemm<Act, Cmp, Cmp, Cmp>(st, (int)R, K * n_q, h1, (const Act*)ws.HL, h1, 1, prep + pl.wT[q], K * n_q, 1,
-                               (Cmp*)ws.dP + (q ? K * s->n_up : 0), ldp, 1, (const Cmp*)nullptr, 0, 1, false);
+    if (kTc) {
+      tc_or_flag(s, launch_gemm_tc((int)R, h1, ws.HL, h1, prep16 + pl.W16, 2 * h1, h1, ldp, (float*)ws.dP, ldp, nullptr,
+                                   0, 1, false, ws.status, st));
+    } else {
+      for (int q = 0; q < 2; ++q) {
+        const int n_q = q ? s->n_dn : s->n_up;
+        if (!n_q) continue;
+        gemm<Act, Cmp, Cmp, Cmp>(st, (int)R, K * n_q, h1, (const Act*)ws.HL, h1, 1, prep + pl.wT[q], K * n_q, 1,
+                                 (Cmp*)ws.dP + (q ? K * s->n_up : 0), ldp, 1, (const Cmp*)nullptr, 0, 1, false);
+      }
     }
   }
   {
@@ -355,7 +411,31 @@ void launch_backward(const fn_system* s, const void* walkers, const Shape& sh, c
     else k_orb_bwd<Cmp, Det, Wlk, kMaxNuclei><<<grid, threads, 0, st>>>(r, s->d_nuclei, sh, a);
   }
   const int ns[2] = {s->n_up, s->n_dn};
-  for (int q = 0; q < 2; ++q) {
+  __nv_bfloat16* g16 = (__nv_bfloat16*)ws.g16;
+  __nv_bfloat16* t16a = (__nv_bfloat16*)ws.t16a;
+  __nv_bfloat16* t16b = (__nv_bfloat16*)ws.t16b;
+  if (kTc) {
+    // dP as a bf16 row-major copy and transposed; h_L transposed
+    bf16_copy_T<Cmp>(s, st, sh, (const Cmp*)ws.dP, ldp, ldp, g16, pl.ldWT, t16b);
+    bf16_copy_T<Act>(s, st, sh, (const Act*)ws.HL, h1, h1, nullptr, 0, t16a);
+    for (int q = 0; q < 2; ++q) {
+      if (!ns[q]) continue;
+      const int n_ko = K * ns[q];
+      // dW_orb^T [h1][K n] += h_L^T dP (K = all rows, split)
+      {
+        ProfScope ps(s->prof, kProfBwdGemm, st);
+        tc_or_flag(s, launch_gemm_tc(h1, (int)R, t16a, (int)R, t16b + (int64_t)(q ? K * s->n_up : 0) * R, (int)R, 0,
+                                     n_ko, (float*)(gradc + pl.wT[q]), n_ko, nullptr, 0,
+                                     ksplit_for(s, h1, n_ko, R), true, ws.status, st));
+      }
+      colsum<Cmp, Cmp>(s, st, (const Cmp*)ws.dP + (q ? K * s->n_up : 0), R, ldp, n_ko, gradc + pl.g[q]);
+    }
+    // dh_L = dP W (both spins: the other spin's columns of a row are zero)
+    ProfScope ps(s->prof, kProfBwdGemm, st);
+    tc_or_flag(s, launch_gemm_tc((int)R, ldp, g16, pl.ldWT, prep16 + pl.W16T, 2 * pl.ldWT, pl.ldWT, h1, (float*)ws.dH,
+                                 h1, nullptr, 0, 1, false, ws.status, st));
+  }
+  for (int q = 0; q < 2 && !kTc; ++q) {
     if (!ns[q]) continue;
     const int n_ko = K * ns[q];
     const Cmp* dPq = (const Cmp*)ws.dP + (q ? K * s->n_up : 0);
@@ -387,11 +467,20 @@ void launch_backward(const fn_system* s, const void* walkers, const Shape& sh, c
       k_bwd_tanh<Cmp><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sh, h1, dH, (const Cmp*)ws.act[l], dZ, dZw);
     }
     const Act* X = (const Act*)ws.X[l];
+    if (kTc) {
+      // bf16 operands: dZ row-major and transposed, X_l transposed
+      bf16_copy_T<Cmp>(s, st, sh, dZ, h1, h1, g16, h1, t16b);
+      bf16_copy_T<Act>(s, st, sh, X, d.ldx, d.k_self, nullptr, 0, t16a);
+    }
     // dV_self (internal [k_self][h1]) += X^T dZ
     {
       ProfScope ps(s->prof, kProfBwdGemm, st);
-      gemm<Act, Cmp, Cmp, Cmp>(st, d.k_self, h1, (int)R, X, 1, d.ldx, dZ, h1, 1, gradc + pl.VsT[l], h1, 1,
-                               (const Cmp*)nullptr, 0, split, true);
+      if (kTc)
+        tc_or_flag(s, launch_gemm_tc(d.k_self, (int)R, t16a, (int)R, t16b, (int)R, 0, h1, (float*)(gradc + pl.VsT[l]),
+                                     h1, nullptr, 0, ksplit_for(s, d.k_self, h1, R), true, ws.status, st));
+      else
+        gemm<Act, Cmp, Cmp, Cmp>(st, d.k_self, h1, (int)R, X, 1, d.ldx, dZ, h1, 1, gradc + pl.VsT[l], h1, 1,
+                                 (const Cmp*)nullptr, 0, split, true);
     }
     colsum<Cmp, Cmp>(s, st, dZw, sh.B, h1, h1, gradc + pl.b[l]);
     // dU (internal [2 d_h][h1]) += Hbar^T dZw
@@ -404,8 +493,12 @@ void launch_backward(const fn_system* s, const void* walkers, const Shape& sh, c
     // dX = dZ V_self^T  ([R][k_self], row stride ldx)
     {
       ProfScope ps(s->prof, kProfBwdGemm, st);
-      gemm<Cmp, Cmp, Cmp, Cmp>(st, (int)R, d.k_self, h1, dZ, h1, 1, prep + pl.VsT[l], 1, h1, dX, d.ldx, 1,
-                               (const Cmp*)nullptr, 0, 1, false);
+      if (kTc)
+        tc_or_flag(s, launch_gemm_tc((int)R, h1, g16, h1, prep16 + pl.VsT16[l], 2 * h1, h1, d.k_self, (float*)dX, d.ldx,
+                                     nullptr, 0, 1, false, ws.status, st));
+      else
+        gemm<Cmp, Cmp, Cmp, Cmp>(st, (int)R, d.k_self, h1, dZ, h1, 1, prep + pl.VsT[l], 1, h1, dX, d.ldx, 1,
+                                 (const Cmp*)nullptr, 0, 1, false);
     }
     if (l >= 1) {
       {

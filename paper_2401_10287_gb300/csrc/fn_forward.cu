@@ -71,9 +71,25 @@ static std::vector<CopyDesc> build_descs(const fn_system* s, bool with16) {
   if (with16)
     for (int a = 0; a < 2; ++a)
       if (ns[a])
-        for (int part = 1; part <= 2; ++part)
+        for (int part = 1; part <= 2; ++part) {
           v.push_back({s->off_w[a], h1, 1, p.W16 + (a ? (int64_t)K * ns[0] * 2 * h1 : 0) + (part == 2 ? h1 : 0),
                        2 * h1, 1, K * ns[a], h1, part});
+          // transposed: row c, column ko (up block first)
+          v.push_back({s->off_w[a], 1, h1, p.W16T + (a ? (int64_t)K * ns[0] : 0) + (part == 2 ? p.ldWT : 0),
+                       2 * p.ldWT, 1, h1, K * ns[a], part});
+        }
+  if (with16)
+    for (int l = 0; l < L; ++l) {
+      const LayerDims& d = s->layer[l];
+      const int f_in = 3 * d.d_h + 2 * d.d_g;
+      // VsT16[k][n] = V[n][k] for k < d_h, V[n][3 d_h + (k - d_h)] for the pair-mean columns
+      for (int part = 1; part <= 2; ++part) {
+        const int oh = part == 2 ? h1 : 0;
+        v.push_back({d.off_V, 1, f_in, p.VsT16[l] + oh, 2 * h1, 1, d.d_h, h1, part});
+        v.push_back({d.off_V + 3 * d.d_h, 1, f_in, p.VsT16[l] + (int64_t)d.d_h * 2 * h1 + oh, 2 * h1, 1, 2 * d.d_g,
+                     h1, part});
+      }
+    }
   for (int a = 0; a < 2; ++a) {
     if (!ns[a]) continue;
     const int ko = K * ns[a];
@@ -818,8 +834,8 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
       ProfScope ps(s->prof, kProfMeanGemm, st);
       if (Mode::kMode == FN_BF16_MIXED) {
         const __nv_bfloat16* U16 = (const __nv_bfloat16*)ws.prep16 + s->prep.U16[l];
-        if (!launch_gemm_tc(sh.T * sh.B, 2 * d.d_h, Hb, 2 * d.d_h, U16, 2 * d.d_h, h1, (float*)ws.Mterm,
-                            (const float*)(prep + s->prep.b[l]), sh.B, ws.status, st))
+        if (!launch_gemm_tc(sh.T * sh.B, 2 * d.d_h, Hb, 2 * d.d_h, U16, 4 * d.d_h, 2 * d.d_h, h1, (float*)ws.Mterm, h1,
+                            (const float*)(prep + s->prep.b[l]), sh.B, 1, false, ws.status, st))
           const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
       } else {
         gemm<Act, Cmp, Cmp, Cmp>(st, sh.T * sh.B, h1, 2 * d.d_h, Hb, 2 * d.d_h, 1, prep + s->prep.UT[l], h1, 1,

@@ -98,6 +98,10 @@ struct PrepLayout {
   int64_t Vs16[kMaxLayers];  // self part of V, rows h1, ld = ldx_l
   int64_t U16[kMaxLayers];   // mean-field part of V, rows h1, ld = 2 d_h
   int64_t W16;               // orbital projections, rows K (n_up + n_dn) (up block first), ld = h1
+  // backward operands (same split layout): rows are the GEMM's output columns
+  int64_t VsT16[kMaxLayers]; // V_self^T: rows k_self, ld = h1  (dX = dZ V_self)
+  int64_t W16T;              // orbital projections transposed: rows h1, ld = ldWT (dh_L = dP W)
+  int ldWT;                  // K (n_up + n_dn) rounded up to 64 (the hi part of a k-block never reaches the lo part)
   int64_t total16;
 };
 
@@ -138,6 +142,10 @@ struct Workspace {
   void* dP = nullptr;            // [R][K (n_up + n_dn)] gradient wrt orbital projections (Cmp)
   float* orbP = nullptr;         // [R][4][K N] projections for the orbital envelope fix-up (BF16 mode)
   float* envv = nullptr;         // [R][K N] envelope values (BF16 mode)
+  // BF16-mode backward operands for the tensor-core GEMMs
+  void* g16 = nullptr;           // [R][max(h1, ldWT)] bf16 copy of dZ or dP
+  void* t16a = nullptr;          // [max(k_self, h1)][R] bf16 transposed activations (X_l^T, h_L^T)
+  void* t16b = nullptr;          // [max(h1, K N)][R] bf16 transposed gradients (dZ^T, dP^T)
   int* status = nullptr;         // device status word
   int64_t* counter = nullptr;    // scratch counter
 };
@@ -179,8 +187,8 @@ fn_status upload_prep_descs(fn_system* s);
 // Tensor-core one-electron layer (BF16 mode); false if a TMA tensor map could not be built.
 bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const void* Vs16, const float* Mterm, void* Y,
                      int ldy, int residual, float* act_out, int h1, int* status, cudaStream_t st);
-bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int ldb, int h1, float* C,
-                    const float* bias, int bias_rows, int* status, cudaStream_t st);
+bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int ldb, int bsplit, int ncols, float* C,
+                    int ldc, const float* bias, int bias_rows, int ksplit, bool atomic, int* status, cudaStream_t st);
 bool launch_orbitals_tc(const Shape& sh, const void* HL, int h1, const void* W16, const float* const* wbias,
                         const float* const* pi, const float* const* sig, int K, int aniso, const float* walkers,
                         const double* nuclei, void* Phi, int64_t PW, float* orbP, const float* envv, int* status,

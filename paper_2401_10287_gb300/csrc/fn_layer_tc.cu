@@ -223,8 +223,10 @@ struct TcArgs {
   int residual;
   float* act_out;        // [R][h1] or null
   int mt_stage;          // 1: the epilogue stages M[t] rows of the tile in shared memory
-  // plain epilogue: C[row][col] = acc + bias[col] (rows < bias_rows)
+  // plain epilogue: C[row][col] = acc + bias[col] (rows < bias_rows), or C += acc (atomic);
+  // the K range may be split over `ksplit` CTAs per output tile (requires atomic)
   int rows; float* C; int ldc; const float* bias; int bias_rows;
+  int ksplit, atomic;
   // orbital epilogue
   const float* wbias[2];              // orbital bias g, [K n_s]
   const float* pi[2]; const float* sig[2];
@@ -365,6 +367,19 @@ __device__ __forceinline__ void stage_mterm(const TcArgs& a, int t, int tile, in
   cp_async_commit();
 }
 
+// Work item -> (row tile, k-block range): split-K GEMMs give every (tile, split) pair its
+// own item; the other kernels cover all k-blocks of a tile.
+template <int EPI>
+__device__ __forceinline__ void item_range(const TcArgs& a, int pidx, int nkb, int& tile, int& kb0, int& kb1) {
+  tile = pidx; kb0 = 0; kb1 = nkb;
+  if (EPI == kEpiPlain && a.ksplit > 1) {
+    tile = pidx / a.ksplit;
+    const int sp = pidx - tile * a.ksplit;
+    kb0 = (int)((int64_t)sp * nkb / a.ksplit);
+    kb1 = (int)((int64_t)(sp + 1) * nkb / a.ksplit);
+  }
+}
+
 // ---- epilogue: plain GEMM with bias ----------------------------------------------------
 __device__ __forceinline__ void epi_plain(const TcArgs& a, int cc, int r, uint32_t tmem, uint32_t lane_base, int buf,
                                           int n0, int tile) {
@@ -373,14 +388,26 @@ __device__ __forceinline__ void epi_plain(const TcArgs& a, int cc, int r, uint32
   uint32_t acc[32];
   tmem_ld32(tmem + lane_base + (uint32_t)(buf * a.nt + cc * 32), acc);
   if (row >= a.rows || col0 >= a.h1) return;
+  float* co = a.C + row * a.ldc + col0;
+  if (a.atomic) {
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      if (col0 + q < a.h1) atomicAdd(co + q, __uint_as_float(acc[q]));
+    return;
+  }
   const bool with_bias = a.bias && row < a.bias_rows;
-  float4* co = (float4*)(a.C + row * a.ldc + col0);
+  if (col0 + 32 <= a.h1 && (a.ldc & 3) == 0) {
 #pragma unroll
-  for (int v = 0; v < 8; ++v) {
-    float o[4];
+    for (int v = 0; v < 8; ++v) {
+      float o[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) o[e] = __uint_as_float(acc[4 * v + e]) + (with_bias ? a.bias[col0 + 4 * v + e] : 0.f);
-    co[v] = make_float4(o[0], o[1], o[2], o[3]);
+      for (int e = 0; e < 4; ++e) o[e] = __uint_as_float(acc[4 * v + e]) + (with_bias ? a.bias[col0 + 4 * v + e] : 0.f);
+      ((float4*)co)[v] = make_float4(o[0], o[1], o[2], o[3]);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      if (col0 + q < a.h1) co[q] = __uint_as_float(acc[q]) + (with_bias ? a.bias[col0 + q] : 0.f);
   }
 }
 
@@ -500,9 +527,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       int issued = 0;
       bool ok = true;
       for (int item = 0; item < my_tiles * T && ok; ++item) {
-        const int tile = (int)blockIdx.y + (item / T) * (int)gridDim.y, t = item % T;
+        const int pidx = (int)blockIdx.y + (item / T) * (int)gridDim.y, t = item % T;
+        int tile, kb0, kb1;
+        item_range<EPI>(a, pidx, nkb, tile, kb0, kb1);
         const int arow = EPI == kEpiPlain ? tile * 128 : (int)(t * sh.R + (int64_t)tile * 128);
-        for (int kb = 0; kb < nkb; ++kb, ++issued) {
+        for (int kb = kb0; kb < kb1; ++kb, ++issued) {
           const int stage = issued % kStages;
           const uint32_t round = (uint32_t)(issued / kStages);
           if (*abort_flag || !mbar_wait(empty + stage, (round & 1u) ^ 1u, deadline)) { ok = false; break; }
@@ -532,7 +561,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (*abort_flag || !mbar_wait(acce + buf, (use & 1u) ^ 1u, deadline)) { ok = false; break; }
         fence_after();
         const uint32_t d = tmem + (uint32_t)(buf * nt);
-        for (int kb = 0; kb < nkb; ++kb, ++consumed) {
+        int tile, kb0, kb1;
+        item_range<EPI>(a, (int)blockIdx.y + (item / T) * (int)gridDim.y, nkb, tile, kb0, kb1);
+        (void)tile;
+        for (int kb = kb0; kb < kb1; ++kb, ++consumed) {
           const int stage = consumed % kStages;
           const uint32_t round = (uint32_t)(consumed / kStages);
           if (*abort_flag || !mbar_wait(full + stage, round & 1u, deadline)) { ok = false; break; }
@@ -542,7 +574,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t db = sdesc(smem_u32(sB + (stage * nbparts + part) * bytesB));
 #pragma unroll
             for (int k4 = 0; k4 < kBlockK / 16; ++k4)
-              mma_bf16(d, da + (uint64_t)(2 * k4), db + (uint64_t)(2 * k4), idesc, (kb | k4 | part) != 0 ? 1u : 0u);
+              mma_bf16(d, da + (uint64_t)(2 * k4), db + (uint64_t)(2 * k4), idesc,
+                       (kb != kb0 || k4 != 0 || part != 0) ? 1u : 0u);
           }
           mma_commit(empty + stage);
         }
@@ -566,7 +599,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t xslab = sh.R * a.ldx;
     if (EPI == kEpiLayer && a.mt_stage && n_items > 0) stage_mterm(a, 0, (int)blockIdx.y, ctile * nt, mts, ethread);
     for (int item = 0; item < n_items; ++item) {
-      const int tile = (int)blockIdx.y + (item / T) * (int)gridDim.y, t = item % T;
+      const int t = item % T;
+      int tile, kb0_, kb1_;
+      item_range<EPI>(a, (int)blockIdx.y + (item / T) * (int)gridDim.y, a.nkb, tile, kb0_, kb1_);
       const int buf = item & 1;
       const uint32_t use = (uint32_t)(item >> 1);
       // residual of this slab, both chunks, loaded before the accumulator is ready
@@ -752,28 +787,40 @@ bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const 
   return true;
 }
 
-// C[rows][h1] = A[rows][k] B[h1][k]^T + bias (rows < bias_rows); A, B bf16 K-major, C fp32.
-bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int ldb, int h1, float* C,
-                    const float* bias, int bias_rows, int* status, cudaStream_t st) {
-  const int nt = tc_columns(h1);
+// C[rows][ncols] (row stride ldc, fp32) = A[rows][k] B[ncols][k]^T (+ bias[col] on rows <
+// bias_rows), or C += A B^T by atomic adds with the k range split over `ksplit` CTAs per
+// output tile.  A: bf16 K-major, row stride lda elements.  B: bf16 K-major, row stride ldb;
+// with bsplit > 0 it holds bf16(W) in columns [0, k) and bf16(W - bf16(W)) in
+// [bsplit, bsplit + k), and both are multiplied.  Returns false (nothing launched) if a
+// tensor map could not be built or the shapes are outside what the kernel covers.
+bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int ldb, int bsplit, int ncols, float* C,
+                    int ldc, const float* bias, int bias_rows, int ksplit, bool atomic, int* status, cudaStream_t st) {
+  if (rows <= 0 || k <= 0 || ncols <= 0) return true;
+  const int nt = ncols >= 128 ? 128 : (ncols > 64 ? 128 : (ncols > 32 ? 64 : 32));
+  const int ctiles = (ncols + nt - 1) / nt;
+  const int nkb = (k + tc::kBlockK - 1) / tc::kBlockK;
+  ksplit = std::max(1, std::min(ksplit, nkb));
+  if (ksplit > 1 && !atomic) return false;
   CUtensorMap ta, tb;
   if (!make_map(&ta, A, k, rows, lda, 128)) return false;
-  if (!make_map(&tb, Bw, ldb + k, h1, 2 * ldb, nt)) return false;
+  if (!make_map(&tb, Bw, bsplit ? bsplit + k : k, ncols, ldb, nt)) return false;
   tc::TcArgs a{};
   a.sh.T = 1;
-  a.nkb = (k + tc::kBlockK - 1) / tc::kBlockK;
+  a.nkb = nkb;
   a.nt = nt;
-  a.h1 = h1;
+  a.h1 = ncols;
   a.status = status;
   a.rows = rows;
   a.C = C;
-  a.ldc = h1;
+  a.ldc = ldc;
   a.bias = bias;
   a.bias_rows = bias_rows;
-  a.bsplit = ldb;
+  a.bsplit = bsplit;
+  a.ksplit = ksplit;
+  a.atomic = atomic ? 1 : 0;
   a.tmem_cols = pow2_cols(2 * nt);
-  a.tiles = (rows + 127) / 128;
-  launch_tc<tc::kEpiPlain>(ta, tb, a, persistent_grid(h1 / nt, a.tiles), false, st);
+  a.tiles = (rows + 127) / 128 * ksplit;
+  launch_tc<tc::kEpiPlain>(ta, tb, a, persistent_grid(ctiles, a.tiles), false, st);
   return true;
 }
 
