@@ -194,15 +194,17 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
   std::vector<std::pair<void**, size_t>> items;
   size_t o_X[kMaxLayers], o_Hbar[kMaxLayers], o_act[kMaxLayers], o_gp[kMaxLayers];
   int max_ldx = 0, max_dh = 0;
+  // BF16 storage adds one slab after the tangent slabs: the value slab's low part
+  const int Tx = T + (Mode::kMode == FN_BF16_MIXED ? 1 : 0);
   for (int l = 0; l < L; ++l) {
-    o_X[l] = take((size_t)T * sh.R * s->layer[l].ldx * sizeof(Act));
-    o_Hbar[l] = take((size_t)T * B * 2 * s->layer[l].d_h * sizeof(Act));
+    o_X[l] = take((size_t)Tx * sh.R * s->layer[l].ldx * sizeof(Act));
+    o_Hbar[l] = take((size_t)Tx * B * 2 * s->layer[l].d_h * sizeof(Act));
     o_act[l] = take((size_t)sh.R * h1 * sizeof(Cmp));
     o_gp[l] = take((size_t)B * N * N * h2 * sizeof(Cmp));
     max_ldx = std::max(max_ldx, s->layer[l].ldx);
     max_dh = std::max(max_dh, s->layer[l].d_h);
   }
-  const size_t o_HL = take((size_t)T * sh.R * h1 * sizeof(Act));
+  const size_t o_HL = take((size_t)Tx * sh.R * h1 * sizeof(Act));
   const size_t o_M = take((size_t)T * B * h1 * sizeof(Cmp));
   const size_t o_Phi = take((size_t)B * phi_walker_stride(s, T) * sizeof(typename Mode::PhiT));
   const size_t o_prep = take((size_t)s->prep.total * sizeof(Cmp));

@@ -15,10 +15,26 @@ __device__ __forceinline__ void st(float* p, double v) { *p = (float)v; }
 __device__ __forceinline__ void st(double* p, float v) { *p = (double)v; }
 __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ void st(__nv_bfloat16* p, double v) { *p = __float2bfloat16_rn((float)v); }
+// BF16 storage keeps the value slab (t = 0) of the stream activations as a pair: bf16(v)
+// in the slab itself and the remainder bf16(v - bf16(v)) in an extra slab after the last
+// tangent slab, about 16 significant bits together.  The tangent slabs keep one bf16.
+template <typename Act> struct SplitValue { static constexpr bool value = false; };
+template <> struct SplitValue<__nv_bfloat16> { static constexpr bool value = true; };
+__device__ __forceinline__ float bf16_rem(float v) { return v - __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ void st_lo(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(bf16_rem(v)); }
+__device__ __forceinline__ void st_lo(__nv_bfloat16* p, double v) {
+  *p = __float2bfloat16_rn((float)(v - (double)__bfloat162float(__float2bfloat16_rn((float)v))));
+}
+template <typename T, typename V> __device__ __forceinline__ void st_lo(T*, V) {}
+
 // two adjacent elements at an even element offset from an aligned base
 __device__ __forceinline__ void st2(double* p, double a, double b) { *(double2*)p = make_double2(a, b); }
 __device__ __forceinline__ void st2(float* p, float a, float b) { *(float2*)p = make_float2(a, b); }
 __device__ __forceinline__ void st2(__nv_bfloat16* p, float a, float b) { *(__nv_bfloat162*)p = __floats2bfloat162_rn(a, b); }
+__device__ __forceinline__ void st2_lo(__nv_bfloat16* p, float a, float b) {
+  *(__nv_bfloat162*)p = __floats2bfloat162_rn(bf16_rem(a), bf16_rem(b));
+}
+template <typename T, typename V> __device__ __forceinline__ void st2_lo(T*, V, V) {}
 
 __device__ __forceinline__ float f_tanh(float x) { return tanhf(x); }
 __device__ __forceinline__ double f_tanh(double x) { return tanh(x); }

@@ -139,6 +139,11 @@ __global__ void k_features_en(const Wlk* __restrict__ r, const double* __restric
     Act* base = X0 + row * ldx + 4 * m;
     for (int a = 0; a < 3; ++a) st(base + a, d[a]);
     st(base + 3, dist);
+    if (SplitValue<Act>::value) {
+      Act* lo = base + sh.T * slab;
+      for (int a = 0; a < 3; ++a) st_lo(lo + a, d[a]);
+      st_lo(lo + 3, dist);
+    }
     if (sh.T == 1) continue;
     for (int t = 1; t < sh.T; ++t) {
       Act* o = base + t * slab;
@@ -183,6 +188,8 @@ __global__ void k_features_mean(const Wlk* __restrict__ r, const double* __restr
       }
   }
   for (int a = 0; a < 4; ++a) st(base + a, v[a] * inv);
+  if (SplitValue<Act>::value)
+    for (int a = 0; a < 4; ++a) st_lo(base + sh.T * slab + a, v[a] * inv);
   if (sh.T == 1) return;
   Act* o = base + (sh.T - 1) * slab;
   st(o, 0.0); st(o + 1, 0.0); st(o + 2, 0.0); st(o + 3, lap * inv);
@@ -365,8 +372,10 @@ __global__ void __launch_bounds__(256) k_pair_full(const Wlk* __restrict__ r, Sh
       for (int jj = sh.n_up; jj < sh.N; ++jj) { dn0 += src[jj * 165 + c0]; dn1 += src[jj * 165 + c1]; }
       const Cmp iu = sh.n_up ? (Cmp)1 / (Cmp)sh.n_up : (Cmp)0, id = sh.n_dn ? (Cmp)1 / (Cmp)sh.n_dn : (Cmp)0;
       const int t = qq == 0 ? 0 : (qq == 1 ? sh.T - 1 : 1 + 3 * ie + (qq - 2));
-      st2(Xc + t * slab + tile_row(w, ie, sh.N, sh.wpt) * ldx + col, half0 ? dn0 * id : up0 * iu,
-          half1 ? dn1 * id : up1 * iu);
+      const Cmp m0 = half0 ? dn0 * id : up0 * iu, m1 = half1 ? dn1 * id : up1 * iu;
+      const int64_t o = tile_row(w, ie, sh.N, sh.wpt) * ldx + col;
+      st2(Xc + t * slab + o, m0, m1);
+      if (SplitValue<Act>::value && qq == 0) st2_lo(Xc + sh.T * slab + o, m0, m1);
     }
     if (l == a.L - 1) break;
     __syncthreads();
@@ -423,7 +432,10 @@ __global__ void __launch_bounds__(512) k_pair_value(const Wlk* __restrict__ r, S
       Cmp sum = 0;
       for (int jj = lo; jj < hi; ++jj) sum += gs[(ii * N + jj) * 33 + c];
       const int64_t rowi = tile_row(w, ii, N, sh.wpt);
-      st(X + rowi * a.ldx[l] + a.col0[l] + s2 * dg + c, hi > lo ? sum / (Cmp)(hi - lo) : (Cmp)0);
+      const Cmp mean = hi > lo ? sum / (Cmp)(hi - lo) : (Cmp)0;
+      Act* o = X + rowi * a.ldx[l] + a.col0[l] + s2 * dg + c;
+      st(o, mean);
+      if (SplitValue<Act>::value) st_lo(o + sh.T * sh.R * a.ldx[l], mean);
     }
     if (l == a.L - 1) break;
     __syncthreads();
@@ -451,7 +463,9 @@ __global__ void __launch_bounds__(512) k_pair_value(const Wlk* __restrict__ r, S
 
 // Spin means of a BF16 stream-layer output, the next layer's mean-field input:
 // Hbar[t][w][s h1 + c] = mean over the electrons i of spin s of Y[t][row(w, i)][c].
-// One thread per (slab, walker, spin, 8 columns); a warp reads 512 contiguous bytes of a row.
+// The value slab adds its low part (slab T of Y) and stores the mean as a pair as well
+// (slab T of Hbar).  One thread per (slab, walker, spin, 8 columns); a warp reads 512
+// contiguous bytes of a row.
 __global__ void k_spin_means_bf16(Shape sh, const __nv_bfloat16* __restrict__ Y, int ldy, int h1,
                                   __nv_bfloat16* __restrict__ Hbar) {
   const int g8 = h1 >> 3;
@@ -466,23 +480,33 @@ __global__ void k_spin_means_bf16(Shape sh, const __nv_bfloat16* __restrict__ Y,
     float acc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = 0.f;
-    const __nv_bfloat16* base = Y + (int64_t)t * sh.R * ldy + 8 * c8;
-    for (int i = lo; i < hi; ++i) {
-      const uint4 u = *(const uint4*)(base + tile_row(w, i, sh.N, sh.wpt) * ldy);
-      const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u;
+    const int parts = t == 0 ? 2 : 1;
+    for (int part = 0; part < parts; ++part) {
+      const __nv_bfloat16* base = Y + (int64_t)(part ? sh.T : t) * sh.R * ldy + 8 * c8;
+      for (int i = lo; i < hi; ++i) {
+        const uint4 u = *(const uint4*)(base + tile_row(w, i, sh.N, sh.wpt) * ldy);
+        const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float2 f = __bfloat1622float2(p2[k]);
-        acc[2 * k] += f.x;
-        acc[2 * k + 1] += f.y;
+        for (int k = 0; k < 4; ++k) {
+          const float2 f = __bfloat1622float2(p2[k]);
+          acc[2 * k] += f.x;
+          acc[2 * k + 1] += f.y;
+        }
       }
     }
     const float sc = hi > lo ? 1.0f / (float)(hi - lo) : 0.f;
-    uint4 o;
+    uint4 o, ol;
     __nv_bfloat162* q = (__nv_bfloat162*)&o;
+    __nv_bfloat162* ql = (__nv_bfloat162*)&ol;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) q[k] = __floats2bfloat162_rn(acc[2 * k] * sc, acc[2 * k + 1] * sc);
-    *(uint4*)(Hbar + ((int64_t)t * sh.B + w) * 2 * h1 + s2 * h1 + 8 * c8) = o;
+    for (int k = 0; k < 4; ++k) {
+      const float a0 = acc[2 * k] * sc, a1 = acc[2 * k + 1] * sc;
+      q[k] = __floats2bfloat162_rn(a0, a1);
+      ql[k] = __floats2bfloat162_rn(bf16_rem(a0), bf16_rem(a1));
+    }
+    const int64_t off = ((int64_t)t * sh.B + w) * 2 * h1 + s2 * h1 + 8 * c8;
+    *(uint4*)(Hbar + off) = o;
+    if (t == 0) *(uint4*)(Hbar + (int64_t)sh.T * sh.B * 2 * h1 + off) = ol;
   }
 }
 
@@ -836,6 +860,10 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
         const __nv_bfloat16* U16 = (const __nv_bfloat16*)ws.prep16 + s->prep.U16[l];
         if (!launch_gemm_tc(sh.T * sh.B, 2 * d.d_h, Hb, 2 * d.d_h, U16, 4 * d.d_h, 2 * d.d_h, h1, (float*)ws.Mterm, h1,
                             (const float*)(prep + s->prep.b[l]), sh.B, 1, false, ws.status, st))
+          const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
+        // value rows: add the low part of the spin means times the high part of U
+        if (!launch_gemm_tc(sh.B, 2 * d.d_h, Hb + (int64_t)sh.T * sh.B * 2 * d.d_h, 2 * d.d_h, U16, 4 * d.d_h, 0, h1,
+                            (float*)ws.Mterm, h1, nullptr, 0, 1, true, ws.status, st))
           const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
       } else {
         gemm<Act, Cmp, Cmp, Cmp>(st, sh.T * sh.B, h1, 2 * d.d_h, Hb, 2 * d.d_h, 1, prep + s->prep.UT[l], h1, 1,

@@ -227,6 +227,9 @@ struct TcArgs {
   // the K range may be split over `ksplit` CTAs per output tile (requires atomic)
   int rows; float* C; int ldc; const float* bias; int bias_rows;
   int ksplit, atomic;
+  // value-slab pairs (BF16 storage): the low part of slab 0 sits at A row alo_row + tile
+  // row; slab-0 items then also multiply it by the high part of B (0: no low part)
+  int64_t alo_row;
   // orbital epilogue
   const float* wbias[2];              // orbital bias g, [K n_s]
   const float* pi[2]; const float* sig[2];
@@ -319,6 +322,21 @@ __device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, bool h
               out[8 * v + 2 * e + 1] += f.y;
             }
           }
+          if (kind == 0 && a.alo_row > 0) {
+            // the value slab's residual is a pair: add its low part (slab T of X)
+            const uint4* xl = (const uint4*)(a.X + (int64_t)T * sh.R * a.ldx + row * a.ldx + col0 + hh * 16);
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+              const uint4 u = xl[v];
+              const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u;
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float2 f = __bfloat1622float2(p2[e]);
+                out[8 * v + 2 * e] += f.x;
+                out[8 * v + 2 * e + 1] += f.y;
+              }
+            }
+          }
         }
         uint4* yo = (uint4*)(a.Y + t * yslab + row * a.ldy + col0 + hh * 16);
 #pragma unroll
@@ -328,6 +346,19 @@ __device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, bool h
 #pragma unroll
           for (int e = 0; e < 4; ++e) p2[e] = __floats2bfloat162_rn(out[8 * v + 2 * e], out[8 * v + 2 * e + 1]);
           yo[v] = u;
+        }
+        if (kind == 0 && a.alo_row > 0) {
+          // and the output's value slab is stored as a pair (slab T of Y)
+          uint4* yl = (uint4*)(a.Y + (int64_t)T * yslab + row * a.ldy + col0 + hh * 16);
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            uint4 u;
+            __nv_bfloat162* p2 = (__nv_bfloat162*)&u;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              p2[e] = __floats2bfloat162_rn(bf16_rem(out[8 * v + 2 * e]), bf16_rem(out[8 * v + 2 * e + 1]));
+            yl[v] = u;
+          }
         }
         if (kind == 0 && a.act_out) {
           float4* ao = (float4*)(a.act_out + row * a.h1 + col0 + hh * 16);
@@ -531,13 +562,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         int tile, kb0, kb1;
         item_range<EPI>(a, pidx, nkb, tile, kb0, kb1);
         const int arow = EPI == kEpiPlain ? tile * 128 : (int)(t * sh.R + (int64_t)tile * 128);
-        for (int kb = kb0; kb < kb1; ++kb, ++issued) {
+        const int nk = kb1 - kb0;
+        const int n_k = (EPI != kEpiPlain && a.alo_row > 0 && t == 0) ? 2 * nk : nk;
+        for (int kk = 0; kk < n_k; ++kk, ++issued) {
+          const bool lo = kk >= nk;
+          const int kb = kb0 + (lo ? kk - nk : kk);
+          const int parts = lo ? 1 : nbparts;
           const int stage = issued % kStages;
           const uint32_t round = (uint32_t)(issued / kStages);
           if (*abort_flag || !mbar_wait(empty + stage, (round & 1u) ^ 1u, deadline)) { ok = false; break; }
-          mbar_expect_tx(full + stage, bytesA + nbparts * bytesB);
-          tma_load_2d(sA + stage * bytesA, &tmA, full + stage, kb * kBlockK, arow);
-          for (int part = 0; part < nbparts; ++part)
+          mbar_expect_tx(full + stage, bytesA + parts * bytesB);
+          tma_load_2d(sA + stage * bytesA, &tmA, full + stage, kb * kBlockK,
+                      lo ? (int)(a.alo_row + (int64_t)tile * 128) : arow);
+          for (int part = 0; part < parts; ++part)
             tma_load_2d(sB + (stage * nbparts + part) * bytesB, &tmB, full + stage, part * a.bsplit + kb * kBlockK,
                         brow0);
         }
@@ -564,18 +601,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         int tile, kb0, kb1;
         item_range<EPI>(a, (int)blockIdx.y + (item / T) * (int)gridDim.y, nkb, tile, kb0, kb1);
         (void)tile;
-        for (int kb = kb0; kb < kb1; ++kb, ++consumed) {
+        const int t = item % T;
+        const int nk = kb1 - kb0;
+        const int n_k = (EPI != kEpiPlain && a.alo_row > 0 && t == 0) ? 2 * nk : nk;
+        for (int kk = 0; kk < n_k; ++kk, ++consumed) {
+          const int parts = kk >= nk ? 1 : nbparts;
           const int stage = consumed % kStages;
           const uint32_t round = (uint32_t)(consumed / kStages);
           if (*abort_flag || !mbar_wait(full + stage, round & 1u, deadline)) { ok = false; break; }
           fence_after();
           const uint64_t da = sdesc(smem_u32(sA + stage * bytesA));
-          for (int part = 0; part < nbparts; ++part) {
+          for (int part = 0; part < parts; ++part) {
             const uint64_t db = sdesc(smem_u32(sB + (stage * nbparts + part) * bytesB));
 #pragma unroll
             for (int k4 = 0; k4 < kBlockK / 16; ++k4)
               mma_bf16(d, da + (uint64_t)(2 * k4), db + (uint64_t)(2 * k4), idesc,
-                       (kb != kb0 || k4 != 0 || part != 0) ? 1u : 0u);
+                       (kk != 0 || k4 != 0 || part != 0) ? 1u : 0u);
           }
           mma_commit(empty + stage);
         }
@@ -762,7 +803,8 @@ bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const 
                      int ldy, int residual, float* act_out, int h1, int* status, cudaStream_t st) {
   const int nt = tc_columns(h1);
   CUtensorMap ta, tb;
-  if (!make_map(&ta, X, k_self, (int64_t)sh.T * sh.R, ldx, 128)) return false;
+  // slabs 0..T-1 and the value slab's low part (slab T)
+  if (!make_map(&ta, X, k_self, (int64_t)(sh.T + 1) * sh.R, ldx, 128)) return false;
   if (!make_map(&tb, Vs16, ldx + k_self, h1, 2 * ldx, nt)) return false;
   tc::TcArgs a{};
   a.sh = sh;
@@ -778,6 +820,7 @@ bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const 
   a.residual = residual;
   a.act_out = act_out;
   a.bsplit = ldx;
+  a.alo_row = (int64_t)sh.T * sh.R;
   // stage M[t] in shared memory when the tile's walkers fit beside the ring
   a.mt_stage = tc_smem_bytes(nt, tc::kEpiLayer, true, sh.wpt) <= kMaxDynamicSmem ? 1 : 0;
   const bool full = sh.T > 1;
@@ -832,7 +875,7 @@ bool launch_orbitals_tc(const Shape& sh, const void* HL, int h1, const void* W16
   const int nmax = std::max(sh.n_up, sh.n_dn);
   const int nt = (int)std::min<int64_t>(128, round_up((int64_t)K * nmax, 32));
   CUtensorMap ta, tb;
-  if (!make_map(&ta, HL, h1, (int64_t)sh.T * sh.R, h1, 128)) return false;
+  if (!make_map(&ta, HL, h1, (int64_t)(sh.T + 1) * sh.R, h1, 128)) return false;
   if (!make_map(&tb, W16, 2 * h1, (int64_t)K * sh.N, 2 * h1, nt)) return false;
   tc::TcArgs a{};
   a.sh = sh;
@@ -852,6 +895,7 @@ bool launch_orbitals_tc(const Shape& sh, const void* HL, int h1, const void* W16
   a.orbP = orbP;
   a.bsplit = h1;
   a.envv = envv;
+  a.alo_row = (int64_t)sh.T * sh.R;
   const bool full = sh.T > 1;
   a.tmem_cols = pow2_cols(3 * nt);
   a.tiles = sh.tiles;

@@ -62,11 +62,12 @@ static size_t value_pass_layout(const fn_system* s, int B, unsigned char* base, 
     return o;
   };
   size_t o_X[kMaxLayers], o_Hbar[kMaxLayers];
+  const int Tx = Mode::kMode == FN_BF16_MIXED ? 2 : 1;       // value slab and, in BF16 storage, its low part
   for (int l = 0; l < L; ++l) {
-    o_X[l] = take((size_t)sh.R * s->layer[l].ldx * sizeof(Act));
-    o_Hbar[l] = take((size_t)B * 2 * s->layer[l].d_h * sizeof(Act));
+    o_X[l] = take((size_t)Tx * sh.R * s->layer[l].ldx * sizeof(Act));
+    o_Hbar[l] = take((size_t)Tx * B * 2 * s->layer[l].d_h * sizeof(Act));
   }
-  const size_t o_HL = take((size_t)sh.R * h1 * sizeof(Act));
+  const size_t o_HL = take((size_t)Tx * sh.R * h1 * sizeof(Act));
   const size_t o_M = take((size_t)B * h1 * sizeof(Cmp));
   const size_t o_Phi = take((size_t)B * phi_walker_stride(s, 1) * sizeof(typename Mode::PhiT));
   const size_t o_prep = take((size_t)s->prep.total * sizeof(Cmp));
