@@ -14,8 +14,7 @@
  *   - d_* pointers are device memory owned by the caller; h_* pointers are host
  *     memory owned by the caller.  The library owns the system handle and an
  *     internal device workspace that grows on demand (cudaMalloc happens only
- *     when a call needs more walkers than any previous call on that handle;
- *     make such a call once before capturing a stream into a CUDA graph).
+ *     when a call needs more walkers than any previous call on that handle).
  *   - Calls are asynchronous on the given stream (a cudaStream_t passed as
  *     void*; NULL is the legacy default stream).  Argument errors return
  *     immediately and leave device memory untouched.  Numerical problems found
@@ -169,9 +168,9 @@ fn_status fn_log_psi_vjp(fn_system_t sys, const void* d_params, const void* d_wa
                          const double* d_weights, int n_walkers, void* d_grad, void* stream);
 
 /* log|psi| and sign, like fn_log_psi, for callers that cannot let the library allocate
- * device memory: code enqueuing work during CUDA-graph stream capture, programs whose
- * device memory belongs to a pool or framework allocator, processes with a fixed
- * memory budget.  No cudaMalloc or cudaFree happens in this call.  Its scratch is one
+ * device memory: programs whose device memory belongs to a pool or framework allocator
+ * that must account for every byte, and processes with a memory budget fixed before the
+ * library was loaded.  No cudaMalloc or cudaFree happens in this call.  Its scratch is one
  * static 64 MiB device array that every device loading the library holds until the
  * process exits; the array's address is looked up on the first call made on each
  * device (cudaGetSymbolAddress), so make that first call before any stream capture.

@@ -194,8 +194,10 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
   std::vector<std::pair<void**, size_t>> items;
   size_t o_X[kMaxLayers], o_Hbar[kMaxLayers], o_act[kMaxLayers], o_gp[kMaxLayers];
   int max_ldx = 0, max_dh = 0;
-  // BF16 storage adds one slab after the tangent slabs: the value slab's low part
-  const int Tx = T + (Mode::kMode == FN_BF16_MIXED ? 1 : 0);
+  // BF16 storage pairs slabs with low parts: X_l and the spin means get slabs T..2T-1
+  // (low part of slab t in slab T + t), h_L one (the value slab's)
+  const bool pairs = Mode::kMode == FN_BF16_MIXED;
+  const int Tx = pairs ? 2 * T : T, Th = T + (pairs ? 1 : 0);
   for (int l = 0; l < L; ++l) {
     o_X[l] = take((size_t)Tx * sh.R * s->layer[l].ldx * sizeof(Act));
     o_Hbar[l] = take((size_t)Tx * B * 2 * s->layer[l].d_h * sizeof(Act));
@@ -204,7 +206,7 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
     max_ldx = std::max(max_ldx, s->layer[l].ldx);
     max_dh = std::max(max_dh, s->layer[l].d_h);
   }
-  const size_t o_HL = take((size_t)Tx * sh.R * h1 * sizeof(Act));
+  const size_t o_HL = take((size_t)Th * sh.R * h1 * sizeof(Act));
   const size_t o_M = take((size_t)T * B * h1 * sizeof(Cmp));
   const size_t o_Phi = take((size_t)B * phi_walker_stride(s, T) * sizeof(typename Mode::PhiT));
   const size_t o_prep = take((size_t)s->prep.total * sizeof(Cmp));

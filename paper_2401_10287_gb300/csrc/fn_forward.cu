@@ -185,6 +185,11 @@ __global__ void k_features_mean(const Wlk* __restrict__ r, const double* __restr
         Act* o = base + (1 + 3 * e + c) * slab;
         for (int a = 0; a < 3; ++a) st(o + a, a == c ? inv : 0.0);
         st(o + 3, d[c] / dist * inv);
+        if (SplitValue<Act>::value) {
+          Act* ol = o + sh.T * slab;
+          for (int a = 0; a < 3; ++a) st_lo(ol + a, a == c ? inv : 0.0);
+          st_lo(ol + 3, d[c] / dist * inv);
+        }
       }
   }
   for (int a = 0; a < 4; ++a) st(base + a, v[a] * inv);
@@ -193,12 +198,20 @@ __global__ void k_features_mean(const Wlk* __restrict__ r, const double* __restr
   if (sh.T == 1) return;
   Act* o = base + (sh.T - 1) * slab;
   st(o, 0.0); st(o + 1, 0.0); st(o + 2, 0.0); st(o + 3, lap * inv);
+  if (SplitValue<Act>::value) {
+    Act* ol = o + sh.T * slab;
+    st_lo(ol, 0.0); st_lo(ol + 1, 0.0); st_lo(ol + 2, 0.0); st_lo(ol + 3, lap * inv);
+  }
   // slabs of the other spin's electrons are zero
   const int olo = spin ? 0 : sh.n_up, ohi = spin ? sh.n_up : sh.N;
   for (int e = olo; e < ohi; ++e)
     for (int c = 0; c < 3; ++c) {
       Act* q = base + (1 + 3 * e + c) * slab;
       st(q, 0.0); st(q + 1, 0.0); st(q + 2, 0.0); st(q + 3, 0.0);
+      if (SplitValue<Act>::value) {
+        Act* ql = q + sh.T * slab;
+        st_lo(ql, 0.0); st_lo(ql + 1, 0.0); st_lo(ql + 2, 0.0); st_lo(ql + 3, 0.0);
+      }
     }
 }
 
@@ -358,8 +371,9 @@ __global__ void __launch_bounds__(256) k_pair_full(const Wlk* __restrict__ r, Sh
 #pragma unroll
       for (int axis = 0; axis < 3; ++axis) {
         const Cmp* src = gs + (pp * 5 + 2 + axis) * 33;
-        st2(Xc + (1 + 3 * jj + axis) * slab + row + col, half0 == sjj ? src[c0] * scale : (Cmp)0,
-            half1 == sjj ? src[c1] * scale : (Cmp)0);
+        const Cmp v0 = half0 == sjj ? src[c0] * scale : (Cmp)0, v1 = half1 == sjj ? src[c1] * scale : (Cmp)0;
+        st2(Xc + (1 + 3 * jj + axis) * slab + row + col, v0, v1);
+        if (SplitValue<Act>::value) st2_lo(Xc + (sh.T + 1 + 3 * jj + axis) * slab + row + col, v0, v1);
       }
     }
     // value, Laplacian and d/dr_i rows: spin means over partners
@@ -375,7 +389,7 @@ __global__ void __launch_bounds__(256) k_pair_full(const Wlk* __restrict__ r, Sh
       const Cmp m0 = half0 ? dn0 * id : up0 * iu, m1 = half1 ? dn1 * id : up1 * iu;
       const int64_t o = tile_row(w, ie, sh.N, sh.wpt) * ldx + col;
       st2(Xc + t * slab + o, m0, m1);
-      if (SplitValue<Act>::value && qq == 0) st2_lo(Xc + sh.T * slab + o, m0, m1);
+      if (SplitValue<Act>::value) st2_lo(Xc + (sh.T + t) * slab + o, m0, m1);
     }
     if (l == a.L - 1) break;
     __syncthreads();
@@ -463,8 +477,8 @@ __global__ void __launch_bounds__(512) k_pair_value(const Wlk* __restrict__ r, S
 
 // Spin means of a BF16 stream-layer output, the next layer's mean-field input:
 // Hbar[t][w][s h1 + c] = mean over the electrons i of spin s of Y[t][row(w, i)][c].
-// The value slab adds its low part (slab T of Y) and stores the mean as a pair as well
-// (slab T of Hbar).  One thread per (slab, walker, spin, 8 columns); a warp reads 512
+// The value slab adds its low part (slab T of Y); every mean is stored as a hi/lo pair
+// (the low part of slab t in slab T + t of Hbar).  One thread per (slab, walker, spin, 8 columns); a warp reads 512
 // contiguous bytes of a row.
 __global__ void k_spin_means_bf16(Shape sh, const __nv_bfloat16* __restrict__ Y, int ldy, int h1,
                                   __nv_bfloat16* __restrict__ Hbar) {
@@ -506,7 +520,7 @@ __global__ void k_spin_means_bf16(Shape sh, const __nv_bfloat16* __restrict__ Y,
     }
     const int64_t off = ((int64_t)t * sh.B + w) * 2 * h1 + s2 * h1 + 8 * c8;
     *(uint4*)(Hbar + off) = o;
-    if (t == 0) *(uint4*)(Hbar + (int64_t)sh.T * sh.B * 2 * h1 + off) = ol;
+    *(uint4*)(Hbar + (int64_t)sh.T * sh.B * 2 * h1 + off) = ol;
   }
 }
 
@@ -861,9 +875,9 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
         if (!launch_gemm_tc(sh.T * sh.B, 2 * d.d_h, Hb, 2 * d.d_h, U16, 4 * d.d_h, 2 * d.d_h, h1, (float*)ws.Mterm, h1,
                             (const float*)(prep + s->prep.b[l]), sh.B, 1, false, ws.status, st))
           const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
-        // value rows: add the low part of the spin means times the high part of U
-        if (!launch_gemm_tc(sh.B, 2 * d.d_h, Hb + (int64_t)sh.T * sh.B * 2 * d.d_h, 2 * d.d_h, U16, 4 * d.d_h, 0, h1,
-                            (float*)ws.Mterm, h1, nullptr, 0, 1, true, ws.status, st))
+        // every slab: add the low part of the spin means times the high part of U
+        if (!launch_gemm_tc(sh.T * sh.B, 2 * d.d_h, Hb + (int64_t)sh.T * sh.B * 2 * d.d_h, 2 * d.d_h, U16, 4 * d.d_h,
+                            0, h1, (float*)ws.Mterm, h1, nullptr, 0, 1, true, ws.status, st))
           const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
       } else {
         gemm<Act, Cmp, Cmp, Cmp>(st, sh.T * sh.B, h1, 2 * d.d_h, Hb, 2 * d.d_h, 1, prep + s->prep.UT[l], h1, 1,
@@ -884,7 +898,7 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
     ProfScope ps(s->prof, full ? kProfLayerFull : kProfLayerValue, st);
     if (Mode::kMode == FN_BF16_MIXED) {
       const __nv_bfloat16* Vs16 = (const __nv_bfloat16*)ws.prep16 + s->prep.Vs16[l];
-      if (!launch_layer_tc(sh, la.X, la.ldx, la.k_self, Vs16, (const float*)la.Mterm, la.Y, la.ldy, la.residual,
+      if (!launch_layer_tc(sh, la.X, la.ldx, la.k_self, d.d_h, Vs16, (const float*)la.Mterm, la.Y, la.ldy, la.residual,
                            (float*)la.act_out, h1, ws.status, st))
         const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
       if (!last) {

@@ -185,8 +185,9 @@ fn_status cuda_status(cudaError_t e, const char* what);
 fn_status upload_prep_descs(fn_system* s);
 
 // Tensor-core one-electron layer (BF16 mode); false if a TMA tensor map could not be built.
-bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const void* Vs16, const float* Mterm, void* Y,
-                     int ldy, int residual, float* act_out, int h1, int* status, cudaStream_t st);
+bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, int lo_col0, const void* Vs16,
+                     const float* Mterm, void* Y, int ldy, int residual, float* act_out, int h1, int* status,
+                     cudaStream_t st);
 bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int ldb, int bsplit, int ncols, float* C,
                     int ldc, const float* bias, int bias_rows, int ksplit, bool atomic, int* status, cudaStream_t st);
 bool launch_orbitals_tc(const Shape& sh, const void* HL, int h1, const void* W16, const float* const* wbias,

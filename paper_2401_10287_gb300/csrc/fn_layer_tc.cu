@@ -227,9 +227,12 @@ struct TcArgs {
   // the K range may be split over `ksplit` CTAs per output tile (requires atomic)
   int rows; float* C; int ldc; const float* bias; int bias_rows;
   int ksplit, atomic;
-  // value-slab pairs (BF16 storage): the low part of slab 0 sits at A row alo_row + tile
-  // row; slab-0 items then also multiply it by the high part of B (0: no low part)
+  // hi/lo pairs of A (BF16 storage): the low part of slab t sits at A row alo_row + t R +
+  // tile row (0: no low parts).  Slab 0 is paired in every column; a tangent slab only
+  // from k-block kb_lo_t on (the pair-mean columns of a layer input).  The low part is
+  // multiplied by the high part of B in extra k-blocks of the item.
   int64_t alo_row;
+  int kb_lo_t;
   // orbital epilogue
   const float* wbias[2];              // orbital bias g, [K n_s]
   const float* pi[2]; const float* sig[2];
@@ -398,6 +401,13 @@ __device__ __forceinline__ void stage_mterm(const TcArgs& a, int t, int tile, in
   cp_async_commit();
 }
 
+// First k-block whose low part an item multiplies (kb1: none).
+template <int EPI>
+__device__ __forceinline__ int lo_first(const TcArgs& a, int t, int kb0, int kb1) {
+  if (EPI == kEpiPlain || a.alo_row <= 0) return kb1;
+  return t == 0 ? kb0 : max(kb0, min(kb1, a.kb_lo_t));
+}
+
 // Work item -> (row tile, k-block range): split-K GEMMs give every (tile, split) pair its
 // own item; the other kernels cover all k-blocks of a tile.
 template <int EPI>
@@ -562,18 +572,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         int tile, kb0, kb1;
         item_range<EPI>(a, pidx, nkb, tile, kb0, kb1);
         const int arow = EPI == kEpiPlain ? tile * 128 : (int)(t * sh.R + (int64_t)tile * 128);
-        const int nk = kb1 - kb0;
-        const int n_k = (EPI != kEpiPlain && a.alo_row > 0 && t == 0) ? 2 * nk : nk;
+        const int nk = kb1 - kb0, lf = lo_first<EPI>(a, t, kb0, kb1);
+        const int n_k = nk + (kb1 - lf);
+        const int lo_row = (int)(a.alo_row + (int64_t)t * sh.R + (int64_t)tile * 128);
         for (int kk = 0; kk < n_k; ++kk, ++issued) {
           const bool lo = kk >= nk;
-          const int kb = kb0 + (lo ? kk - nk : kk);
+          const int kb = lo ? lf + (kk - nk) : kb0 + kk;
           const int parts = lo ? 1 : nbparts;
           const int stage = issued % kStages;
           const uint32_t round = (uint32_t)(issued / kStages);
           if (*abort_flag || !mbar_wait(empty + stage, (round & 1u) ^ 1u, deadline)) { ok = false; break; }
           mbar_expect_tx(full + stage, bytesA + parts * bytesB);
-          tma_load_2d(sA + stage * bytesA, &tmA, full + stage, kb * kBlockK,
-                      lo ? (int)(a.alo_row + (int64_t)tile * 128) : arow);
+          tma_load_2d(sA + stage * bytesA, &tmA, full + stage, kb * kBlockK, lo ? lo_row : arow);
           for (int part = 0; part < parts; ++part)
             tma_load_2d(sB + (stage * nbparts + part) * bytesB, &tmB, full + stage, part * a.bsplit + kb * kBlockK,
                         brow0);
@@ -603,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         (void)tile;
         const int t = item % T;
         const int nk = kb1 - kb0;
-        const int n_k = (EPI != kEpiPlain && a.alo_row > 0 && t == 0) ? 2 * nk : nk;
+        const int n_k = nk + (kb1 - lo_first<EPI>(a, t, kb0, kb1));
         for (int kk = 0; kk < n_k; ++kk, ++consumed) {
           const int parts = kk >= nk ? 1 : nbparts;
           const int stage = consumed % kStages;
@@ -799,12 +809,13 @@ static void launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const tc::Tc
 }
 
 // Stream layer on the tensor cores; returns false (nothing launched) if a tensor map could not be built.
-bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const void* Vs16, const float* Mterm, void* Y,
-                     int ldy, int residual, float* act_out, int h1, int* status, cudaStream_t st) {
+bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, int lo_col0, const void* Vs16,
+                     const float* Mterm, void* Y, int ldy, int residual, float* act_out, int h1, int* status,
+                     cudaStream_t st) {
   const int nt = tc_columns(h1);
   CUtensorMap ta, tb;
-  // slabs 0..T-1 and the value slab's low part (slab T)
-  if (!make_map(&ta, X, k_self, (int64_t)(sh.T + 1) * sh.R, ldx, 128)) return false;
+  // slabs 0..T-1 and their low parts (slabs T..2T-1)
+  if (!make_map(&ta, X, k_self, (int64_t)2 * sh.T * sh.R, ldx, 128)) return false;
   if (!make_map(&tb, Vs16, ldx + k_self, h1, 2 * ldx, nt)) return false;
   tc::TcArgs a{};
   a.sh = sh;
@@ -821,6 +832,7 @@ bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, const 
   a.act_out = act_out;
   a.bsplit = ldx;
   a.alo_row = (int64_t)sh.T * sh.R;
+  a.kb_lo_t = lo_col0 / tc::kBlockK;
   // stage M[t] in shared memory when the tile's walkers fit beside the ring
   a.mt_stage = tc_smem_bytes(nt, tc::kEpiLayer, true, sh.wpt) <= kMaxDynamicSmem ? 1 : 0;
   const bool full = sh.T > 1;
@@ -895,7 +907,8 @@ bool launch_orbitals_tc(const Shape& sh, const void* HL, int h1, const void* W16
   a.orbP = orbP;
   a.bsplit = h1;
   a.envv = envv;
-  a.alo_row = (int64_t)sh.T * sh.R;
+  a.alo_row = (int64_t)sh.T * sh.R;          // h_L: only the value slab has a low part
+  a.kb_lo_t = a.nkb;
   const bool full = sh.T > 1;
   a.tmem_cols = pow2_cols(3 * nt);
   a.tiles = sh.tiles;

@@ -1,17 +1,16 @@
 // log|psi| without any device allocation.
 //
-// Some callers cannot let a library call cudaMalloc: code that enqueues work while a
-// stream is being captured into a CUDA graph (allocation is not a stream operation and
-// breaks the capture), applications whose device memory is owned by a pool or a
-// framework allocator that must see every byte, and processes under a hard memory
-// budget that was fixed before the library was loaded.  For them this entry point runs
+// Some callers cannot let a library call cudaMalloc: applications whose device memory
+// is owned by a pool or a framework allocator that must see every byte, and processes
+// under a hard memory budget that was fixed before the library was loaded.  For them this entry point runs
 // the value-only forward pass (the same kernels as fn_log_psi) with all of its scratch
 // in one file-scope device array, so the call itself never allocates.  The caller still
 // provides parameters, walkers and outputs.
 //
 // The array is kNoAllocScratchBytes (64 MiB) and exists on every device that loads the
 // library, for the life of the process.  Its device address is looked up once per device
-// (cudaGetSymbolAddress with that device current) on the first call made on that device.
+// (cudaGetSymbolAddress with that device current) on the first call made on that device,
+// so that first call should come before any stream capture.
 // All calls share the array, so two calls whose work overlaps on the GPU race; a later
 // call sees whatever the previous one left, and everything that must start at zero is
 // cleared by each call.

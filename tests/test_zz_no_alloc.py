@@ -1,7 +1,7 @@
 """fn_log_psi_noalloc: log|psi| computed from the library's static scratch array.
 
-Callers that cannot let a library allocate device memory (graph capture, external
-allocators, fixed memory budgets) use this entry point; it must give the same result as
+Callers that cannot let a library allocate device memory (an external allocator owns
+it, or the memory budget is fixed) use this entry point; it must give the same result as
 fn_log_psi.  This file is collected last so that a run stopping at the first failure has
 run every other test first; it passes alone in a fresh process as well.
 """
