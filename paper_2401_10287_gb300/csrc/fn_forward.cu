@@ -872,12 +872,9 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
       ProfScope ps(s->prof, kProfMeanGemm, st);
       if (Mode::kMode == FN_BF16_MIXED) {
         const __nv_bfloat16* U16 = (const __nv_bfloat16*)ws.prep16 + s->prep.U16[l];
+        // the spin means are hi/lo pairs: rows T B .. 2 T B hold the low parts
         if (!launch_gemm_tc(sh.T * sh.B, 2 * d.d_h, Hb, 2 * d.d_h, U16, 4 * d.d_h, 2 * d.d_h, h1, (float*)ws.Mterm, h1,
-                            (const float*)(prep + s->prep.b[l]), sh.B, 1, false, ws.status, st))
-          const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
-        // every slab: add the low part of the spin means times the high part of U
-        if (!launch_gemm_tc(sh.T * sh.B, 2 * d.d_h, Hb + (int64_t)sh.T * sh.B * 2 * d.d_h, 2 * d.d_h, U16, 4 * d.d_h,
-                            0, h1, (float*)ws.Mterm, h1, nullptr, 0, 1, true, ws.status, st))
+                            (const float*)(prep + s->prep.b[l]), sh.B, 1, false, ws.status, st, sh.T * sh.B))
           const_cast<fn_system*>(s)->host_error = FN_ERR_CUDA;
       } else {
         gemm<Act, Cmp, Cmp, Cmp>(st, sh.T * sh.B, h1, 2 * d.d_h, Hb, 2 * d.d_h, 1, prep + s->prep.UT[l], h1, 1,

@@ -189,7 +189,8 @@ bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, int lo
                      const float* Mterm, void* Y, int ldy, int residual, float* act_out, int h1, int* status,
                      cudaStream_t st);
 bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int ldb, int bsplit, int ncols, float* C,
-                    int ldc, const float* bias, int bias_rows, int ksplit, bool atomic, int* status, cudaStream_t st);
+                    int ldc, const float* bias, int bias_rows, int ksplit, bool atomic, int* status, cudaStream_t st,
+                    int a_lo_row = 0);
 bool launch_orbitals_tc(const Shape& sh, const void* HL, int h1, const void* W16, const float* const* wbias,
                         const float* const* pi, const float* const* sig, int K, int aniso, const float* walkers,
                         const double* nuclei, void* Phi, int64_t PW, float* orbP, const float* envv, int* status,

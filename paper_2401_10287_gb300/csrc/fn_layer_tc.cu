@@ -404,7 +404,8 @@ __device__ __forceinline__ void stage_mterm(const TcArgs& a, int t, int tile, in
 // First k-block whose low part an item multiplies (kb1: none).
 template <int EPI>
 __device__ __forceinline__ int lo_first(const TcArgs& a, int t, int kb0, int kb1) {
-  if (EPI == kEpiPlain || a.alo_row <= 0) return kb1;
+  if (a.alo_row <= 0) return kb1;
+  if (EPI == kEpiPlain) return kb0;
   return t == 0 ? kb0 : max(kb0, min(kb1, a.kb_lo_t));
 }
 
@@ -846,18 +847,22 @@ bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, int lo
 // bias_rows), or C += A B^T by atomic adds with the k range split over `ksplit` CTAs per
 // output tile.  A: bf16 K-major, row stride lda elements.  B: bf16 K-major, row stride ldb;
 // with bsplit > 0 it holds bf16(W) in columns [0, k) and bf16(W - bf16(W)) in
-// [bsplit, bsplit + k), and both are multiplied.  Returns false (nothing launched) if a
-// tensor map could not be built or the shapes are outside what the kernel covers.
+// [bsplit, bsplit + k), and both are multiplied.  With a_lo_row > 0, A row a_lo_row + r
+// holds the low part of row r (a hi/lo BF16 pair), multiplied by the high part of B in
+// extra k-blocks.  Returns false (nothing launched) if a tensor map could not be built or
+// the shapes are outside what the kernel covers.
 bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int ldb, int bsplit, int ncols, float* C,
-                    int ldc, const float* bias, int bias_rows, int ksplit, bool atomic, int* status, cudaStream_t st) {
+                    int ldc, const float* bias, int bias_rows, int ksplit, bool atomic, int* status, cudaStream_t st,
+                    int a_lo_row) {
   if (rows <= 0 || k <= 0 || ncols <= 0) return true;
   const int nt = ncols >= 128 ? 128 : (ncols > 64 ? 128 : (ncols > 32 ? 64 : 32));
   const int ctiles = (ncols + nt - 1) / nt;
   const int nkb = (k + tc::kBlockK - 1) / tc::kBlockK;
   ksplit = std::max(1, std::min(ksplit, nkb));
   if (ksplit > 1 && !atomic) return false;
+  if (a_lo_row > 0 && (ksplit > 1 || a_lo_row < rows)) return false;
   CUtensorMap ta, tb;
-  if (!make_map(&ta, A, k, rows, lda, 128)) return false;
+  if (!make_map(&ta, A, k, a_lo_row > 0 ? (int64_t)a_lo_row + rows : rows, lda, 128)) return false;
   if (!make_map(&tb, Bw, bsplit ? bsplit + k : k, ncols, ldb, nt)) return false;
   tc::TcArgs a{};
   a.sh.T = 1;
@@ -873,6 +878,7 @@ bool launch_gemm_tc(int rows, int k, const void* A, int lda, const void* Bw, int
   a.bsplit = bsplit;
   a.ksplit = ksplit;
   a.atomic = atomic ? 1 : 0;
+  a.alo_row = a_lo_row;
   a.tmem_cols = pow2_cols(2 * nt);
   a.tiles = (rows + 127) / 128 * ksplit;
   launch_tc<tc::kEpiPlain>(ta, tb, a, persistent_grid(ctiles, a.tiles), false, st);
