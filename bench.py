@@ -317,6 +317,9 @@ def run_mine(args):
     if not args.no_cpu_baseline and ws == 1:
         cb = cpu_baseline(args.precision)
     launches_total = int(sum(v[0] for v in prof.values()))
+    comparison = None
+    if prec == P.BF16_MIXED and ws == 1 and not args.no_compare:
+        comparison = compare_modes(P, sysm, a, cfg, B, ms / args.steps)
     serving = None
     if args.serving_jobs > 0 and ws == 1:
         serving = run_serving(args.serving_jobs, args.serving_budget_gb, args.serving_slots)
@@ -324,7 +327,8 @@ def run_mine(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"bf16": "bf16", "fp32": "f32", "fp64": "f64"}[args.precision],
-        "precision_mode": {"bf16": "BF16 tensor-core stream GEMMs, FP32 elementwise, FP64 determinants and E_L",
+        "precision_mode": {"bf16": "BF16 tensor-core stream GEMMs (hi/lo BF16 pairs for values and mean tangents), "
+                                   "FP32 elementwise, FP64 determinants and E_L",
                            "fp32": "FP32 throughout, FP64 energy accumulation",
                            "fp64": "FP64 throughout"}[args.precision],
         "data": "synthetic",
@@ -339,6 +343,7 @@ def run_mine(args):
         "roofline": roof,
         "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         "cpu_baseline": cb,
+        "bf16_vs_fp32_and_fp64": comparison,
         "serving": serving,
         "acceptance": float(acc.item()) / max(1, (args.warmup + 2 * args.steps) * cfg["mcmc_steps"] * B),
     }
@@ -346,6 +351,56 @@ def run_mine(args):
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+def compare_modes(P, sysm, a, cfg, B, bf16_ms):
+    """Outside the timed region: (1) the FP32 step time on the same workload and step (the
+    plain-precision baseline of the metric); (2) the BF16 energy error against the FP64 path
+    (equal to the FP64 oracle within 1e-8, see the parity tests) on B walkers equilibrated by
+    300 BF16 Metropolis steps."""
+    import torch
+    seed = cfg["seed"]
+    g32 = P.System(sysm.nuclei, sysm.charges, sysm.n_up, sysm.n_down, P.NetConfig.from_ansatz(a, P.FP32))
+    p32 = g32.init_params(seed)
+
+    def step32(k):
+        w, _ = g32.init_walkers(B, seed + 1000 * k, cfg["init_std"])
+        lp, _ = g32.log_psi(p32, w)
+        g32.mcmc_steps(p32, w, lp, cfg["mcmc_steps"], cfg["step_size"], seed, step_offset=k * 64)
+        e, _, _ = g32.local_energy(p32, w)
+        g32.energy_grad(p32, w, e)
+    step32(0)
+    torch.cuda.synchronize()
+    t = []
+    for k in range(1, 3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step32(k)
+        e1.record()
+        e1.synchronize()
+        t.append(e0.elapsed_time(e1))
+    fp32_ms = float(np.mean(t))
+    g32.close()
+    g16 = P.System(sysm.nuclei, sysm.charges, sysm.n_up, sysm.n_down, P.NetConfig.from_ansatz(a, P.BF16_MIXED))
+    g64 = P.System(sysm.nuclei, sysm.charges, sysm.n_up, sysm.n_down, P.NetConfig.from_ansatz(a, P.FP64))
+    p16 = g16.init_params(seed)
+    w, _ = g16.init_walkers(B, seed + 77, cfg["init_std"])
+    lp, _ = g16.log_psi(p16, w)
+    g16.mcmc_steps(p16, w, lp, 300, cfg["step_size"], seed + 78)
+    e16, _, _ = g16.local_energy(p16, w)
+    e64, _, _ = g64.local_energy(p16.double(), w.double())
+    torch.cuda.synchronize()
+    d = (e16 - e64).cpu().numpy()
+    e64m = float(e64.mean())
+    g16.close()
+    g64.close()
+    return {"fp32_ms_per_step": fp32_ms, "bf16_speedup_vs_fp32": fp32_ms / bf16_ms,
+            "bf16_energy_error": {"walkers": B, "equilibration": "300 BF16 Metropolis steps",
+                                  "reference": "FP64 path on the same walkers and parameters",
+                                  "mean_energy_fp64_ha": e64m, "bias_mha": float(d.mean() * 1e3),
+                                  "bias_stderr_mha": float(d.std() / np.sqrt(B) * 1e3),
+                                  "median_abs_de_ha": float(np.median(np.abs(d)))}}
 
 
 def run_serving(n_jobs: int, budget_gb: float, slots: int):
@@ -381,6 +436,8 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
     ap.add_argument("--walkers", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP32 step time and the BF16-vs-FP64 energy error after the timed region")
     ap.add_argument("--serving-jobs", type=int, default=150,
                     help="jobs of the serving stream to replay after the timed steps (0 to skip)")
     ap.add_argument("--serving-budget-gb", type=float, default=160.0)
