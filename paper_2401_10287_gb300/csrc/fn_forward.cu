@@ -524,6 +524,129 @@ __global__ void k_spin_means_bf16(Shape sh, const __nv_bfloat16* __restrict__ Y,
   }
 }
 
+// Value pass of the two-electron stream in BF16 mode.  Per walker the products
+// [N^2 pairs x d_g] x [d_g x h2] of every pair layer run on warp-level BF16 tensor-core
+// MMAs (m16n8k16, FP32 accumulation).  Activations and weights are split into hi/lo BF16
+// parts and the three leading products are accumulated (about 16 significant bits, the
+// precision the BF16 storage keeps for the pair means).  One CTA per walker, 4 warps over
+// 16-pair row tiles; the pair activations stay in shared memory (FP32) between layers.
+constexpr int kPairWLd = 40;   // bf16 row stride of the staged weights: conflict-free fragment loads
+
+__device__ __forceinline__ void split_pack(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  hi = *(const uint32_t*)&h;
+  lo = *(const uint32_t*)&l;
+}
+
+__device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <typename Wlk>
+__global__ void __launch_bounds__(128) k_pair_value_mma(const Wlk* __restrict__ r, Shape sh, PairArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L1 = a.L - 1;
+  __nv_bfloat16* wh = (__nv_bfloat16*)smem_raw;                  // [L-1][32 n][kPairWLd]: bf16(W[n][k])
+  __nv_bfloat16* wl = wh + L1 * 32 * kPairWLd;                    // bf16(W - bf16(W))
+  float* sc = (float*)(wl + L1 * 32 * kPairWLd);                  // [L-1][32] biases
+  float* gs = sc + L1 * 32;                                       // [16-padded N^2][33] activations
+  const int w = blockIdx.x, N = sh.N, NP = N * N, NPp = (NP + 15) & ~15;
+  for (int l = 0; l < L1; ++l) {
+    const float* W = (const float*)a.W[l];                        // [h2][d_g]
+    const int dg = a.d_g[l];
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+      const int n = e >> 5, k = e & 31;
+      const float v = (n < a.h2 && k < dg) ? W[n * dg + k] : 0.f;
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      wh[(l * 32 + n) * kPairWLd + k] = h;
+      wl[(l * 32 + n) * kPairWLd + k] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+    for (int c = threadIdx.x; c < 32; c += blockDim.x) sc[l * 32 + c] = c < a.h2 ? ((const float*)a.c[l])[c] : 0.f;
+  }
+  for (int e = threadIdx.x; e < NPp * 33; e += blockDim.x) gs[e] = 0.f;
+  __syncthreads();
+  const Wlk* rw = r + (int64_t)w * N * 3;
+  for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+    const int i = p / N, j = p - (p / N) * N;
+    if (j == i) continue;
+    const double d0 = (double)rw[3 * i] - (double)rw[3 * j], d1 = (double)rw[3 * i + 1] - (double)rw[3 * j + 1],
+                 d2 = (double)rw[3 * i + 2] - (double)rw[3 * j + 2];
+    float* gp = gs + p * 33;
+    gp[0] = (float)d0; gp[1] = (float)d1; gp[2] = (float)d2;
+    gp[3] = (float)sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane >> 2, tig = lane & 3;
+  for (int l = 0; l < a.L; ++l) {
+    const int dg = a.d_g[l];
+    __syncthreads();
+    __nv_bfloat16* X = (__nv_bfloat16*)a.X[l];
+    for (int e = threadIdx.x; e < N * 2 * dg; e += blockDim.x) {
+      const int ii = e / (2 * dg), s2 = (e / dg) % 2, c = e % dg;
+      const int lo = s2 ? sh.n_up : 0, hi = s2 ? N : sh.n_up;
+      float sum = 0.f;
+      for (int jj = lo; jj < hi; ++jj) sum += gs[(ii * N + jj) * 33 + c];
+      const float mean = hi > lo ? sum / (float)(hi - lo) : 0.f;
+      __nv_bfloat16* o = X + tile_row(w, ii, N, sh.wpt) * a.ldx[l] + a.col0[l] + s2 * dg + c;
+      st(o, mean);
+      st_lo(o + sh.T * sh.R * a.ldx[l], mean);
+    }
+    if (l == a.L - 1) break;
+    __syncthreads();
+    const int nks = (dg + 15) / 16;
+    const __nv_bfloat16* whl = wh + l * 32 * kPairWLd;
+    const __nv_bfloat16* wll = wl + l * 32 * kPairWLd;
+    for (int mt = warp; mt < NPp / 16; mt += (int)(blockDim.x >> 5)) {
+      const int p0 = mt * 16;
+      float c[4][4];
+#pragma unroll
+      for (int nb = 0; nb < 4; ++nb) {
+        const float b0 = sc[l * 32 + 8 * nb + 2 * tig], b1 = sc[l * 32 + 8 * nb + 2 * tig + 1];
+        c[nb][0] = b0; c[nb][1] = b1; c[nb][2] = b0; c[nb][3] = b1;
+      }
+      for (int ks = 0; ks < nks; ++ks) {
+        const int k0 = ks * 16;
+        const float* r0 = gs + (p0 + grp) * 33 + k0 + 2 * tig;
+        const float* r1 = gs + (p0 + grp + 8) * 33 + k0 + 2 * tig;
+        uint32_t ah[4], al[4];
+        split_pack(r0[0], r0[1], ah[0], al[0]);
+        split_pack(r1[0], r1[1], ah[1], al[1]);
+        split_pack(r0[8], r0[9], ah[2], al[2]);
+        split_pack(r1[8], r1[9], ah[3], al[3]);
+#pragma unroll
+        for (int nb = 0; nb < 4; ++nb) {
+          const int off = (8 * nb + grp) * kPairWLd + k0 + 2 * tig;
+          const uint32_t bh0 = *(const uint32_t*)(whl + off), bh1 = *(const uint32_t*)(whl + off + 8);
+          const uint32_t bl0 = *(const uint32_t*)(wll + off), bl1 = *(const uint32_t*)(wll + off + 8);
+          mma_16816(c[nb], ah, bh0, bh1);
+          mma_16816(c[nb], ah, bl0, bl1);
+          mma_16816(c[nb], al, bh0, bh1);
+        }
+      }
+      __syncwarp();                                              // every lane's A reads precede the writes
+#pragma unroll
+      for (int nb = 0; nb < 4; ++nb)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int row = p0 + grp + (q >= 2 ? 8 : 0), col = 8 * nb + 2 * tig + (q & 1);
+          float* gp = gs + row * 33 + col;
+          const float h = col < a.h2 ? tanh_fast(c[nb][q]) : 0.f;
+          *gp = (l > 0 ? *gp : 0.f) + h;
+        }
+    }
+    if (a.gstore[l + 1]) {
+      __syncthreads();
+      float* gsto = (float*)a.gstore[l + 1] + (int64_t)w * NP * a.h2;
+      for (int e = threadIdx.x; e < NP * a.h2; e += blockDim.x) gsto[e] = gs[(e / a.h2) * 33 + e % a.h2];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // one-electron layer: for every 128-row walker tile and 64 output columns, loop over
 // the tangent slabs: value first (h = tanh z), then every gradient slab
@@ -858,10 +981,17 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
       cudaFuncSetAttribute(k_pair_full<Act, Cmp, Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_pair_full<Act, Cmp, Wlk><<<(unsigned)blocks, 32 * warps, smem, st>>>(r, sh, pa, ib);
     } else {
-      const size_t smem = wbytes + sizeof(Cmp) * sh.N * sh.N * 33;
-      const int threads = (int)std::min<int64_t>(512, round_up((int64_t)sh.N * sh.N, 32));
-      cudaFuncSetAttribute(k_pair_value<Act, Cmp, Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_pair_value<Act, Cmp, Wlk><<<(unsigned)sh.B, threads, smem, st>>>(r, sh, pa);
+      if (Mode::kMode == FN_BF16_MIXED) {
+        const int L1 = L - 1, npp = (sh.N * sh.N + 15) & ~15;
+        const size_t smem = (size_t)L1 * (2 * 32 * kPairWLd * 2 + 32 * 4) + (size_t)npp * 33 * 4;
+        cudaFuncSetAttribute(k_pair_value_mma<Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_pair_value_mma<Wlk><<<(unsigned)sh.B, 128, smem, st>>>(r, sh, pa);
+      } else {
+        const size_t smem = wbytes + sizeof(Cmp) * sh.N * sh.N * 33;
+        const int threads = (int)std::min<int64_t>(512, round_up((int64_t)sh.N * sh.N, 32));
+        cudaFuncSetAttribute(k_pair_value<Act, Cmp, Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_pair_value<Act, Cmp, Wlk><<<(unsigned)sh.B, threads, smem, st>>>(r, sh, pa);
+      }
     }
   }
   for (int l = 0; l < L; ++l) {
