@@ -575,11 +575,11 @@ __global__ void __launch_bounds__(128) k_pair_value_mma(const Wlk* __restrict__ 
   for (int p = threadIdx.x; p < NP; p += blockDim.x) {
     const int i = p / N, j = p - (p / N) * N;
     if (j == i) continue;
-    const double d0 = (double)rw[3 * i] - (double)rw[3 * j], d1 = (double)rw[3 * i + 1] - (double)rw[3 * j + 1],
-                 d2 = (double)rw[3 * i + 2] - (double)rw[3 * j + 2];
+    const float d0 = (float)rw[3 * i] - (float)rw[3 * j], d1 = (float)rw[3 * i + 1] - (float)rw[3 * j + 1],
+                d2 = (float)rw[3 * i + 2] - (float)rw[3 * j + 2];
     float* gp = gs + p * 33;
-    gp[0] = (float)d0; gp[1] = (float)d1; gp[2] = (float)d2;
-    gp[3] = (float)sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    gp[0] = d0; gp[1] = d1; gp[2] = d2;
+    gp[3] = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, grp = lane >> 2, tig = lane & 3;
   for (int l = 0; l < a.L; ++l) {
@@ -864,9 +864,11 @@ __global__ void k_envelope_values(const Wlk* __restrict__ r, const double* __res
   const Wlk* rj = r + ((int64_t)w * sh.N + j) * 3;
   const float* pi = (const float*)a.pi[spin] + (int64_t)ko * sh.M;
   float env = 0.f;
+  // FP32 differences: the envelope values are FP32 in this mode, and FP64 arithmetic runs at
+  // a small fraction of the FP32 rate on this part
+  const float x = (float)rj[0], y = (float)rj[1], z = (float)rj[2];
   for (int m = 0; m < sh.M; ++m) {
-    const float d0 = (float)((double)rj[0] - nuc[3 * m]), d1 = (float)((double)rj[1] - nuc[3 * m + 1]),
-                d2 = (float)((double)rj[2] - nuc[3 * m + 2]);
+    const float d0 = x - (float)nuc[3 * m], d1 = y - (float)nuc[3 * m + 1], d2 = z - (float)nuc[3 * m + 2];
     float s2;
     if (!a.aniso) {
       const float sg = ((const float*)a.sig[spin])[(int64_t)ko * sh.M + m];
