@@ -13,6 +13,7 @@ The metric is walker local energies per second of whole-step time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -176,9 +177,17 @@ def _algorithmic(cls, B, N, a, T_full, act_bytes, launches=1):
         return fl / max(1, launches), "flop"
     if cls in ("layer_full", "layer_value"):
         T = T_full if cls == "layer_full" else 1
-        # per layer: X_l read, h_{l+1} written, mean-field term read; averaged over the L
-        # launches of one pass (the spin means of h_{l+1} are a separate pass)
-        per = [T * R * (k + h1) * act_bytes + T * B * h1 * 4 for k in k_self]
+        d_g = [4] + [h2] * (L - 1)
+        # per layer: X_l read, h_{l+1} written, mean-field term read; in BF16 storage also the
+        # low parts of the value slab (X_l read, h_{l+1} written) and of the pair-mean columns of
+        # the other slabs; averaged over the L launches of one pass (the spin means of h_{l+1}
+        # are a separate pass)
+        per = []
+        for k, dg in zip(k_self, d_g):
+            b = T * R * (k + h1) * act_bytes + T * B * h1 * 4
+            if act_bytes == 2:
+                b += R * (k + h1) * 2 + (T - 1) * R * 2 * dg * 2
+            per.append(b)
         return float(np.mean(per)), "bytes"
     if cls == "det_full":
         # per walker, determinant k, spin: 3N tangent items x 2 n^3 + Laplacian trace + LU/inverse
@@ -190,6 +199,25 @@ def _algorithmic(cls, B, N, a, T_full, act_bytes, launches=1):
     if cls == "orbitals_full":
         return float(2.0 * B * N * T_full * h1 * K * n), "flop"
     return None, None
+
+
+def _measured_traffic(cls):
+    """DRAM bytes per launch of the layer kernel from the committed ncu capture, valid only while
+    the kernel source is the one that was profiled (else None)."""
+    if cls != "layer_full":
+        return None
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "profiles", "layer_full_traffic.txt")
+    src = os.path.join(here, "paper_2401_10287_gb300", "csrc", "fn_layer_tc.cu")
+    try:
+        kv = dict(line.split()[:2] for line in open(path) if line.strip() and not line.startswith("#"))
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if kv.get("source_sha256") != sha:
+            return None
+        return float(kv["dram_bytes_per_launch_4096"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def run_mine(args):
@@ -301,7 +329,8 @@ def run_mine(args):
             achieved = work / avg_s / 1e9
             pk = peaks["hbm_gbs"]
             roof = {"kernel": cls, "bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
-                    "frac": achieved / pk, "traffic": args.traffic, "algorithmic_bytes_per_launch": work,
+                    "frac": achieved / pk, "traffic": args.traffic if args.traffic is not None else _measured_traffic(cls),
+                    "algorithmic_bytes_per_launch": work,
                     "peak_source": f"{peak_src} HBM copy bandwidth"}
         elif kind == "flop64":
             achieved = work / avg_s / 1e12
