@@ -647,6 +647,157 @@ __global__ void __launch_bounds__(128) k_pair_value_mma(const Wlk* __restrict__ 
   }
 }
 
+// Full (E_L) pass of the two-electron stream in BF16 mode.  The 5-row pair jets of one CTA
+// (walker w, electrons i0 .. i0 + ib - 1, all partners j) are the rows of one matrix; every
+// pair layer is (1) its product with the layer weights on warp-level BF16 MMAs (hi/lo
+// splits of activations and weights, three products) into a shared-memory buffer, (2) the
+// tanh forward-Laplacian rule, one thread per (pair, channel), and (3) the coalesced write
+// of the spin means and d/dr_j slabs to the next layer input, as in k_pair_full.
+template <typename Wlk>
+__global__ void __launch_bounds__(256) k_pair_full_mma(const Wlk* __restrict__ r, Shape sh, PairArgs a, int ib) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int L1 = a.L - 1;
+  __nv_bfloat16* wh = (__nv_bfloat16*)smem_raw;                  // [L-1][32 n][kPairWLd]: bf16(W[n][k])
+  __nv_bfloat16* wl = wh + L1 * 32 * kPairWLd;                    // bf16(W - bf16(W))
+  float* sc = (float*)(wl + L1 * 32 * kPairWLd);                  // [L-1][32] biases
+  const int rows_p = (ib * sh.N * 5 + 15) & ~15;
+  float* gs = sc + L1 * 32;                                       // [rows_p][33]: pair p, row srow at p * 5 + srow
+  float* zs = gs + rows_p * 33;                                   // [rows_p][33]: products of the current layer
+  const int blocks_per_walker = (sh.N + ib - 1) / ib;
+  const int w = blockIdx.x / blocks_per_walker, i0 = (blockIdx.x % blocks_per_walker) * ib;
+  const int n_i = min(ib, sh.N - i0);
+  const int npair = n_i * sh.N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+  const int grp = lane >> 2, tig = lane & 3;
+  for (int l = 0; l < L1; ++l) {
+    const float* W = (const float*)a.W[l];
+    const int dg = a.d_g[l];
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+      const int n = e >> 5, k = e & 31;
+      const float v = (n < a.h2 && k < dg) ? W[n * dg + k] : 0.f;
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      wh[(l * 32 + n) * kPairWLd + k] = h;
+      wl[(l * 32 + n) * kPairWLd + k] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+    for (int c = threadIdx.x; c < 32; c += blockDim.x) sc[l * 32 + c] = c < a.h2 ? ((const float*)a.c[l])[c] : 0.f;
+  }
+  for (int e = threadIdx.x; e < rows_p * 33; e += blockDim.x) gs[e] = 0.f;
+  __syncthreads();
+  // layer-0 jets of the pair features [r_i - r_j, |r_i - r_j|]: value, Laplacian over both
+  // electrons, d/dr_i along x, y, z
+  const Wlk* rw = r + (int64_t)w * sh.N * 3;
+  for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+    const int i = i0 + p / sh.N, j = p % sh.N;
+    if (j == i) continue;
+    const float d[3] = {(float)rw[3 * i] - (float)rw[3 * j], (float)rw[3 * i + 1] - (float)rw[3 * j + 1],
+                        (float)rw[3 * i + 2] - (float)rw[3 * j + 2]};
+    const float dist = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    float* g0 = gs + p * 5 * 33;
+    g0[0] = d[0]; g0[1] = d[1]; g0[2] = d[2]; g0[3] = dist;
+    g0[33 + 3] = 4.f / dist;
+    for (int c = 0; c < 3; ++c) {
+      g0[(2 + c) * 33 + c] = 1.f;
+      g0[(2 + c) * 33 + 3] = d[c] / dist;
+    }
+  }
+  for (int l = 0; l < a.L; ++l) {
+    const int dg = a.d_g[l];
+    __nv_bfloat16* X = (__nv_bfloat16*)a.X[l];
+    const int64_t slab = sh.R * a.ldx[l];
+    __syncthreads();
+    // (3) layer-l input: spin means and d/dr_j slabs, adjacent column pairs per lane
+    const int64_t ldx = a.ldx[l];
+    __nv_bfloat16* Xc = X + a.col0[l];
+    const int col = 2 * lane, half0 = col < dg ? 0 : 1, half1 = col + 1 < dg ? 0 : 1;
+    const int c0 = col - half0 * dg, c1 = col + 1 - half1 * dg;
+    for (int pp = warp; pp < npair; pp += n_warps) {
+      const int e_i = pp / sh.N, jj = pp - e_i * sh.N;
+      if (jj == i0 + e_i || lane >= dg) continue;
+      const int sjj = jj < sh.n_up ? 0 : 1;
+      const float scale = -1.f / (float)(sjj ? sh.n_dn : sh.n_up);
+      const int64_t row = tile_row(w, i0 + e_i, sh.N, sh.wpt) * ldx;
+#pragma unroll
+      for (int axis = 0; axis < 3; ++axis) {
+        const float* src = gs + (pp * 5 + 2 + axis) * 33;
+        const float v0 = half0 == sjj ? src[c0] * scale : 0.f, v1 = half1 == sjj ? src[c1] * scale : 0.f;
+        st2(Xc + (1 + 3 * jj + axis) * slab + row + col, v0, v1);
+        st2_lo(Xc + (sh.T + 1 + 3 * jj + axis) * slab + row + col, v0, v1);
+      }
+    }
+    for (int rr = warp; rr < n_i * 5; rr += n_warps) {
+      if (lane >= dg) continue;
+      const int e_i = rr / 5, qq = rr - 5 * e_i, ie = i0 + e_i;
+      const float* src = gs + (e_i * sh.N * 5 + qq) * 33;
+      float up0 = 0.f, up1 = 0.f, dn0 = 0.f, dn1 = 0.f;
+      for (int jj = 0; jj < sh.n_up; ++jj) { up0 += src[jj * 165 + c0]; up1 += src[jj * 165 + c1]; }
+      for (int jj = sh.n_up; jj < sh.N; ++jj) { dn0 += src[jj * 165 + c0]; dn1 += src[jj * 165 + c1]; }
+      const float iu = sh.n_up ? 1.f / (float)sh.n_up : 0.f, id = sh.n_dn ? 1.f / (float)sh.n_dn : 0.f;
+      const int t = qq == 0 ? 0 : (qq == 1 ? sh.T - 1 : 1 + 3 * ie + (qq - 2));
+      const float m0 = half0 ? dn0 * id : up0 * iu, m1 = half1 ? dn1 * id : up1 * iu;
+      const int64_t o = tile_row(w, ie, sh.N, sh.wpt) * ldx + col;
+      st2(Xc + t * slab + o, m0, m1);
+      st2_lo(Xc + (sh.T + t) * slab + o, m0, m1);
+    }
+    if (l == a.L - 1) break;
+    // (1) products of every jet row with the layer weights (no bias) into zs
+    const int nks = (dg + 15) / 16;
+    const __nv_bfloat16* whl = wh + l * 32 * kPairWLd;
+    const __nv_bfloat16* wll = wl + l * 32 * kPairWLd;
+    for (int mt = warp; mt < rows_p / 16; mt += n_warps) {
+      const int p0 = mt * 16;
+      float c[4][4];
+#pragma unroll
+      for (int nb = 0; nb < 4; ++nb) c[nb][0] = c[nb][1] = c[nb][2] = c[nb][3] = 0.f;
+      for (int ks = 0; ks < nks; ++ks) {
+        const int k0 = ks * 16;
+        const float* r0 = gs + (p0 + grp) * 33 + k0 + 2 * tig;
+        const float* r1 = gs + (p0 + grp + 8) * 33 + k0 + 2 * tig;
+        uint32_t ah[4], al[4];
+        split_pack(r0[0], r0[1], ah[0], al[0]);
+        split_pack(r1[0], r1[1], ah[1], al[1]);
+        split_pack(r0[8], r0[9], ah[2], al[2]);
+        split_pack(r1[8], r1[9], ah[3], al[3]);
+#pragma unroll
+        for (int nb = 0; nb < 4; ++nb) {
+          const int off = (8 * nb + grp) * kPairWLd + k0 + 2 * tig;
+          const uint32_t bh0 = *(const uint32_t*)(whl + off), bh1 = *(const uint32_t*)(whl + off + 8);
+          const uint32_t bl0 = *(const uint32_t*)(wll + off), bl1 = *(const uint32_t*)(wll + off + 8);
+          mma_16816(c[nb], ah, bh0, bh1);
+          mma_16816(c[nb], ah, bl0, bl1);
+          mma_16816(c[nb], al, bh0, bh1);
+        }
+      }
+#pragma unroll
+      for (int nb = 0; nb < 4; ++nb)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          zs[(p0 + grp + (q >= 2 ? 8 : 0)) * 33 + 8 * nb + 2 * tig + (q & 1)] = c[nb][q];
+    }
+    __syncthreads();
+    // (2) tanh forward-Laplacian rule per (pair, channel); the 6 tangent rows of a pair
+    // (d/dr_j = -d/dr_i) give 2 (z_x^2 + z_y^2 + z_z^2)
+    for (int e = threadIdx.x; e < npair * 32; e += blockDim.x) {
+      const int pp = e >> 5, ch = e & 31;
+      const float* zr = zs + pp * 5 * 33 + ch;
+      float* gr = gs + pp * 5 * 33 + ch;
+      float ov = 0.f, ol = 0.f, ox = 0.f, oy = 0.f, oz = 0.f;
+      if (ch < a.h2) {
+        const float zv = zr[0] + sc[l * 32 + ch], zl = zr[33], zx = zr[66], zy = zr[99], zz = zr[132];
+        const float h = tanh_fast(zv), dh = 1.f - h * h;
+        ov = h;
+        ox = dh * zx; oy = dh * zy; oz = dh * zz;
+        ol = dh * zl - 4.f * h * dh * (zx * zx + zy * zy + zz * zz);
+      }
+      const bool res = l > 0;
+      gr[0] = (res ? gr[0] : 0.f) + ov;
+      gr[33] = (res ? gr[33] : 0.f) + ol;
+      gr[66] = (res ? gr[66] : 0.f) + ox;
+      gr[99] = (res ? gr[99] : 0.f) + oy;
+      gr[132] = (res ? gr[132] : 0.f) + oz;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // one-electron layer: for every 128-row walker tile and 64 output columns, loop over
 // the tangent slabs: value first (h = tanh z), then every gradient slab
@@ -848,33 +999,37 @@ __global__ void k_orbital_fixup(const Wlk* __restrict__ r, const double* __restr
 template <typename Wlk>
 __global__ void k_envelope_values(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh, OrbArgs a,
                                   float* __restrict__ envv) {
-  // one thread per (walker, electron j, orbital of j's spin); K n_s orbitals per electron
-  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // one thread per (walker, electron j, orbital of j's spin); K n_s orbitals per electron.
+  // Nuclei as FP32 in shared memory: the envelope values are FP32 in this mode, and FP64
+  // arithmetic (conversions included) runs at a small fraction of the FP32 rate on this part.
+  __shared__ float nucf[3 * kMaxNuclei];
+  for (int q = threadIdx.x; q < 3 * sh.M; q += blockDim.x) nucf[q] = (float)nuc[q];
+  __syncthreads();
   const int per_walker = a.K * (sh.n_up * sh.n_up + sh.n_dn * sh.n_dn);
-  if (gid >= (int64_t)sh.B * per_walker) return;
-  const int w = (int)(gid / per_walker);
-  int rem = (int)(gid % per_walker);
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;       // the host checks B * per_walker < 2^31
+  if (gid >= sh.B * per_walker) return;
+  const int w = gid / per_walker;
+  int rem = gid - w * per_walker;
   const int up_block = a.K * sh.n_up * sh.n_up;
   const int spin = rem < up_block ? 0 : 1;
   if (spin) rem -= up_block;
   const int n_s = spin ? sh.n_dn : sh.n_up;
-  const int j = (spin ? sh.n_up : 0) + rem / (a.K * n_s);
-  const int ko = rem % (a.K * n_s);
+  const int jj = rem / (a.K * n_s);
+  const int j = (spin ? sh.n_up : 0) + jj;
+  const int ko = rem - jj * (a.K * n_s);
   const int64_t row = tile_row(w, j, sh.N, sh.wpt);
   const Wlk* rj = r + ((int64_t)w * sh.N + j) * 3;
-  const float* pi = (const float*)a.pi[spin] + (int64_t)ko * sh.M;
-  float env = 0.f;
-  // FP32 differences: the envelope values are FP32 in this mode, and FP64 arithmetic runs at
-  // a small fraction of the FP32 rate on this part
+  const float* pi = (const float*)(spin ? a.pi[1] : a.pi[0]) + ko * sh.M;
+  const float* sg = (const float*)(spin ? a.sig[1] : a.sig[0]);
   const float x = (float)rj[0], y = (float)rj[1], z = (float)rj[2];
+  float env = 0.f;
   for (int m = 0; m < sh.M; ++m) {
-    const float d0 = x - (float)nuc[3 * m], d1 = y - (float)nuc[3 * m + 1], d2 = z - (float)nuc[3 * m + 2];
+    const float d0 = x - nucf[3 * m], d1 = y - nucf[3 * m + 1], d2 = z - nucf[3 * m + 2];
     float s2;
     if (!a.aniso) {
-      const float sg = ((const float*)a.sig[spin])[(int64_t)ko * sh.M + m];
-      s2 = sg * sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+      s2 = sg[ko * sh.M + m] * sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
     } else {
-      const float* S = (const float*)a.sig[spin] + ((int64_t)ko * sh.M + m) * 9;
+      const float* S = sg + (ko * sh.M + m) * 9;
       const float u0 = S[0] * d0 + S[1] * d1 + S[2] * d2;
       const float u1 = S[3] * d0 + S[4] * d1 + S[5] * d2;
       const float u2 = S[6] * d0 + S[7] * d1 + S[8] * d2;
@@ -978,10 +1133,20 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
         if (warps <= best) { best = warps; ib = c; }
       }
       const int warps = (ib * sh.N + per_warp - 1) / per_warp;
+      if (Mode::kMode == FN_BF16_MIXED) {
+        // electrons per CTA: at most 256 jet rows (5 per pair)
+        const int ibm = std::max(1, std::min(sh.N, 256 / (5 * sh.N)));
+        const int rows_p = (ibm * sh.N * 5 + 15) & ~15;
+        const size_t smem_m = (size_t)(L - 1) * (2 * 32 * kPairWLd * 2 + 32 * 4) + (size_t)2 * rows_p * 33 * 4;
+        const int64_t blocks_m = (int64_t)sh.B * ((sh.N + ibm - 1) / ibm);
+        cudaFuncSetAttribute(k_pair_full_mma<Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
+        k_pair_full_mma<Wlk><<<(unsigned)blocks_m, 256, smem_m, st>>>(r, sh, pa, ibm);
+      } else {
       const size_t smem = wbytes + sizeof(Cmp) * ib * sh.N * 5 * 33;
       const int64_t blocks = (int64_t)sh.B * ((sh.N + ib - 1) / ib);
       cudaFuncSetAttribute(k_pair_full<Act, Cmp, Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_pair_full<Act, Cmp, Wlk><<<(unsigned)blocks, 32 * warps, smem, st>>>(r, sh, pa, ib);
+      }
     } else {
       if (Mode::kMode == FN_BF16_MIXED) {
         const int L1 = L - 1, npp = (sh.N * sh.N + 15) & ~15;
@@ -1065,6 +1230,10 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
       {
       ProfScope ps(s->prof, full ? kProfOrbFull : kProfOrbValue, st);
       const int64_t n_env = (int64_t)sh.B * s->cfg.n_dets * (s->n_up * s->n_up + s->n_dn * s->n_dn);
+      if (n_env >= ((int64_t)1 << 31)) {
+        const_cast<fn_system*>(s)->host_error = FN_ERR_UNSUPPORTED;
+        return;
+      }
       k_envelope_values<Wlk><<<(unsigned)((n_env + 255) / 256), 256, 0, st>>>(r, s->d_nuclei, sh, oa, ws.envv);
       const float* wb[2] = {(const float*)oa.g[0], (const float*)oa.g[1]};
       const float* pis[2] = {(const float*)oa.pi[0], (const float*)oa.pi[1]};
