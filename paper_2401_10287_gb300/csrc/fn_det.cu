@@ -39,6 +39,21 @@ struct DetArgs {
 // neighbouring words).  Partial pivoting picks the first maximal |pivot|; the
 // determinant is tracked as mantissa * 2^exponent so that a single log per matrix is
 // needed; the pivot reciprocals are kept for the inverse.
+// Widening of a stored orbital entry to the determinant type.  FP32 -> FP64 goes through
+// integer bit operations (sign, exponent re-biased by 1023 - 127, mantissa shifted into the
+// top of the 52-bit field): exact for every normal FP32 value, FP32 subnormals become signed
+// zero, infinities and NaNs keep their class.  It keeps the conversions off the FP64 pipe,
+// which sets the pace of this stage.
+template <typename Det, typename PhiT> __device__ __forceinline__ Det widen(PhiT v) { return (Det)v; }
+template <> __device__ __forceinline__ double widen<double, float>(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ex = (u >> 23) & 0xFFu, sign = u & 0x80000000u, man = u & 0x7FFFFFu;
+  const uint32_t ex64 = ex == 0 ? 0u : (ex == 0xFFu ? 0x7FFu : ex + 896u);
+  const uint32_t hi = sign | (ex64 << 20) | (ex == 0 ? 0u : (man >> 3));
+  const uint32_t lo = ex == 0 ? 0u : (man << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 template <typename Det>
 __device__ void thread_lu(Det* A, int n, int ST, int* perm, Det* rcp, Det* ld_out, Det* sign_out) {
   Det sgn = 1, mant = 1;
@@ -115,7 +130,7 @@ __device__ __forceinline__ void tangent_item_fixed(const Det* __restrict__ Cm, i
 #pragma unroll
   for (int m = 0; m < NN; ++m)
 #pragma unroll
-    for (int j = 0; j < NN; ++j) d[m][j] = (Det)D[m * NN + j];
+    for (int j = 0; j < NN; ++j) d[m][j] = widen<Det, PhiT>(D[m * NN + j]);
 #pragma unroll
   for (int i = 0; i < NN; ++i) {
 #pragma unroll
@@ -147,13 +162,13 @@ __device__ void tangent_item_any(const Det* __restrict__ Cm, int ST, const PhiT*
   for (int i = 0; i < n; ++i) {
     for (int j = i; j < n; ++j) {
       Det bij = 0;
-      for (int m = 0; m < n; ++m) bij += Cm[(int64_t)(i * n + m) * ST] * (Det)D[m * n + j];
+      for (int m = 0; m < n; ++m) bij += Cm[(int64_t)(i * n + m) * ST] * widen<Det, PhiT>(D[m * n + j]);
       if (j == i) {
         g += bij;
         q += bij * bij;
       } else {
         Det bji = 0;
-        for (int m = 0; m < n; ++m) bji += Cm[(int64_t)(j * n + m) * ST] * (Det)D[m * n + i];
+        for (int m = 0; m < n; ++m) bji += Cm[(int64_t)(j * n + m) * ST] * widen<Det, PhiT>(D[m * n + i]);
         q += (Det)2 * bij * bji;
       }
     }
@@ -210,7 +225,7 @@ __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, c
     const int nn = ns[sp] * ns[sp];
     for (int e = tid; e < K * nn; e += blockDim.x) {
       const int k = e / nn, idx = e % nn;
-      A[(int64_t)idx * ST + 2 * k + sp] = (Det)Phi[blk_off[sp] + (int64_t)k * T * nn + idx];
+      A[(int64_t)idx * ST + 2 * k + sp] = widen<Det, PhiT>(Phi[blk_off[sp] + (int64_t)k * T * nn + idx]);
     }
   }
   __syncthreads();
@@ -246,7 +261,7 @@ __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, c
     } else {
       Det l = 0;
       for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) l += Cm[(int64_t)(j * n + i) * ST] * (Det)D[i * n + j];
+        for (int j = 0; j < n; ++j) l += Cm[(int64_t)(j * n + i) * ST] * widen<Det, PhiT>(D[i * n + j]);
       lt[p] = l;
     }
   }
@@ -346,7 +361,7 @@ __global__ void k_det_value(Shape sh, DetArgs a) {
     const int n = ns[sp];
     const int64_t q = e - blk_off[sp];
     const int k = (int)(q / (n * n)), idx = (int)(q % (n * n));
-    A[(int64_t)idx * ST + 2 * k + sp] = (Det)Phi[e];
+    A[(int64_t)idx * ST + 2 * k + sp] = widen<Det, PhiT>(Phi[e]);
   }
   __syncthreads();
   if (tid < NM) {
