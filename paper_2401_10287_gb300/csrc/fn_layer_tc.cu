@@ -4,7 +4,7 @@
 // Per CTA: 128 electron rows (one walker-aligned tile) x N_t output columns, looping
 // over every tangent slab t (value, 3N gradient slabs, Laplacian):
 //   warp 0      TMA producer: X_l[t] tile (128 x 64 bf16) and the V_self tiles (N_t x 64,
-//               high and low BF16 parts) per k-block into a kStages-deep shared-memory
+//               high and low BF16 parts) per k-block into a 3-stage shared-memory
 //               ring (128B swizzle);
 //   warp 1      allocates tensor memory; one lane issues tcgen05.mma (M=128, N=N_t, K=16)
 //               into a double-buffered accumulator and commits to mbarriers;
@@ -30,7 +30,7 @@
 namespace fn {
 namespace tc {
 
-constexpr int kStages = 4;
+constexpr int kStages = 4;                      // TMA ring depth (the layer kernel uses 3, see stages_for)
 constexpr int kMaxNucleiTc = 16;
 constexpr int kBlockK = 64;                     // bf16 elements per 128-byte swizzled row
 constexpr int kEpiWarps = 8;                   // two warps per TMEM lane quarter
@@ -208,6 +208,11 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 
 enum { kEpiLayer = 0, kEpiPlain = 1, kEpiOrbital = 2 };
 
+// Ring depth per kernel: the layer kernel gives one stage's worth of shared memory to the
+// double-buffered residual tiles.
+__host__ __device__ constexpr int stages_for(int epi) { return epi == kEpiLayer ? 3 : kStages; }
+constexpr uint32_t kResBox = 128 * 128;          // one residual box: 128 rows x 64 bf16 (128B swizzle)
+
 struct TcArgs {
   Shape sh;
   int tiles;             // row tiles of 128; CTA y index strides over them (persistent)
@@ -255,7 +260,7 @@ struct TcArgs {
 // means of the output, the next layer's mean-field input, are taken by a separate pass.
 template <bool FULL>
 __device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, bool has_chunk, int r, uint32_t tmem,
-                                          uint32_t lane_base, int buf, int n0, int tile, const uint4 (&res)[4],
+                                          uint32_t lane_base, int buf, int n0, int tile, const unsigned char* rs,
                                           const float* mrow) {
   const Shape& sh = a.sh;
   const int nt = a.nt, T = sh.T;
@@ -316,7 +321,10 @@ __device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, bool h
         if (a.residual) {
 #pragma unroll
           for (int v = 0; v < 2; ++v) {
-            const uint4 u = res[2 * hh + v];
+            // residual tile in shared memory (TMA, 128B swizzle): 16-byte chunk j of row r sits at
+            // chunk j ^ (r % 8) of the row's 128 bytes
+            const int cl = cc * 32 + hh * 16 + 8 * v;
+            const uint4 u = *(const uint4*)(rs + (cl >> 6) * kResBox + r * 128 + ((((cl & 63) >> 3) ^ (r & 7)) << 4));
             const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -516,17 +524,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nt = a.nt;
   const int nbparts = a.bsplit ? 2 : 1;                       // B_hi (and B_lo) per stage
   const uint32_t bytesA = 128 * 128, bytesB = (uint32_t)nt * 128;
-  unsigned char* sA = base;                                   // kStages x 16 KB
-  unsigned char* sB = sA + kStages * bytesA;                  // kStages x nbparts x nt*128
-  float* mts = (float*)(sB + kStages * nbparts * bytesB);     // [2][wpt][nt + 4] M[t] staging (layer)
+  constexpr int NS = stages_for(EPI);
+  const bool rstage = EPI == kEpiLayer && a.residual;         // residual tiles staged by TMA
+  const int nbox = (nt + 63) / 64;
+  unsigned char* sA = base;                                   // NS x 16 KB
+  unsigned char* sB = sA + NS * bytesA;                       // NS x nbparts x nt*128
+  unsigned char* sR = sB + NS * nbparts * bytesB;             // [2][nbox] residual boxes (layer)
+  float* mts = (float*)(sR + (rstage ? 2 * nbox * kResBox : 0));   // [2][wpt][nt + 4] M[t] staging (layer)
   const size_t mt_floats = (EPI == kEpiLayer && a.mt_stage) ? (size_t)2 * a.sh.wpt * (nt + 4) : 0;
   uint64_t* bars = (uint64_t*)(mts + mt_floats);
   uint64_t* full = bars;
-  uint64_t* empty = bars + kStages;
-  uint64_t* accf = bars + 2 * kStages;
+  uint64_t* empty = bars + NS;
+  uint64_t* accf = bars + 2 * NS;
   uint64_t* acce = accf + 2;
   uint64_t* mma_done = acce + 2;
-  uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
+  uint64_t* resf = mma_done + 1;
+  uint64_t* rese = resf + 2;
+  uint32_t* tmem_slot = (uint32_t*)(rese + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -546,8 +560,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nkb = a.nkb;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
-    for (int b = 0; b < 2; ++b) { mbar_init(accf + b, 1); mbar_init(acce + b, kEpiWarps); }
+    for (int s = 0; s < NS; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf + b, 1); mbar_init(acce + b, kEpiWarps);
+      mbar_init(resf + b, 1); mbar_init(rese + b, kEpiWarps);
+    }
     mbar_init(mma_done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -566,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
+      int issued = 0, res_issued = 0;
       bool ok = true;
       for (int item = 0; item < my_tiles * T && ok; ++item) {
         const int pidx = (int)blockIdx.y + (item / T) * (int)gridDim.y, t = item % T;
@@ -576,12 +593,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nk = kb1 - kb0, lf = lo_first<EPI>(a, t, kb0, kb1);
         const int n_k = nk + (kb1 - lf);
         const int lo_row = (int)(a.alo_row + (int64_t)t * sh.R + (int64_t)tile * 128);
+        if (rstage) {
+          // this item's residual tile (the layer input's first h1 columns of these rows)
+          const int rb = item & 1;
+          if (*abort_flag || !mbar_wait(rese + rb, ((uint32_t)(item >> 1) & 1u) ^ 1u, deadline)) { ok = false; break; }
+          mbar_expect_tx(resf + rb, (uint32_t)nbox * kResBox);
+          for (int bx = 0; bx < nbox; ++bx)
+            tma_load_2d(sR + (rb * nbox + bx) * kResBox, &tmA, resf + rb, ctile * nt + bx * 64, arow);
+          ++res_issued;
+        }
         for (int kk = 0; kk < n_k; ++kk, ++issued) {
           const bool lo = kk >= nk;
           const int kb = lo ? lf + (kk - nk) : kb0 + kk;
           const int parts = lo ? 1 : nbparts;
-          const int stage = issued % kStages;
-          const uint32_t round = (uint32_t)(issued / kStages);
+          const int stage = issued % NS;
+          const uint32_t round = (uint32_t)(issued / NS);
           if (*abort_flag || !mbar_wait(empty + stage, (round & 1u) ^ 1u, deadline)) { ok = false; break; }
           mbar_expect_tx(full + stage, bytesA + parts * bytesB);
           tma_load_2d(sA + stage * bytesA, &tmA, full + stage, kb * kBlockK, lo ? lo_row : arow);
@@ -595,8 +621,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         atomicOr(a.status, kStatusTimeout);
       }
       const uint64_t dl2 = globaltimer() + kWaitNs;
-      for (int q = issued > kStages ? issued - kStages : 0; q < issued; ++q)
-        mbar_wait(full + (q % kStages), (uint32_t)((q / kStages) & 1), dl2);
+      for (int q = issued > NS ? issued - NS : 0; q < issued; ++q)
+        mbar_wait(full + (q % NS), (uint32_t)((q / NS) & 1), dl2);
+      for (int q = res_issued > 2 ? res_issued - 2 : 0; q < res_issued; ++q)
+        mbar_wait(resf + (q & 1), (uint32_t)((q >> 1) & 1), dl2);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -617,8 +645,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int n_k = nk + (kb1 - lo_first<EPI>(a, t, kb0, kb1));
         for (int kk = 0; kk < n_k; ++kk, ++consumed) {
           const int parts = kk >= nk ? 1 : nbparts;
-          const int stage = consumed % kStages;
-          const uint32_t round = (uint32_t)(consumed / kStages);
+          const int stage = consumed % NS;
+          const uint32_t round = (uint32_t)(consumed / NS);
           if (*abort_flag || !mbar_wait(full + stage, round & 1u, deadline)) { ok = false; break; }
           fence_after();
           const uint64_t da = sdesc(smem_u32(sA + stage * bytesA));
@@ -648,7 +676,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const int nchunks = nt / 32;
     const int n_items = my_tiles * T;
-    const int64_t xslab = sh.R * a.ldx;
     if (EPI == kEpiLayer && a.mt_stage && n_items > 0) stage_mterm(a, 0, (int)blockIdx.y, ctile * nt, mts, ethread);
     for (int item = 0; item < n_items; ++item) {
       const int t = item % T;
@@ -656,24 +683,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       item_range<EPI>(a, (int)blockIdx.y + (item / T) * (int)gridDim.y, a.nkb, tile, kb0_, kb1_);
       const int buf = item & 1;
       const uint32_t use = (uint32_t)(item >> 1);
-      // residual of this slab, both chunks, loaded before the accumulator is ready
-      uint4 res[2][4];
-      if (EPI == kEpiLayer && a.residual) {
-        const int wl = r / sh.N;
-        const bool valid = wl < sh.wpt && tile * sh.wpt + wl < sh.B;
-#pragma unroll
-        for (int it = 0; it < 2; ++it) {
-          const int cc = 2 * it + ehalf;
-          if (valid && cc < nchunks) {
-            const uint4* xr =
-                (const uint4*)(a.X + t * xslab + ((int64_t)tile * 128 + r) * a.ldx + ctile * nt + cc * 32);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) res[it][v] = xr[v];
-          }
-        }
-      }
       if (EPI == kEpiLayer && a.mt_stage) cp_async_wait_all();
-      const bool ok = !*abort_flag && mbar_wait(accf + buf, use & 1u, deadline);
+      bool ok = !*abort_flag && mbar_wait(accf + buf, use & 1u, deadline);
+      if (rstage) ok = ok && mbar_wait(resf + buf, use & 1u, deadline);
       // (the barrier also publishes every thread's staged M[t] copies)
       if (epilogue_any(!ok)) {
         if (ethread == 0) {
@@ -704,7 +716,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int cc = 2 * it + ehalf;
         const bool has = cc < nchunks;
         if (EPI == kEpiLayer) {
-          epi_layer<FULL>(a, t, has ? cc : 0, has, r, tmem, lane_base, buf, ctile * nt, tile, res[it], mrow);
+          epi_layer<FULL>(a, t, has ? cc : 0, has, r, tmem, lane_base, buf, ctile * nt, tile,
+                          sR + buf * nbox * kResBox, mrow);
         } else if (has) {
           if (EPI == kEpiPlain) epi_plain(a, cc, r, tmem, lane_base, buf, ctile * nt, tile);
           else epi_orbital<FULL>(a, t, cc, r, tmem, lane_base, buf, spin, ko0, tile);
@@ -712,7 +725,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acce + buf);
+      if (lane == 0) {
+        mbar_arrive(acce + buf);
+        if (rstage) mbar_arrive(rese + buf);
+      }
     }
   }
   if (EPI == kEpiLayer) cp_async_wait_all();
@@ -772,10 +788,11 @@ static uint32_t pow2_cols(int c) {
 
 // Dynamic shared memory of a launch: alignment slack, the A/B ring, the layer epilogue's
 // M[t] staging (mt_rows walkers, double-buffered), barriers.
-static size_t tc_smem_bytes(int nt, int epi, bool split, int mt_rows = 0) {
-  (void)epi;
+static size_t tc_smem_bytes(int nt, int epi, bool split, int mt_rows = 0, bool res = false) {
+  const int ns = tc::stages_for(epi);
   const size_t mt = (size_t)2 * mt_rows * (nt + 4) * 4;
-  return 1024 + tc::kStages * (128 * 128 + (size_t)nt * 128 * (split ? 2 : 1)) + mt + 8 * (2 * tc::kStages + 5) + 16;
+  const size_t rs = res ? (size_t)2 * ((nt + 63) / 64) * tc::kResBox : 0;
+  return 1024 + ns * (128 * 128 + (size_t)nt * 128 * (split ? 2 : 1)) + rs + mt + 8 * (2 * ns + 9) + 16;
 }
 constexpr size_t kMaxDynamicSmem = 227 * 1024;
 
@@ -799,7 +816,8 @@ static dim3 persistent_grid(int ctiles, int tiles) {
 template <int EPI>
 static void launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const tc::TcArgs& a, dim3 grid, bool full,
                       cudaStream_t st) {
-  const size_t smem = tc_smem_bytes(a.nt, EPI, a.bsplit != 0, (EPI == tc::kEpiLayer && a.mt_stage) ? a.sh.wpt : 0);
+  const size_t smem = tc_smem_bytes(a.nt, EPI, a.bsplit != 0, (EPI == tc::kEpiLayer && a.mt_stage) ? a.sh.wpt : 0,
+                                   EPI == tc::kEpiLayer && a.residual);
   if (full) {
     cudaFuncSetAttribute(tc::k_tc<EPI, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     tc::k_tc<EPI, true><<<grid, tc::kThreads, smem, st>>>(ta, tb, a);
@@ -835,7 +853,7 @@ bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, int lo
   a.alo_row = (int64_t)sh.T * sh.R;
   a.kb_lo_t = lo_col0 / tc::kBlockK;
   // stage M[t] in shared memory when the tile's walkers fit beside the ring
-  a.mt_stage = tc_smem_bytes(nt, tc::kEpiLayer, true, sh.wpt) <= kMaxDynamicSmem ? 1 : 0;
+  a.mt_stage = tc_smem_bytes(nt, tc::kEpiLayer, true, sh.wpt, residual != 0) <= kMaxDynamicSmem ? 1 : 0;
   const bool full = sh.T > 1;
   a.tmem_cols = pow2_cols(full ? 4 * nt : 2 * nt);
   a.tiles = sh.tiles;
