@@ -281,24 +281,44 @@ __global__ void __launch_bounds__(128) k_pair_bwd(const Wlk* __restrict__ r, Sha
   for (int q = 0; q < 32; ++q) accW[q] = 0;
   Cmp accc = 0;
   const Wlk* rw = r + (int64_t)w * N * 3;
-  for (int p = warp; p < N * N; p += 4) {
-    const int i = p / N, j = p - (p / N) * N;
+  // The loads of a warp's next pair are issued before the current pair's products, so
+  // their latency overlaps the 32 x 32 accumulation.
+  struct PairIn { Cmp gin, dgn, gout, dxv; };
+  auto load = [&](int p) {
+    PairIn v{(Cmp)0, (Cmp)0, (Cmp)0, (Cmp)0};
+    if (p >= N * N) return v;
+    const int i = p / N, j = p - i * N;
     const int64_t pidx = ((int64_t)w * N + i) * N + j;
-    // input g^l of this lane's channel
-    Cmp gin = 0;
     if (a.g_in) {
-      gin = lane < a.d_g ? ((const Cmp*)a.g_in)[pidx * a.h2 + lane] : (Cmp)0;
+      v.gin = lane < a.d_g ? ((const Cmp*)a.g_in)[pidx * a.h2 + lane] : (Cmp)0;
     } else if (i != j && lane < 4) {
       const double d[3] = {(double)rw[3 * i] - (double)rw[3 * j], (double)rw[3 * i + 1] - (double)rw[3 * j + 1],
                            (double)rw[3 * i + 2] - (double)rw[3 * j + 2]};
-      gin = lane == 0 ? (Cmp)d[0] : lane == 1 ? (Cmp)d[1] : lane == 2 ? (Cmp)d[2]
-                                                : (Cmp)sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      v.gin = lane == 0 ? (Cmp)d[0] : lane == 1 ? (Cmp)d[1] : lane == 2 ? (Cmp)d[2]
+                                                  : (Cmp)sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     }
+    if (has_layer && lane < a.h2) {
+      v.dgn = ((const Cmp*)a.dG)[pidx * a.h2 + lane];
+      v.gout = ((const Cmp*)a.g_out)[pidx * a.h2 + lane];
+    }
+    if (lane < a.d_g) {
+      const int sj = j < sh.n_up ? 0 : 1;
+      const int nsj = sj ? sh.n_dn : sh.n_up;
+      const int64_t row = tile_row(w, i, N, sh.wpt);
+      v.dxv = ((const Cmp*)a.dX)[row * a.ldx + a.col0 + sj * a.d_g + lane] / (Cmp)nsj;
+    }
+    return v;
+  };
+  PairIn cur = load(warp);
+  for (int p = warp; p < N * N; p += 4) {
+    const PairIn nxt = load(p + 4);
+    const int i = p / N, j = p - (p / N) * N;
+    const int64_t pidx = ((int64_t)w * N + i) * N + j;
+    const Cmp gin = cur.gin;
     Cmp dgl = 0;
     if (has_layer) {
-      const Cmp dgn = lane < a.h2 ? ((const Cmp*)a.dG)[pidx * a.h2 + lane] : (Cmp)0;
-      const Cmp gout = lane < a.h2 ? ((const Cmp*)a.g_out)[pidx * a.h2 + lane] : (Cmp)0;
-      const Cmp t = a.l >= 1 ? gout - gin : gout;
+      const Cmp dgn = cur.dgn;
+      const Cmp t = a.l >= 1 ? cur.gout - gin : cur.gout;
       const Cmp dz = lane < a.h2 ? dgn * ((Cmp)1 - t * t) : (Cmp)0;
       accc += dz;
 #pragma unroll
@@ -309,13 +329,9 @@ __global__ void __launch_bounds__(128) k_pair_bwd(const Wlk* __restrict__ r, Sha
       }
       if (a.l >= 1) dgl += dgn;
     }
-    if (lane < a.d_g) {
-      const int sj = j < sh.n_up ? 0 : 1;
-      const int nsj = sj ? sh.n_dn : sh.n_up;
-      const int64_t row = tile_row(w, i, N, sh.wpt);
-      dgl += ((const Cmp*)a.dX)[row * a.ldx + a.col0 + sj * a.d_g + lane] / (Cmp)nsj;
-    }
+    dgl += cur.dxv;
     if (a.l >= 1 && lane < a.h2) ((Cmp*)a.dG)[pidx * a.h2 + lane] = dgl;
+    cur = nxt;
   }
   if (!has_layer) return;
   // block reduction of dW (lane = column, q = row) and dc
