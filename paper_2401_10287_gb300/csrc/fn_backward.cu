@@ -351,6 +351,167 @@ __global__ void __launch_bounds__(128) k_pair_bwd(const Wlk* __restrict__ r, Sha
                                              red[3][0][threadIdx.x]);
 }
 
+// BF16 mode: the same level on warp-level BF16 MMAs (hi/lo splits, three products, FP32
+// accumulation).  Per walker, with dz = dG^{l+1} (1 - t^2) for all N^2 pairs in shared memory:
+// the weight gradient dW = dz^T g^l (pairs as the contraction dimension; the four warps split
+// the 32 x 32 output) and the input gradient dz W (pairs as rows), then one coalesced pass adds
+// dG^{l+1} (residual, l >= 1) and the layer input's spin-mean gradient, as k_pair_bwd does.
+constexpr int kBwdWLd = 40;
+
+template <typename Wlk>
+__global__ void __launch_bounds__(128) k_pair_bwd_mma(const Wlk* __restrict__ r, Shape sh, PairBwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = lane >> 2, tig = lane & 3;
+  const int N = sh.N, NP = N * N, NPp = (NP + 15) & ~15;
+  const bool has_layer = a.l < a.L - 1;
+  __nv_bfloat16* wth = (__nv_bfloat16*)smem_raw;                 // [32 c][kBwdWLd]: bf16(W[q][c]) at [c][q]
+  __nv_bfloat16* wtl = wth + 32 * kBwdWLd;
+  float* gin_s = (float*)(wtl + 32 * kBwdWLd);                   // [NPp][33] g^l, later dz W
+  float* dz_s = gin_s + NPp * 33;                                // [NPp][33]
+  const float* dG = (const float*)a.dG + (int64_t)w * NP * a.h2;
+  if (has_layer) {
+    const float* W = (const float*)a.W;                          // [h2][d_g]
+    for (int e = tid; e < 32 * 32; e += blockDim.x) {
+      const int c = e >> 5, q = e & 31;
+      const float v = (q < a.h2 && c < a.d_g) ? W[q * a.d_g + c] : 0.f;
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      wth[c * kBwdWLd + q] = h;
+      wtl[c * kBwdWLd + q] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+    for (int e = tid; e < NPp * 33; e += blockDim.x) { gin_s[e] = 0.f; dz_s[e] = 0.f; }
+    __syncthreads();
+    const Wlk* rw = r + (int64_t)w * N * 3;
+    const float* gin_g = a.g_in ? (const float*)a.g_in + (int64_t)w * NP * a.h2 : nullptr;
+    const float* gout_g = (const float*)a.g_out + (int64_t)w * NP * a.h2;
+    // four elements per thread and round: all their global loads are issued before any use
+    for (int e0 = tid; e0 < NP * 32; e0 += 4 * blockDim.x) {
+      float gin[4], gout[4], dg[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * blockDim.x;
+        const int p = e >> 5, c = e & 31;
+        gin[u] = 0.f; gout[u] = 0.f; dg[u] = 0.f;
+        if (e >= NP * 32) continue;
+        if (gin_g) {
+          if (c < a.d_g) gin[u] = gin_g[p * a.h2 + c];
+        } else if (c < 4) {
+          const int i = p / N, j = p - (p / N) * N;
+          if (i != j) {
+            const float d0 = (float)rw[3 * i] - (float)rw[3 * j], d1 = (float)rw[3 * i + 1] - (float)rw[3 * j + 1],
+                        d2 = (float)rw[3 * i + 2] - (float)rw[3 * j + 2];
+            gin[u] = c == 0 ? d0 : c == 1 ? d1 : c == 2 ? d2 : sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+          }
+        }
+        if (c < a.h2) {
+          gout[u] = gout_g[p * a.h2 + c];
+          dg[u] = dG[p * a.h2 + c];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e >= NP * 32) continue;
+        const int p = e >> 5, c = e & 31;
+        gin_s[p * 33 + c] = gin[u];
+        if (c < a.h2) {
+          const float t = a.l >= 1 ? gout[u] - gin[u] : gout[u];
+          dz_s[p * 33 + c] = dg[u] * (1.f - t * t);
+        }
+      }
+    }
+    __syncthreads();
+    // dc = column sums of dz: four partial sums per column, one atomic per column
+    {
+      __shared__ float dcs[4][32];
+      const int q = tid & 31, k = tid >> 5;
+      float sum = 0.f;
+      for (int p = k; p < NP; p += 4) sum += dz_s[p * 33 + q];
+      dcs[k][q] = sum;
+      __syncthreads();
+      if (tid < a.h2) atomicAdd((float*)a.gc + tid, dcs[0][tid] + dcs[1][tid] + dcs[2][tid] + dcs[3][tid]);
+    }
+    // dW[q][c] = sum_p dz[p][q] g[p][c]: warp -> rows q0 .. q0 + 15, column blocks nb0, nb0 + 1
+    {
+      const int q0 = (warp >> 1) * 16, nb0 = (warp & 1) * 2;
+      float c2[2][4] = {};
+      for (int p0 = 0; p0 < NPp; p0 += 16) {
+        uint32_t ah[4], al[4];
+        const float* zc0 = dz_s + (p0 + 2 * tig) * 33 + q0 + grp;      // A[m = q][k = p] = dz[p][q]
+        split_pack(zc0[0], zc0[33], ah[0], al[0]);
+        split_pack(zc0[8], zc0[33 + 8], ah[1], al[1]);
+        split_pack(zc0[8 * 33], zc0[9 * 33], ah[2], al[2]);
+        split_pack(zc0[8 * 33 + 8], zc0[9 * 33 + 8], ah[3], al[3]);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int n = 8 * (nb0 + u) + grp;                          // B[k = p][n = c] = g[p][c]
+          const float* gc0 = gin_s + (p0 + 2 * tig) * 33 + n;
+          uint32_t bh0, bl0, bh1, bl1;
+          split_pack(gc0[0], gc0[33], bh0, bl0);
+          split_pack(gc0[8 * 33], gc0[9 * 33], bh1, bl1);
+          mma_16816(c2[u], ah, bh0, bh1);
+          mma_16816(c2[u], ah, bl0, bl1);
+          mma_16816(c2[u], al, bh0, bh1);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const int qq = q0 + grp + (q4 >= 2 ? 8 : 0), cc = 8 * (nb0 + u) + 2 * tig + (q4 & 1);
+          if (qq < a.h2 && cc < a.d_g) atomicAdd((float*)a.gW + qq * a.d_g + cc, c2[u][q4]);
+        }
+    }
+    __syncthreads();                                               // gin_s is overwritten below
+    // dz W -> gin_s (rows = pairs)
+    for (int mt = warp; mt < NPp / 16; mt += (int)(blockDim.x >> 5)) {
+      const int p0 = mt * 16;
+      float c[4][4] = {};
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        const int k0 = ks * 16;
+        const float* r0 = dz_s + (p0 + grp) * 33 + k0 + 2 * tig;
+        const float* r1 = dz_s + (p0 + grp + 8) * 33 + k0 + 2 * tig;
+        uint32_t ah[4], al[4];
+        split_pack(r0[0], r0[1], ah[0], al[0]);
+        split_pack(r1[0], r1[1], ah[1], al[1]);
+        split_pack(r0[8], r0[9], ah[2], al[2]);
+        split_pack(r1[8], r1[9], ah[3], al[3]);
+#pragma unroll
+        for (int nb = 0; nb < 4; ++nb) {
+          const int off = (8 * nb + grp) * kBwdWLd + k0 + 2 * tig;
+          const uint32_t bh0 = *(const uint32_t*)(wth + off), bh1 = *(const uint32_t*)(wth + off + 8);
+          const uint32_t bl0 = *(const uint32_t*)(wtl + off), bl1 = *(const uint32_t*)(wtl + off + 8);
+          mma_16816(c[nb], ah, bh0, bh1);
+          mma_16816(c[nb], ah, bl0, bl1);
+          mma_16816(c[nb], al, bh0, bh1);
+        }
+      }
+#pragma unroll
+      for (int nb = 0; nb < 4; ++nb)
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4)
+          gin_s[(p0 + grp + (q4 >= 2 ? 8 : 0)) * 33 + 8 * nb + 2 * tig + (q4 & 1)] = c[nb][q4];
+    }
+    __syncthreads();
+  }
+  if (a.l < 1) return;                                             // no gradient below the input features
+  // dG^l = (dz W) + dG^{l+1} (residual) + the spin-mean gradient of the layer input
+  float* dGo = (float*)a.dG + (int64_t)w * NP * a.h2;
+  for (int e = tid; e < NP * a.h2; e += blockDim.x) {
+    const int p = e / a.h2, c = e - (e / a.h2) * a.h2;
+    const int i = p / N, j = p - (p / N) * N;
+    float v = 0.f;
+    if (has_layer) v = gin_s[p * 33 + c] + dGo[e];
+    if (c < a.d_g) {
+      const int sj = j < sh.n_up ? 0 : 1;
+      const int nsj = sj ? sh.n_dn : sh.n_up;
+      v += ((const float*)a.dX)[tile_row(w, i, N, sh.wpt) * a.ldx + a.col0 + sj * a.d_g + c] / (float)nsj;
+    }
+    dGo[e] = v;
+  }
+}
+
 // ---- internal layout -> blob order ---------------------------------------------------
 template <typename Par, typename Cmp>
 __global__ void k_unprep(Par* __restrict__ blob, const CopyDesc* __restrict__ descs, const Cmp* __restrict__ gradc) {
@@ -538,7 +699,13 @@ void launch_backward(const fn_system* s, const void* walkers, const Shape& sh, c
       }
       a.dG = ws.dG; a.dX = dX; a.ldx = d.ldx; a.col0 = d.d_h;
       ProfScope ps(s->prof, kProfBwdPair, st);
-      k_pair_bwd<Cmp, Wlk><<<sh.B, 128, 0, st>>>(r, sh, a);
+      if (Mode::kMode == FN_BF16_MIXED) {
+        const size_t smem = 2 * 32 * kBwdWLd * 2 + (size_t)2 * ((N * N + 15) & ~15) * 33 * 4;
+        cudaFuncSetAttribute(k_pair_bwd_mma<Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_pair_bwd_mma<Wlk><<<sh.B, 128, smem, st>>>(r, sh, a);
+      } else {
+        k_pair_bwd<Cmp, Wlk><<<sh.B, 128, 0, st>>>(r, sh, a);
+      }
     }
   }
   dim3 grid(32, s->n_descs);

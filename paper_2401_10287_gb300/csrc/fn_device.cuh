@@ -27,6 +27,25 @@ __device__ __forceinline__ void st_lo(__nv_bfloat16* p, double v) {
 }
 template <typename T, typename V> __device__ __forceinline__ void st_lo(T*, V) {}
 
+// Warp-level BF16 tensor-core product (m16n8k16, FP32 accumulation) and the hi/lo split of
+// two FP32 values into packed BF16 pairs: bf16(v) and bf16(v - bf16(v)).
+__device__ __forceinline__ void split_pack(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  hi = *(const uint32_t*)&h;
+  lo = *(const uint32_t*)&l;
+}
+
+__device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+
 // two adjacent elements at an even element offset from an aligned base
 __device__ __forceinline__ void st2(double* p, double a, double b) { *(double2*)p = make_double2(a, b); }
 __device__ __forceinline__ void st2(float* p, float a, float b) { *(float2*)p = make_float2(a, b); }

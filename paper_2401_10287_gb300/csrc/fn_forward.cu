@@ -532,22 +532,6 @@ __global__ void k_spin_means_bf16(Shape sh, const __nv_bfloat16* __restrict__ Y,
 // 16-pair row tiles; the pair activations stay in shared memory (FP32) between layers.
 constexpr int kPairWLd = 40;   // bf16 row stride of the staged weights: conflict-free fragment loads
 
-__device__ __forceinline__ void split_pack(float a, float b, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  const float2 hf = __bfloat1622float2(h);
-  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
-  hi = *(const uint32_t*)&h;
-  lo = *(const uint32_t*)&l;
-}
-
-__device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 template <typename Wlk>
 __global__ void __launch_bounds__(128) k_pair_value_mma(const Wlk* __restrict__ r, Shape sh, PairArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
