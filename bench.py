@@ -424,12 +424,80 @@ def compare_modes(P, sysm, a, cfg, B, bf16_ms):
     e64m = float(e64.mean())
     g16.close()
     g64.close()
+    rates = per_call_rates(P, sysm, a, cfg, B)
+    h2 = h2_precision(P)
     return {"fp32_ms_per_step": fp32_ms, "bf16_speedup_vs_fp32": fp32_ms / bf16_ms,
+            "per_call": rates, "h2_precision_config": h2,
             "bf16_energy_error": {"walkers": B, "equilibration": "300 BF16 Metropolis steps",
                                   "reference": "FP64 path on the same walkers and parameters",
                                   "mean_energy_fp64_ha": e64m, "bias_mha": float(d.mean() * 1e3),
                                   "bias_stderr_mha": float(d.std() / np.sqrt(B) * 1e3),
                                   "median_abs_de_ha": float(np.median(np.abs(d)))}}
+
+
+def _time_calls(fn, reps):
+    import torch
+    out = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return float(np.median(out))
+
+
+def per_call_rates(P, sysm, a, cfg, B):
+    """Per-call throughputs on the N2 workload (CUDA events, median over repetitions): walker local
+    energies per second of one local_energy call and walker Metropolis steps per second of a
+    10-step mcmc_steps call, for BF16-mixed, FP32 and FP64 (FP64 on 1024 walkers)."""
+    out = {}
+    for name, prec, nb, reps in (("bf16", P.BF16_MIXED, B, 20), ("fp32", P.FP32, B, 5), ("fp64", P.FP64, 1024, 3)):
+        g = P.System(sysm.nuclei, sysm.charges, sysm.n_up, sysm.n_down, P.NetConfig.from_ansatz(a, prec))
+        p = g.init_params(cfg["seed"])
+        w, _ = g.init_walkers(nb, cfg["seed"] + 5, cfg["init_std"])
+        lp, _ = g.log_psi(p, w)
+        g.mcmc_steps(p, w, lp, 10, cfg["step_size"], cfg["seed"])
+        g.local_energy(p, w)
+        le_ms = _time_calls(lambda: g.local_energy(p, w), reps)
+        mc_ms = _time_calls(lambda: g.mcmc_steps(p, w, lp, 10, cfg["step_size"], cfg["seed"] + 1), reps)
+        out[name] = {"walkers": nb, "local_energy_ms": le_ms, "walker_e_l_per_s": nb / le_ms * 1e3,
+                     "mcmc_10_steps_ms": mc_ms, "walker_steps_per_s": 10 * nb / mc_ms * 1e3}
+        g.close()
+    out["bf16_local_energy_speedup_vs_fp32"] = out["bf16"]["walker_e_l_per_s"] / out["fp32"]["walker_e_l_per_s"]
+    return out
+
+
+def h2_precision(P):
+    """The precision configuration: H2 (1.4 bohr), 2 layers 32/8, 1 determinant, isotropic
+    envelopes, 4096 and 16384 walkers equilibrated by 300 BF16 Metropolis steps of 0.3 bohr;
+    BF16-mixed local energies against the FP64 path on the same walkers, and the local-energy
+    call time of BF16 against FP32."""
+    sysm = W.h2()
+    a = W.Ansatz(2, 32, 8, 1, "iso")
+    res = {}
+    for nb in (4096, 16384):
+        g16 = P.System(sysm.nuclei, sysm.charges, sysm.n_up, sysm.n_down, P.NetConfig.from_ansatz(a, P.BF16_MIXED))
+        g64 = P.System(sysm.nuclei, sysm.charges, sysm.n_up, sysm.n_down, P.NetConfig.from_ansatz(a, P.FP64))
+        g32 = P.System(sysm.nuclei, sysm.charges, sysm.n_up, sysm.n_down, P.NetConfig.from_ansatz(a, P.FP32))
+        p = g16.init_params(0)
+        w, _ = g16.init_walkers(nb, 0, 1.0)
+        lp, _ = g16.log_psi(p, w)
+        g16.mcmc_steps(p, w, lp, 300, 0.3, 1)
+        e16, _, _ = g16.local_energy(p, w)
+        e64, _, _ = g64.local_energy(p.double(), w.double())
+        d = (e16 - e64).cpu().numpy()
+        t16 = _time_calls(lambda: g16.local_energy(p, w), 10)
+        t32 = _time_calls(lambda: g32.local_energy(p, w), 10)
+        res[str(nb)] = {"mean_energy_fp64_ha": float(e64.mean()), "bias_mha": float(d.mean() * 1e3),
+                        "bias_stderr_mha": float(d.std() / np.sqrt(nb) * 1e3),
+                        "median_abs_de_ha": float(np.median(np.abs(d))),
+                        "bf16_local_energy_ms": t16, "fp32_local_energy_ms": t32, "bf16_speedup_vs_fp32": t32 / t16}
+        for g in (g16, g64, g32):
+            g.close()
+    return res
 
 
 def run_serving(n_jobs: int, budget_gb: float, slots: int):

@@ -115,3 +115,20 @@ def test_bf16_energy_grad_against_fp64_and_oracle(name, make, ans, B):
     for b, f, d in dirs:
         assert abs(f - d) <= 1e-5 * max(1.0, abs(d))
         assert abs(b - d) <= 3e-2 * np.linalg.norm(gd)
+
+
+def test_bf16_h2_precision_config_mean_energy():
+    """Precision configuration: H2 at 1.4 bohr, 2 layers 32/8, 1 determinant, isotropic
+    envelopes, 4096 walkers equilibrated by the oracle's Metropolis chain.  The BF16-mixed
+    mean local energy must be within 1 mHa of the oracle's on the same walkers (the target
+    of the precision mode); per-walker errors are reported."""
+    sysm = W.h2()
+    ans = W.Ansatz(2, 32, 8, 1, "iso")
+    e, lp, e_ref, lp_ref, scale = _run(sysm, ans, 4096, seed=0, perturb=0.0, burn_in=200, step=0.3)
+    d = e - e_ref
+    err = abs(d.mean())
+    se = d.std() / np.sqrt(d.size)
+    print(f"H2 cfg3, 4096 walkers: mean-energy error {d.mean() * 1e3:.3f} +- {se * 1e3:.3f} mHa of "
+          f"{e_ref.mean():.5f} Ha; per-walker median |dE| {np.median(np.abs(d)):.2e} Ha, max {np.abs(d).max():.2e}")
+    assert np.all(np.isfinite(e))
+    assert err <= 1e-3
