@@ -155,8 +155,9 @@ def run_reference(args):
 
 
 def _algorithmic(cls, B, N, a, T_full, act_bytes, launches=1):
-    """Algorithmic work of one launch of a kernel class at this workload:
-    returns (amount, kind) with kind "bytes" (HBM-bound), "flop" (FP32/tensor) or "flop64"."""
+    """Algorithmic work of one launch of a kernel class at this workload: the bytes a launch
+    must move or the operations it must execute, independent of how the kernel does it.
+    Returns (amount, kind) with kind "bytes" (HBM-bound), "flop" (FP32/tensor) or "flop64"."""
     M = 2
     h1, h2, K = a.h1, a.h2, a.n_dets
     n = N // 2
