@@ -292,7 +292,9 @@ static fn_status check_launch(fn_system* s, const char* what) {
   if (s->host_error != FN_OK) {
     const fn_status e = s->host_error;
     s->host_error = FN_OK;
-    set_error(std::string(what) + ": a TMA tensor map could not be encoded");
+    set_error(std::string(what) + (e == FN_ERR_UNSUPPORTED
+                                       ? ": batch too large (walkers x determinants x orbitals must stay below 2^31)"
+                                       : ": a TMA tensor map could not be encoded or a GEMM shape is not covered"));
     return e;
   }
   return cuda_status(cudaGetLastError(), what);
