@@ -253,6 +253,36 @@ struct TcArgs {
 };
 
 
+// Packed two-lane FP32 arithmetic (one instruction for two values) for the epilogue.
+__device__ __forceinline__ uint64_t pack_f2(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack_f2(uint64_t v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t add_f2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub_f2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul_f2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t fma_f2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // ---- epilogue: stream layer ------------------------------------------------------------
 // One 32-column chunk, in two 16-column halves (register budget).  `res` holds the
 // chunk's residual (8 bf16 per uint4), loaded before the accumulator wait; `mrow` is the
@@ -285,55 +315,38 @@ __device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, bool h
       }
       float out[16];
       if (live) {
-        float z[16];
         const float4* mt = (const float4*)(mrow + cc * 32 + hh * 16);
+        // residual of this piece from the shared-memory tile (TMA, 128B swizzle: 16-byte chunk j
+        // of row r sits at chunk j ^ (r % 8) of the row's 128 bytes); zero without a residual
+        float rv[16];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const float4 m4 = mt[v];
-          z[4 * v] = __uint_as_float(acc[4 * v]) + m4.x;
-          z[4 * v + 1] = __uint_as_float(acc[4 * v + 1]) + m4.y;
-          z[4 * v + 2] = __uint_as_float(acc[4 * v + 2]) + m4.z;
-          z[4 * v + 3] = __uint_as_float(acc[4 * v + 3]) + m4.w;
+        for (int v = 0; v < 2; ++v) {
+          const int cl = cc * 32 + hh * 16 + 8 * v;
+          uint4 u = make_uint4(0u, 0u, 0u, 0u);
+          if (a.residual) u = *(const uint4*)(rs + (cl >> 6) * kResBox + r * 128 + ((((cl & 63) >> 3) ^ (r & 7)) << 4));
+          const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 f = __bfloat1622float2(p2[e]);
+            rv[8 * v + 2 * e] = f.x;
+            rv[8 * v + 2 * e + 1] = f.y;
+          }
         }
         if (kind == 0) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float h = tanh_fast(z[j]);
-            hv[j] = __float_as_uint(h);
-            sq[j] = 0u;
-            out[j] = h;
-          }
-        } else if (kind == 1) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float h = __uint_as_float(hv[j]);
-            out[j] = (1.0f - h * h) * z[j];
-            sq[j] = __float_as_uint(fmaf(z[j], z[j], __uint_as_float(sq[j])));
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float h = __uint_as_float(hv[j]);
-            const float d = 1.0f - h * h;
-            out[j] = d * (z[j] - 2.0f * h * __uint_as_float(sq[j]));
-          }
-        }
-        if (a.residual) {
-#pragma unroll
-          for (int v = 0; v < 2; ++v) {
-            // residual tile in shared memory (TMA, 128B swizzle): 16-byte chunk j of row r sits at
-            // chunk j ^ (r % 8) of the row's 128 bytes
-            const int cl = cc * 32 + hh * 16 + 8 * v;
-            const uint4 u = *(const uint4*)(rs + (cl >> 6) * kResBox + r * 128 + ((((cl & 63) >> 3) ^ (r & 7)) << 4));
-            const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u;
+          for (int v = 0; v < 4; ++v) {
+            const float4 m4 = mt[v];
+            const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              const float2 f = __bfloat1622float2(p2[e]);
-              out[8 * v + 2 * e] += f.x;
-              out[8 * v + 2 * e + 1] += f.y;
+              const int j = 4 * v + e;
+              const float h = tanh_fast(__uint_as_float(acc[j]) + mv[e]);
+              hv[j] = __float_as_uint(h);
+              sq[j] = 0u;
+              out[j] = h + rv[j];
             }
           }
-          if (kind == 0 && a.alo_row > 0) {
+          if (a.residual && a.alo_row > 0) {
             // the value slab's residual is a pair: add its low part (slab T of X)
             const uint4* xl = (const uint4*)(a.X + (int64_t)T * sh.R * a.ldx + row * a.ldx + col0 + hh * 16);
 #pragma unroll
@@ -347,6 +360,31 @@ __device__ __forceinline__ void epi_layer(const TcArgs& a, int t, int cc, bool h
                 out[8 * v + 2 * e + 1] += f.y;
               }
             }
+          }
+        } else {
+          // tangent and Laplacian slabs on packed two-lane FP32 operations:
+          //   z = acc + M,  -(1 - h^2) = h h - 1,  out = residual - (-(1 - h^2)) w,
+          //   w = z (tangent; and sum z^2 += z z) or z - 2 h sum z^2 (Laplacian)
+          const uint64_t m1 = pack_f2(-1.f, -1.f), m2 = pack_f2(-2.f, -2.f);
+#pragma unroll
+          for (int jp = 0; jp < 8; ++jp) {
+            const float4 m4 = mt[jp >> 1];
+            const uint64_t z2 = add_f2(pack_f2(__uint_as_float(acc[2 * jp]), __uint_as_float(acc[2 * jp + 1])),
+                                       (jp & 1) ? pack_f2(m4.z, m4.w) : pack_f2(m4.x, m4.y));
+            const uint64_t h2 = pack_f2(__uint_as_float(hv[2 * jp]), __uint_as_float(hv[2 * jp + 1]));
+            const uint64_t s2 = pack_f2(__uint_as_float(sq[2 * jp]), __uint_as_float(sq[2 * jp + 1]));
+            const uint64_t nd2 = fma_f2(h2, h2, m1);
+            uint64_t w2;
+            if (kind == 1) {
+              w2 = z2;
+              float s0, s1;
+              unpack_f2(fma_f2(z2, z2, s2), s0, s1);
+              sq[2 * jp] = __float_as_uint(s0);
+              sq[2 * jp + 1] = __float_as_uint(s1);
+            } else {
+              w2 = fma_f2(mul_f2(h2, s2), m2, z2);
+            }
+            unpack_f2(sub_f2(pack_f2(rv[2 * jp], rv[2 * jp + 1]), mul_f2(nd2, w2)), out[2 * jp], out[2 * jp + 1]);
           }
         }
         uint4* yo = (uint4*)(a.Y + t * yslab + row * a.ldy + col0 + hh * 16);
