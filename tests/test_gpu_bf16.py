@@ -132,3 +132,20 @@ def test_bf16_h2_precision_config_mean_energy():
           f"{e_ref.mean():.5f} Ha; per-walker median |dE| {np.median(np.abs(d)):.2e} Ha, max {np.abs(d).max():.2e}")
     assert np.all(np.isfinite(e))
     assert err <= 1e-3
+
+
+@pytest.mark.parametrize("name,make", [
+    ("H", W.hydrogen_atom),                 # one electron: no pairs, an empty spin group
+    ("Li", lambda: W.atom(3)),              # 2 up / 1 down
+    ("O-", lambda: W.atom(8, -1)),          # 5 up / 4 down
+])
+def test_bf16_atoms_unequal_spins_against_oracle(name, make):
+    """BF16 mode on atoms with unequal (or empty) spin groups, against the FP64 oracle on
+    oracle-equilibrated walkers: same per-walker bound as the molecules above."""
+    e, lp, e_ref, lp_ref, scale = _run(make(), W.Ansatz(3, 64, 16, 4, "aniso"), 96, seed=1, burn_in=100)
+    rel = np.abs(e - e_ref) / scale
+    print(f"{name}: median rel {np.median(rel):.2e} max rel {rel.max():.2e}; mean-energy error "
+          f"{abs(e.mean() - e_ref.mean()) * 1e3:.3f} mHa of {e_ref.mean():.4f} Ha")
+    assert np.all(np.isfinite(e))
+    assert np.median(rel) < 1e-2
+    assert np.median(np.abs(lp - lp_ref)) < 1e-2
