@@ -10,9 +10,12 @@
 //                  dU = Hbar^T (walker sums of dz); dX = dz V_self;
 //                  dh_l = dX_h + dh_{l+1} (residual) + dHbar / n_spin
 //   pair layer     one warp per pair, lane = channel; dW, dc reduced in registers,
-//                  then per CTA, then one atomic per element
-// Parameter gradients accumulate in the internal layout and are scattered back to
-// the blob order at the end.
+//                  then per CTA, then one atomic per element (BF16 mode: warp-level
+//                  BF16 MMAs over all pairs of a walker)
+// In BF16 mode the large GEMMs run on the tensor cores (fn_layer_tc.cu): row-major
+// products directly, weight gradients as split-K products over the electron rows on
+// transposed BF16 copies.  Parameter gradients accumulate in the internal layout and
+// are scattered back to the blob order at the end.
 #include <algorithm>
 
 #include "fn_device.cuh"

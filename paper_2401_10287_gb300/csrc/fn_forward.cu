@@ -1,15 +1,19 @@
 // Forward pass of the wavefunction with forward-mode Laplacian tangents
-// ("FermiNet Model" section; Eq. 4 envelope), SIMT kernels for FP64/FP32 and the
-// glue of the BF16 mode:
-//   k_prep          parameter blob -> internal layouts (one launch, descriptor table)
-//   k_features_en   one-electron stream input [r_i - R_m, |r_i - R_m|] with tangents
-//   k_features_mean spin means of the one-electron input
-//   k_pair_stream   two-electron stream (sparse tangents: only r_i and r_j move a pair)
-//                   and its spin means for every layer
-//   k_gemm          tiled SIMT GEMM (mean-field term U [hbar_up, hbar_dn] + b)
-//   k_layer         one-electron layer GEMM over all tangent slabs with the fused
-//                   tanh forward-Laplacian epilogue, residual and next spin means
-//   k_orbitals      orbital projection x envelope with the product rule
+// ("FermiNet Model" section; Eq. 4 envelope): SIMT kernels for FP64/FP32, the BF16-mode
+// kernels around the tensor-core ones of fn_layer_tc.cu, and the launch sequence:
+//   k_prep             parameter blob -> internal layouts (one launch, descriptor table)
+//   k_features_en      one-electron stream input [r_i - R_m, |r_i - R_m|] with tangents
+//   k_features_mean    spin means of the one-electron input
+//   k_pair_full/value  two-electron stream, SIMT (a pair depends on r_i - r_j only: 5 jet
+//                      rows) and its spin means for every layer
+//   k_pair_*_mma       the same on warp-level BF16 MMAs with hi/lo splits (BF16 mode)
+//   k_spin_means_bf16  spin means of a BF16 stream-layer output (next mean-field input)
+//   k_gemm             tiled SIMT GEMM (mean-field term U [hbar_up, hbar_dn] + b)
+//   k_layer            one-electron layer GEMM over all tangent slabs with the fused
+//                      tanh forward-Laplacian epilogue, residual and next spin means
+//   k_envelope_values  envelope values per (electron, orbital) for the tensor-core orbitals
+//   k_orbital_fixup    envelope-derivative terms of the tensor-core orbitals
+//   k_orbitals         orbital projection x envelope with the product rule (SIMT)
 #include <algorithm>
 #include <vector>
 
