@@ -350,6 +350,9 @@ def run_mine(args):
     comparison = None
     if prec == P.BF16_MIXED and ws == 1 and not args.no_compare:
         comparison = compare_modes(P, sysm, a, cfg, B, ms / args.steps)
+    train = None
+    if prec == P.BF16_MIXED and ws == 1 and not args.no_train:
+        train = training(P, sysm, a, cfg, B)
     serving = None
     if args.serving_jobs > 0 and ws == 1:
         serving = run_serving(args.serving_jobs, args.serving_budget_gb, args.serving_slots)
@@ -374,6 +377,7 @@ def run_mine(args):
         "kernels_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         "cpu_baseline": cb,
         "bf16_vs_fp32_and_fp64": comparison,
+        "training": train,
         "serving": serving,
         "acceptance": float(acc.item()) / max(1, (args.warmup + 2 * args.steps) * cfg["mcmc_steps"] * B),
     }
@@ -501,6 +505,57 @@ def h2_precision(P):
     return res
 
 
+H2_EXACT_HA = -1.174476   # H2 at 1.4 bohr, Born-Oppenheimer, non-relativistic (Kolos & Wolniewicz)
+
+
+def training(P, sysm, a, cfg, B):
+    """The optimisation loop (fn_vmc_iteration: log|psi|, 10 Metropolis steps, E_L, clipping at
+    5 mean absolute deviations, the Eq. 6 gradient, Adam) on persistent walkers.
+    (1) Iteration time on the N2 workload (BF16-mixed, CUDA events, 10 iterations after 3).
+    (2) H2 at 1.4 bohr trained from its random initial parameters (2 layers 32/8, 1 determinant,
+        isotropic envelopes, 4096 walkers, BF16-mixed, Adam lr 0.01, 0.3 bohr proposals, 1500
+        iterations after 20 sampler-only ones): the mean local energy of the last 200
+        iterations against the exact energy."""
+    import torch
+    g = P.System(sysm.nuclei, sysm.charges, sysm.n_up, sysm.n_down, P.NetConfig.from_ansatz(a, P.BF16_MIXED))
+    p = g.init_params(cfg["seed"])
+    w, _ = g.init_walkers(B, cfg["seed"] + 9, cfg["init_std"])
+    tc = P.TrainConfig(n_mcmc_steps=cfg["mcmc_steps"], step_size=cfg["step_size"], seed=cfg["seed"] + 10,
+                       clip_width=5.0, lr=1e-4)
+    tr = P.Trainer(g, p, w, tc)
+    for _ in range(3):
+        tr.step()
+    it_ms = _time_calls(tr.step, 10)
+    g.sync()
+    n2 = {"walkers": B, "ms_per_iteration": it_ms, "walker_iterations_per_s": B / it_ms * 1e3,
+          "iteration": "log|psi| + 10 Metropolis steps + E_L + clipping + Eq. 6 gradient + Adam"}
+    g.close()
+
+    h2 = W.h2()
+    ha = W.Ansatz(2, 32, 8, 1, "iso")
+    g = P.System(h2.nuclei, h2.charges, h2.n_up, h2.n_down, P.NetConfig.from_ansatz(ha, P.BF16_MIXED))
+    p = g.init_params(0)
+    w, _ = g.init_walkers(4096, 1, 1.0)
+    P.Trainer(g, p, w, P.TrainConfig(n_mcmc_steps=10, step_size=0.3, seed=3, optimizer="sgd", lr=0.0)).run(20)
+    tr = P.Trainer(g, p, w, P.TrainConfig(n_mcmc_steps=10, step_size=0.3, seed=2, clip_width=5.0, lr=1e-2))
+    n_it = 1500
+    means = torch.empty(n_it, dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    for k in range(n_it):
+        tr.step()
+        means[k] = tr.e_local.mean()
+    g.sync()
+    wall = time.perf_counter() - t0
+    tail = means[-200:].cpu().numpy()
+    g.close()
+    return {"n2": n2,
+            "h2_trained": {"iterations": n_it, "wall_s": round(wall, 3),
+                           "mean_energy_last_200_ha": float(tail.mean()),
+                           "stderr_of_iteration_means_ha": float(tail.std() / np.sqrt(tail.size)),
+                           "exact_ha": H2_EXACT_HA,
+                           "above_exact_mha": float((tail.mean() - H2_EXACT_HA) * 1e3)}}
+
+
 def run_serving(n_jobs: int, budget_gb: float, slots: int):
     """The serving workload: Poisson arrivals (50/s, seed 4) of atoms Z = 1..14 with charge
     -1/0/+1 and H2/LiH/N2/CO, 256-4096 walkers, 50 Metropolis steps and one E_L each, on the
@@ -536,6 +591,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the FP32 step time and the BF16-vs-FP64 energy error after the timed region")
+    ap.add_argument("--no-train", action="store_true",
+                    help="skip the training-loop measurements (N2 iteration time, H2 trained energy)")
     ap.add_argument("--serving-jobs", type=int, default=150,
                     help="jobs of the serving stream to replay after the timed steps (0 to skip)")
     ap.add_argument("--serving-budget-gb", type=float, default=160.0)

@@ -181,6 +181,74 @@ fn_status fn_log_psi_vjp(fn_system_t sys, const void* d_params, const void* d_wa
 fn_status fn_log_psi_noalloc(fn_system_t sys, const void* d_params, const void* d_walkers,
                              int n_walkers, double* d_log_psi, int8_t* d_sign, void* stream);
 
+/* ---- VMC training loop ------------------------------------------------------------
+ * The training phase of the method updates the parameters with the Eq. 6 gradient
+ * between rounds of the electron sampler.  The method names no optimiser: the library
+ * offers Adam (Kingma & Ba 2015, Algorithm 1) and plain gradient descent, and an optional
+ * clamp of the local energies to a window around their median before Eq. 6.           */
+
+/* Adam update of the flat parameter blob, in place, with step count t >= 1:
+ *   m <- beta1 m + (1 - beta1) g,   v <- beta2 v + (1 - beta2) g^2,
+ *   theta <- theta - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps).
+ * d_params, d_grad, d_m, d_v [fn_param_count] blob dtype, caller-owned; d_m and d_v are
+ * zero before the first step and must not alias each other, d_params or d_grad.
+ * Requires 0 <= beta1, beta2 < 1, eps >= 0 and a finite lr; arithmetic in the blob dtype.
+ * A non-finite updated parameter sets the numeric bit reported by fn_sync.          */
+fn_status fn_adam_step(fn_system_t sys, void* d_params, const void* d_grad, void* d_m, void* d_v,
+                       int64_t t, double lr, double beta1, double beta2, double eps, void* stream);
+
+/* Gradient descent, in place: theta <- theta - lr g (blob dtype, [fn_param_count]).  */
+fn_status fn_sgd_step(fn_system_t sys, void* d_params, const void* d_grad, double lr, void* stream);
+
+/* Local-energy clipping: centre = the lower median (the element of rank
+ * floor((B - 1) / 2) of the sorted batch, an exact member of it), spread = mean |E_L - centre|
+ * (summed in FP64), and every energy clamped to centre +- width * spread; width <= 0
+ * copies the energies unchanged.  d_e_local, d_e_clipped [n_walkers] double; they may be
+ * the same buffer.  d_stats [2] double receives (centre, spread), NULL to skip.  One CTA
+ * does the work (a selection pass reads the batch 8 times).  A non-finite energy makes
+ * the spread non-finite: nothing is clamped and fn_sync reports FN_ERR_NUMERIC.     */
+fn_status fn_clip_local_energy(fn_system_t sys, const double* d_e_local, int n_walkers, double width,
+                               double* d_e_clipped, double* d_stats, void* stream);
+
+typedef enum { FN_OPT_ADAM = 0, FN_OPT_SGD = 1 } fn_optimizer;
+
+/* Settings of one training iteration.
+ *   n_mcmc_steps  Metropolis steps per iteration (>= 0);
+ *   step_size     proposal standard deviation in bohr (>= 0);
+ *   seed          key of the sampler's random streams;
+ *   clip_width    local-energy clipping width (fn_clip_local_energy), <= 0 for none;
+ *   optimizer     fn_optimizer;
+ *   lr, beta1, beta2, eps   rate and Adam settings (beta and eps unused by FN_OPT_SGD). */
+typedef struct {
+  int n_mcmc_steps;
+  double step_size;
+  uint64_t seed;
+  double clip_width;
+  int optimizer;
+  double lr, beta1, beta2, eps;
+} fn_train_config;
+
+/* One VMC training iteration with index `iteration` >= 0 on walkers that persist between
+ * iterations, in this order:
+ *   1. log|psi| of d_walkers under the current parameters (value-only pass);
+ *   2. n_mcmc_steps Metropolis steps (fn_mcmc_steps) with step indices
+ *      iteration * n_mcmc_steps + k, k = 0 .. n_mcmc_steps - 1 (taken modulo 2^32);
+ *   3. local energies of the moved walkers (fn_local_energy);
+ *   4. clipping with cfg->clip_width (the clipped copy is internal);
+ *   5. the Eq. 6 gradient with the clipped energies held fixed (fn_energy_grad);
+ *   6. the update: Adam with step count iteration + 1, or gradient descent.
+ * d_params updated in place; d_walkers [B][N][3] updated in place; d_opt_state
+ * [2 fn_param_count] blob dtype = (m, v) of Adam, zero before iteration 0 (NULL for SGD);
+ * d_grad [fn_param_count] blob dtype receives the gradient of step 5; d_log_psi [B] double
+ * receives log|psi| of the moved walkers under the parameters before the update;
+ * d_e_local [B] double receives the unclipped energies; d_e_mean [1] double receives the
+ * mean of the clipped energies (NULL to skip); d_accept [1] int64 is incremented by the
+ * accepted moves (NULL to skip).  Errors as the calls it is made of.                   */
+fn_status fn_vmc_iteration(fn_system_t sys, const fn_train_config* cfg, void* d_params, void* d_walkers,
+                           int n_walkers, int64_t iteration, void* d_opt_state, void* d_grad,
+                           double* d_log_psi, double* d_e_local, double* d_e_mean, int64_t* d_accept,
+                           void* stream);
+
 /* Kernel timing: while enabled, every kernel the handle launches is bracketed by a
  * CUDA event pair on its stream (adds a few microseconds per launch).  Enabling or
  * disabling clears the counters.  fn_profile_read waits for the recorded events and

@@ -5,8 +5,9 @@ The computation runs in ``libfnvmc.so`` (CUDA kernels behind the C ABI of
 builds the library (``build``).  Importing the package does not load the library;
 the first call that needs it does, and fails loudly if it is missing.
 """
-from .api import (FP32, FP64, BF16_MIXED, ISO, ANISO, NetConfig, FnError, System, EnergyGrad,
+from .api import (FP32, FP64, BF16_MIXED, ISO, ANISO, NetConfig, FnError, System, EnergyGrad, TrainConfig,
                   library_path, load_library)
+from .train import Trainer
 
 __all__ = ["FP32", "FP64", "BF16_MIXED", "ISO", "ANISO", "NetConfig", "FnError", "System", "EnergyGrad",
-           "library_path", "load_library"]
+           "TrainConfig", "Trainer", "library_path", "load_library"]

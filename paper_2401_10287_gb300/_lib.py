@@ -13,6 +13,12 @@ class NetConfigC(C.Structure):
                 ("envelope", C.c_int), ("precision", C.c_int)]
 
 
+class TrainConfigC(C.Structure):
+    _fields_ = [("n_mcmc_steps", C.c_int), ("step_size", C.c_double), ("seed", C.c_uint64),
+                ("clip_width", C.c_double), ("optimizer", C.c_int), ("lr", C.c_double),
+                ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double)]
+
+
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 _I = C.POINTER(C.c_int)
@@ -32,6 +38,11 @@ SIGNATURES = {
     "fn_energy_grad": (C.c_int, [_P, _P, _P, _P, C.c_int, _P, _P, _P]),
     "fn_log_psi_noalloc": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P]),
     "fn_log_psi_vjp": (C.c_int, [_P, _P, _P, _P, C.c_int, _P, _P]),
+    "fn_adam_step": (C.c_int, [_P, _P, _P, _P, _P, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double, _P]),
+    "fn_sgd_step": (C.c_int, [_P, _P, _P, C.c_double, _P]),
+    "fn_clip_local_energy": (C.c_int, [_P, _P, C.c_int, C.c_double, _P, _P, _P]),
+    "fn_vmc_iteration": (C.c_int, [_P, C.POINTER(TrainConfigC), _P, _P, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P,
+                                   _P]),
     "fn_profile_enable": (C.c_int, [_P, C.c_int]),
     "fn_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "fn_sync": (C.c_int, [_P, _P, C.c_int]),

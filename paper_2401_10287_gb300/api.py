@@ -51,6 +51,29 @@ class NetConfig:
         return NetConfig(ansatz.n_layers, ansatz.h1, ansatz.h2, ansatz.n_dets, env, precision)
 
 
+OPT_ADAM, OPT_SGD = 0, 1
+
+
+@dataclass(frozen=True)
+class TrainConfig:
+    """Settings of one VMC training iteration (fn_train_config)."""
+    n_mcmc_steps: int = 10
+    step_size: float = 0.02
+    seed: int = 0
+    clip_width: float = 0.0
+    optimizer: str = "adam"          # "adam" or "sgd"
+    lr: float = 1e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+
+    def c_struct(self) -> _lib.TrainConfigC:
+        opt = {"adam": OPT_ADAM, "sgd": OPT_SGD}[self.optimizer]
+        return _lib.TrainConfigC(int(self.n_mcmc_steps), float(self.step_size), int(self.seed),
+                                 float(self.clip_width), opt, float(self.lr), float(self.beta1),
+                                 float(self.beta2), float(self.eps))
+
+
 def _ptr(t: Optional[torch.Tensor]):
     return None if t is None else C.c_void_p(t.data_ptr())
 
@@ -188,6 +211,46 @@ class System:
         _check(self._lib.fn_log_psi_vjp(self._h, _ptr(params), _ptr(walkers), _ptr(weights), B, _ptr(g),
                                         _stream(stream)))
         return g
+
+    def _check_blob(self, *tensors):
+        for t in tensors:
+            if t.dtype != self.dtype or t.numel() != self.param_count or not t.is_contiguous():
+                raise ValueError(f"expected a contiguous {self.dtype} blob of {self.param_count} elements")
+
+    def adam_step(self, params, grad, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                  eps: float = 1e-8, stream=None):
+        """In-place Adam update of params (and of its moments m, v); step counts from 1."""
+        self._check_blob(params, grad, m, v)
+        _check(self._lib.fn_adam_step(self._h, _ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr),
+                                      float(beta1), float(beta2), float(eps), _stream(stream)))
+
+    def sgd_step(self, params, grad, lr: float, stream=None):
+        self._check_blob(params, grad)
+        _check(self._lib.fn_sgd_step(self._h, _ptr(params), _ptr(grad), float(lr), _stream(stream)))
+
+    def clip_local_energy(self, e_local, width: float, out=None, stream=None):
+        """(clipped energies, [centre, spread]); out may be e_local itself."""
+        if e_local.dtype != torch.float64 or not e_local.is_contiguous():
+            raise ValueError("e_local must be a contiguous float64 tensor")
+        B = e_local.shape[0]
+        out = torch.empty_like(e_local) if out is None else out
+        stats = torch.empty(2, dtype=torch.float64, device=e_local.device)
+        _check(self._lib.fn_clip_local_energy(self._h, _ptr(e_local), B, float(width), _ptr(out), _ptr(stats),
+                                              _stream(stream)))
+        return out, stats
+
+    def vmc_iteration(self, cfg: TrainConfig, params, walkers, iteration: int, opt_state, grad, log_psi, e_local,
+                      e_mean=None, accept_count=None, stream=None):
+        """One training iteration (fn_vmc_iteration); every tensor argument is updated in place."""
+        self._check_walkers(params, walkers)
+        self._check_blob(params, grad)
+        if opt_state is not None and (opt_state.dtype != self.dtype or opt_state.numel() != 2 * self.param_count):
+            raise ValueError("opt_state must hold 2 * param_count elements of the blob dtype")
+        B = walkers.shape[0]
+        c = cfg.c_struct()
+        _check(self._lib.fn_vmc_iteration(self._h, C.byref(c), _ptr(params), _ptr(walkers), B, int(iteration),
+                                          _ptr(opt_state), _ptr(grad), _ptr(log_psi), _ptr(e_local), _ptr(e_mean),
+                                          _ptr(accept_count), _stream(stream)))
 
     def profile_enable(self, enable: bool = True):
         _check(self._lib.fn_profile_enable(self._h, 1 if enable else 0))

@@ -530,6 +530,103 @@ fn_status fn_log_psi_vjp(fn_system_t s, const void* d_params, const void* d_walk
   return check_launch(s, "log_psi_vjp");
 }
 
+static bool adam_args_ok(double lr, double beta1, double beta2, double eps) {
+  return std::isfinite(lr) && beta1 >= 0.0 && beta1 < 1.0 && beta2 >= 0.0 && beta2 < 1.0 && eps >= 0.0 &&
+         std::isfinite(eps);
+}
+
+fn_status fn_adam_step(fn_system_t s, void* d_params, const void* d_grad, void* d_m, void* d_v, int64_t t,
+                       double lr, double beta1, double beta2, double eps, void* stream) {
+  if (!s || !d_params || !d_grad || !d_m || !d_v || t < 1 || !adam_args_ok(lr, beta1, beta2, eps)) {
+    set_error("invalid argument"); return FN_ERR_ARG;
+  }
+  fn_status st = ensure_workspace(s, 1);   // holds the device status word
+  if (st != FN_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  dispatch(s, [&](auto m) {
+    launch_adam<decltype(m)>(s, d_params, d_grad, d_m, d_v, t, lr, beta1, beta2, eps, cs);
+    return 0;
+  });
+  return check_launch(s, "adam_step");
+}
+
+fn_status fn_sgd_step(fn_system_t s, void* d_params, const void* d_grad, double lr, void* stream) {
+  if (!s || !d_params || !d_grad || !std::isfinite(lr)) { set_error("invalid argument"); return FN_ERR_ARG; }
+  fn_status st = ensure_workspace(s, 1);
+  if (st != FN_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  dispatch(s, [&](auto m) {
+    launch_sgd<decltype(m)>(s, d_params, d_grad, lr, cs);
+    return 0;
+  });
+  return check_launch(s, "sgd_step");
+}
+
+fn_status fn_clip_local_energy(fn_system_t s, const double* d_e_local, int B, double width, double* d_e_clipped,
+                               double* d_stats, void* stream) {
+  if (!s || !d_e_local || !d_e_clipped || B < 1 || !std::isfinite(width)) {
+    set_error("invalid argument"); return FN_ERR_ARG;
+  }
+  fn_status st = ensure_workspace(s, 1);
+  if (st != FN_OK) return st;
+  launch_clip_energy(s, B, d_e_local, width, d_e_clipped, d_stats, (cudaStream_t)stream);
+  return check_launch(s, "clip_local_energy");
+}
+
+fn_status fn_vmc_iteration(fn_system_t s, const fn_train_config* c, void* d_params, void* d_walkers, int B,
+                           int64_t iteration, void* d_opt_state, void* d_grad, double* d_log_psi, double* d_e_local,
+                           double* d_e_mean, int64_t* d_accept, void* stream) {
+  if (!s || !c || !d_params || !d_walkers || !d_grad || !d_log_psi || !d_e_local || B < 1 || iteration < 0 ||
+      c->n_mcmc_steps < 0 || !(c->step_size >= 0.0) || !std::isfinite(c->clip_width) ||
+      (c->optimizer != FN_OPT_ADAM && c->optimizer != FN_OPT_SGD) || !std::isfinite(c->lr) ||
+      (c->optimizer == FN_OPT_ADAM && (!d_opt_state || !adam_args_ok(c->lr, c->beta1, c->beta2, c->eps)))) {
+    set_error("invalid argument"); return FN_ERR_ARG;
+  }
+  fn_status st = ensure_workspace(s, B);
+  if (st != FN_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  const size_t par_bytes = s->cfg.precision == FN_FP64 ? sizeof(double) : sizeof(float);
+  dispatch(s, [&](auto m) {
+    using Mode = decltype(m);
+    const Shape value = make_shape(s, B, 1);
+    const Shape full = make_shape(s, B, 3 * s->N + 2);
+    launch_prep_params<Mode>(s, d_params, cs);
+    // log|psi| of the persistent walkers under the current parameters
+    launch_forward<Mode>(s, d_walkers, value, false, cs);
+    launch_det_energy<Mode>(s, d_walkers, value, nullptr, d_log_psi, nullptr, false, cs);
+    // Metropolis, step indices iteration * n + k
+    for (int k = 0; k < c->n_mcmc_steps; ++k) {
+      const uint32_t step = (uint32_t)((uint64_t)iteration * (uint64_t)c->n_mcmc_steps + (uint64_t)k);
+      launch_propose<Mode>(s, B, d_walkers, s->ws.walk2, c->step_size, c->seed, step, cs);
+      launch_forward<Mode>(s, s->ws.walk2, value, false, cs);
+      launch_det_energy<Mode>(s, s->ws.walk2, value, nullptr, s->ws.lp2, nullptr, false, cs);
+      launch_accept<Mode>(s, B, d_walkers, s->ws.walk2, d_log_psi, s->ws.lp2, c->seed, step, d_accept, cs);
+    }
+    // local energies (Eqs. 2-3)
+    launch_forward<Mode>(s, d_walkers, full, false, cs);
+    launch_det_energy<Mode>(s, d_walkers, full, d_e_local, nullptr, nullptr, false, cs);
+    // clipping, then the Eq. 6 gradient with the clipped energies held fixed
+    const double* e_used = d_e_local;
+    if (c->clip_width > 0.0) {
+      launch_clip_energy(s, B, d_e_local, c->clip_width, s->ws.scratch_d, nullptr, cs);
+      e_used = s->ws.scratch_d;   // the weights below are formed in place
+    }
+    launch_forward<Mode>(s, d_walkers, value, true, cs);
+    launch_det_energy<Mode>(s, d_walkers, value, nullptr, s->ws.lp2, nullptr, true, cs);
+    launch_energy_weights<Mode>(s, B, e_used, s->ws.scratch_d, d_e_mean, cs);
+    launch_backward<Mode>(s, d_walkers, value, s->ws.scratch_d, d_grad, cs);
+    // parameter update
+    if (c->optimizer == FN_OPT_ADAM) {
+      void* v = (char*)d_opt_state + (size_t)s->P * par_bytes;
+      launch_adam<Mode>(s, d_params, d_grad, d_opt_state, v, iteration + 1, c->lr, c->beta1, c->beta2, c->eps, cs);
+    } else {
+      launch_sgd<Mode>(s, d_params, d_grad, c->lr, cs);
+    }
+    return 0;
+  });
+  return check_launch(s, "vmc_iteration");
+}
+
 fn_status fn_profile_enable(fn_system_t s, int enable) {
   if (!s) { set_error("null system"); return FN_ERR_ARG; }
   if (!s->prof) s->prof = new Profiler();

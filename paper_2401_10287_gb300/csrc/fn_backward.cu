@@ -25,7 +25,9 @@
 namespace fn {
 
 // ---- weights c_w = 2 (E_w - mean) / B -------------------------------------------------
-__global__ void k_energy_weights(int B, const double* __restrict__ e, double* __restrict__ c, double* __restrict__ mean_out) {
+// e and c may be the same buffer: each thread reads e[w] before writing c[w], and only
+// after the barrier that ends the sum.
+__global__ void k_energy_weights(int B, const double* e, double* c, double* __restrict__ mean_out) {
   __shared__ double red[1024];
   double s = 0.0;
   for (int w = threadIdx.x; w < B; w += blockDim.x) s += e[w];

@@ -222,4 +222,13 @@ template <class Mode> void launch_energy_weights(const fn_system* s, int B, cons
 template <class Mode> void launch_backward(const fn_system* s, const void* walkers, const Shape& sh,
                                            const double* weights, void* grad, cudaStream_t st);
 
+// Training loop (fn_optim.cu): parameter updates on the flat blob and local-energy clipping.
+template <class Mode> void launch_adam(const fn_system* s, void* params, const void* grad, void* m, void* v,
+                                       int64_t t, double lr, double beta1, double beta2, double eps,
+                                       cudaStream_t st);
+template <class Mode> void launch_sgd(const fn_system* s, void* params, const void* grad, double lr,
+                                      cudaStream_t st);
+void launch_clip_energy(const fn_system* s, int B, const double* e, double width, double* out, double* stats,
+                        cudaStream_t st);
+
 }  // namespace fn

@@ -13,14 +13,14 @@ namespace fn {
 enum ProfClass {
   kProfPrep = 0, kProfFeatures, kProfPair, kProfPairFull, kProfOrbFix, kProfMeanGemm, kProfLayerValue, kProfLayerFull, kProfOrbValue,
   kProfOrbFull, kProfDetValue, kProfDetFull, kProfSampler, kProfInit, kProfBwdOrb, kProfBwdGemm, kProfBwdPair,
-  kProfBwdMisc, kProfSpinMeans, kProfCount
+  kProfBwdMisc, kProfSpinMeans, kProfOptim, kProfCount
 };
 
 inline const char* prof_name(int c) {
   static const char* names[kProfCount] = {
       "prep_params", "features", "pair_value", "pair_full", "orbital_fixup", "mean_field_gemm", "layer_value", "layer_full",
       "orbitals_value", "orbitals_full", "det_value", "det_full", "sampler", "init",
-      "bwd_orbitals", "bwd_gemm", "bwd_pair", "bwd_misc", "spin_means"};
+      "bwd_orbitals", "bwd_gemm", "bwd_pair", "bwd_misc", "spin_means", "optimizer"};
   return names[c];
 }
 

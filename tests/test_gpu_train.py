@@ -1,0 +1,247 @@
+"""Training loop on the GPU against the oracle: Adam and gradient-descent updates,
+local-energy clipping and whole VMC iterations (log|psi|, Metropolis, Eqs. 2-3, clipping,
+Eq. 6, update) on persistent walkers."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import ansatz, mcmc, optim
+from gpu_helpers import make_pair, need_gpu, oracle_params, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+    yield
+    torch.cuda.synchronize()
+
+
+def _blob_inputs(P, seed, dtype):
+    rs = np.random.default_rng(seed)
+    p = rs.standard_normal(P)
+    gs = [rs.standard_normal(P) * np.exp(rs.uniform(-8, 2, P)) for _ in range(3)]
+    for g in gs:
+        g[rs.choice(P, P // 50, replace=False)] = 0.0          # exact zeros: m = v = 0, no move
+    return [x.astype(dtype).astype(np.float64) for x in [p] + gs]
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_adam_steps_match_oracle(prec):
+    """Three Adam steps on a seeded blob (gradients spanning 10 decades, 2 % exact zeros).
+    beta1 m + (1 - beta1) g can cancel, so the moment error is bounded by the running sum of
+    magnitudes S_t = beta1 S_(t-1) + (1 - beta1) |g_t| (a few units of the last place of the
+    blob dtype times S_t), not by |m|; the parameter error by that bound through the update."""
+    sysm = W.n2()
+    net, gpu = make_pair(sysm, W.Ansatz(2, 32, 8, 2, "aniso"), prec)
+    npdt = np.float64 if prec == 0 else np.float32
+    dt = torch.float64 if prec == 0 else torch.float32
+    ulp = 2.0 ** -52 if prec == 0 else 2.0 ** -23
+    p, *gs = _blob_inputs(gpu.param_count, 11, npdt)
+    lr, b1, b2, eps = 3e-3, 0.9, 0.99, 1e-8
+    pd = to_dev(p, dt)
+    md = torch.zeros(gpu.param_count, dtype=dt, device="cuda")
+    vd = torch.zeros_like(md)
+    po, mo, vo = p.copy(), np.zeros_like(p), np.zeros_like(p)
+    S = np.zeros_like(p)
+    for t, g in enumerate(gs, start=1):
+        gpu.adam_step(pd, to_dev(g, dt), md, vd, t, lr, b1, b2, eps)
+        gpu.sync()
+        po, mo, vo = optim.adam_step(po, g, mo, vo, t, lr, b1, b2, eps)
+        S = b1 * S + (1 - b1) * np.abs(g)
+        assert np.all(np.abs(md.cpu().numpy() - mo) <= 8 * t * ulp * S)
+        np.testing.assert_allclose(vd.cpu().numpy(), vo, rtol=8 * t * ulp, atol=0)
+        np.testing.assert_allclose(pd.cpu().numpy(), po, rtol=2 * ulp, atol=(1e-12 if prec == 0 else 1e-4) * lr)
+    moved = np.abs(pd.cpu().numpy() - p) > 0
+    assert moved.sum() >= 0.97 * gpu.param_count
+
+
+def test_sgd_step_matches_oracle():
+    sysm = W.h2()
+    net, gpu = make_pair(sysm, W.Ansatz(2, 32, 8, 1, "iso"), 0)
+    p, g, _, _ = _blob_inputs(gpu.param_count, 3, np.float64)
+    pd = to_dev(p, torch.float64)
+    gpu.sgd_step(pd, to_dev(g, torch.float64), 0.125)
+    gpu.sync()
+    np.testing.assert_allclose(pd.cpu().numpy(), optim.sgd_step(p, g, 0.125), rtol=1e-15, atol=1e-300)
+
+
+def _energies(B, seed):
+    """N2-like local energies with heavy tails, duplicates and a few extreme outliers."""
+    rs = np.random.default_rng(seed)
+    e = -109.4 + 0.8 * rs.standard_cauchy(B)
+    if B > 8:
+        e[rs.choice(B, B // 8, replace=False)] = e[0]            # ties, including at the median
+        e[rs.integers(B)] = 1e6
+        e[rs.integers(B)] = -1e6
+    return e
+
+
+@pytest.mark.parametrize("B", [1, 2, 3, 31, 1000, 1024, 1025, 4097, 40000])
+@pytest.mark.parametrize("width", [0.0, 0.5, 5.0])
+def test_clip_local_energy_matches_oracle(B, width):
+    sysm = W.h2()
+    _, gpu = make_pair(sysm, W.Ansatz(2, 32, 8, 1, "iso"), 1)
+    e = _energies(B, B + int(10 * width))
+    ref, centre, spread = optim.clip_local_energy(e, width)
+    ed = torch.as_tensor(e).cuda()
+    out, stats = gpu.clip_local_energy(ed, width)
+    gpu.sync()
+    st = stats.cpu().numpy()
+    assert st[0] == centre                      # the median is a batch member: bit-exact
+    assert st[1] == pytest.approx(spread, rel=1e-12, abs=1e-300)
+    o = out.cpu().numpy()
+    inside = np.abs(e - centre) < width * spread * (1 - 1e-9) if width > 0 else np.ones(B, bool)
+    np.testing.assert_array_equal(o[inside], e[inside])
+    np.testing.assert_allclose(o, ref, rtol=1e-12, atol=0)
+    # in place
+    gpu.clip_local_energy(ed, width, out=ed)
+    gpu.sync()
+    np.testing.assert_array_equal(ed.cpu().numpy(), o)
+
+
+def test_clip_constant_batch_and_bad_arguments():
+    import paper_2401_10287_gb300 as P
+    _, gpu = make_pair(W.h2(), W.Ansatz(2, 32, 8, 1, "iso"), 1)
+    e = torch.full((777,), -1.25, dtype=torch.float64, device="cuda")
+    out, stats = gpu.clip_local_energy(e, 5.0)
+    gpu.sync()
+    assert stats.cpu().tolist() == [-1.25, 0.0]
+    assert torch.equal(out, e)
+    with pytest.raises(P.FnError) as err:
+        gpu.clip_local_energy(e[:0], 5.0)
+    assert err.value.code == 1
+    with pytest.raises(P.FnError) as err:
+        gpu.clip_local_energy(e, float("nan"))
+    assert err.value.code == 1
+
+
+def test_adam_non_finite_gradient_is_reported():
+    """A NaN gradient (made on the host) leaves a NaN parameter; fn_sync reports it."""
+    import paper_2401_10287_gb300 as P
+    _, gpu = make_pair(W.h2(), W.Ansatz(2, 32, 8, 1, "iso"), 1)
+    p = torch.zeros(gpu.param_count, dtype=torch.float32, device="cuda")
+    g = torch.ones_like(p)
+    g[5] = float("nan")
+    m, v = torch.zeros_like(p), torch.zeros_like(p)
+    gpu.adam_step(p, g, m, v, 1, 1e-3)
+    with pytest.raises(P.FnError) as err:
+        gpu.sync()
+    assert err.value.code == 5
+    with pytest.raises(P.FnError) as err:
+        gpu.adam_step(p, g, m, v, 0, 1e-3)          # step count starts at 1
+    assert err.value.code == 1
+    with pytest.raises(P.FnError) as err:
+        gpu.adam_step(p, g, m, v, 1, 1e-3, beta1=1.0)
+    assert err.value.code == 1
+
+
+def test_vmc_iterations_fp64_match_oracle_trajectory():
+    """Four iterations of the whole loop (Adam, clipping on) in FP64 on H2 with a network of
+    228 parameters, against the oracle's loop whose gradient is Richardson-extrapolated
+    central differences.  eps = 1e-3 keeps Adam's normalisation of gradient entries far
+    below eps from amplifying the differences' truncation error."""
+    import paper_2401_10287_gb300 as P
+    sysm = W.h2()
+    ans = W.Ansatz(2, 4, 2, 1, "iso")
+    net, gpu = make_pair(sysm, ans, 0)
+    p0 = oracle_params(net, 0, 0.05)
+    r0, _ = mcmc.init_walkers(sysm.nuclei, sysm.charges, 1, 1, None, 24, 1, 1.0)
+    cfg = P.TrainConfig(n_mcmc_steps=4, step_size=0.3, seed=3, clip_width=2.0, optimizer="adam", lr=0.01,
+                        eps=1e-3)
+    state = optim.TrainState(p0, r0)
+    tr = P.Trainer(gpu, to_dev(p0, torch.float64), to_dev(r0, torch.float64), cfg)
+    accepted = 0
+    for it in range(4):
+        out = optim.train_iteration(net, state, sysm.nuclei, sysm.charges, seed=3, n_mcmc=4, step_size=0.3,
+                                    clip_width=2.0, optimizer="adam", lr=0.01, eps=1e-3)
+        tr.step()
+        gpu.sync()
+        np.testing.assert_allclose(tr.walkers.cpu().numpy(), state.walkers, rtol=0, atol=1e-9)
+        e = tr.e_local.cpu().numpy()
+        np.testing.assert_allclose(e, out["e_local"], rtol=1e-7, atol=1e-7)
+        np.testing.assert_allclose(tr.log_psi.cpu().numpy(), out["log_psi"], rtol=0, atol=1e-8)
+        assert tr.e_mean.item() == pytest.approx(out["e_clipped"].mean(), abs=1e-7)
+        g = tr.grad.cpu().numpy()
+        np.testing.assert_allclose(g, out["grad"], rtol=1e-5, atol=1e-6 * max(1.0, np.abs(out["grad"]).max()))
+        np.testing.assert_allclose(tr.params.cpu().numpy(), state.params, rtol=0, atol=1e-6)
+        np.testing.assert_allclose(tr.opt_state[: gpu.param_count].cpu().numpy(), state.m, rtol=1e-4,
+                                   atol=1e-6 * max(1.0, np.abs(state.m).max()))
+        accepted += int(out["accepted"].sum())
+    assert tr.accepted.item() == accepted > 0
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_vmc_iteration_equals_its_separate_calls(prec):
+    """fn_vmc_iteration is the chain of the public calls: log_psi, mcmc_steps with step
+    offset t*n, local_energy, clip_local_energy, energy_grad and adam_step."""
+    import paper_2401_10287_gb300 as P
+    sysm = W.n2()
+    net, gpu = make_pair(sysm, W.Ansatz(2, 32, 8, 2, "aniso"), prec)
+    B = 96
+    p0 = gpu.init_params(5)
+    w0, _ = gpu.init_walkers(B, 6, 1.0)
+    cfg = P.TrainConfig(n_mcmc_steps=3, step_size=0.05, seed=8, clip_width=3.0, lr=1e-3)
+    tr = P.Trainer(gpu, p0.clone(), w0.clone(), cfg)
+    p, w = p0.clone(), w0.clone()
+    m = torch.zeros(gpu.param_count, dtype=gpu.dtype, device="cuda")
+    v = torch.zeros_like(m)
+    acc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for t in range(2):
+        tr.step()
+        lp, _ = gpu.log_psi(p, w)
+        gpu.mcmc_steps(p, w, lp, 3, 0.05, 8, step_offset=3 * t, accept_count=acc)
+        e, _, _ = gpu.local_energy(p, w)
+        ec, _ = gpu.clip_local_energy(e, 3.0)
+        g, mean = gpu.energy_grad(p, w, ec)
+        gpu.adam_step(p, g, m, v, t + 1, 1e-3)
+        gpu.sync()
+        assert torch.equal(tr.walkers, w)
+        assert torch.equal(tr.log_psi, lp)
+        assert torch.equal(tr.e_local, e)
+        assert tr.e_mean.item() == mean.item()
+        torch.testing.assert_close(tr.grad, g, rtol=1e-4, atol=1e-6 * g.abs().max().item())
+        torch.testing.assert_close(tr.params, p, rtol=0, atol=1e-5 * 1e-3)
+        # the split-K backward sums with atomics, so the two gradients may differ in their last
+        # bits: continue both chains from the same state
+        p.copy_(tr.params)
+        m.copy_(tr.opt_state[: gpu.param_count])
+        v.copy_(tr.opt_state[gpu.param_count:])
+    assert tr.accepted.item() == acc.item() > 0
+
+
+H2_EXACT_HA = -1.174476    # H2 at 1.4 bohr, Born-Oppenheimer, non-relativistic (Kolos & Wolniewicz)
+
+
+def _train(sysm, prec, lr, iters, B=4096):
+    import paper_2401_10287_gb300 as P
+    gpu = P.System(sysm.nuclei, sysm.charges, sysm.n_up, sysm.n_down,
+                   P.NetConfig.from_ansatz(W.Ansatz(2, 32, 8, 1, "iso"), prec))
+    p = gpu.init_params(0)
+    w, _ = gpu.init_walkers(B, 1, 1.0)
+    P.Trainer(gpu, p, w, P.TrainConfig(n_mcmc_steps=10, step_size=0.3, seed=3, optimizer="sgd", lr=0.0)).run(20)
+    tr = P.Trainer(gpu, p, w, P.TrainConfig(n_mcmc_steps=10, step_size=0.3, seed=2, clip_width=5.0, lr=lr))
+    means = torch.empty(iters, dtype=torch.float64, device="cuda")
+    for k in range(iters):
+        tr.step()
+        means[k] = tr.e_local.mean()
+    gpu.sync()
+    return means.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_training_h2_reaches_the_exact_energy(prec):
+    """The whole loop against physics: from random parameters, 1000 Adam iterations on 4096
+    walkers bring the mean local energy of H2 to within 2.5 mHa of the exact ground-state
+    energy, and not below it beyond the sampling noise (variational principle)."""
+    e = _train(W.h2(), prec, 1e-2, 1000)
+    tail = e[-200:].mean()
+    assert e[:20].mean() - tail > 0.05
+    assert H2_EXACT_HA - 1.5e-3 <= tail <= H2_EXACT_HA + 2.5e-3, tail
+
+
+def test_training_hydrogen_atom_reaches_minus_one_half():
+    e = _train(W.hydrogen_atom(), 1, 3e-3, 800)
+    assert abs(e[-200:].mean() + 0.5) <= 1e-3, e[-200:].mean()
