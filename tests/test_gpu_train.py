@@ -196,19 +196,20 @@ def test_vmc_iteration_equals_its_separate_calls(prec):
         e, _, _ = gpu.local_energy(p, w)
         ec, _ = gpu.clip_local_energy(e, 3.0)
         g, mean = gpu.energy_grad(p, w, ec)
-        gpu.adam_step(p, g, m, v, t + 1, 1e-3)
         gpu.sync()
         assert torch.equal(tr.walkers, w)
         assert torch.equal(tr.log_psi, lp)
         assert torch.equal(tr.e_local, e)
         assert tr.e_mean.item() == mean.item()
+        # the split-K backward sums with atomics, so two evaluations of the gradient may differ
+        # in their last bits, and Adam's g / (|g| + eps) magnifies that for entries far below
+        # eps: compare the gradients to a tolerance, then update with the fused call's gradient
         torch.testing.assert_close(tr.grad, g, rtol=1e-4, atol=1e-6 * g.abs().max().item())
-        torch.testing.assert_close(tr.params, p, rtol=0, atol=1e-5 * 1e-3)
-        # the split-K backward sums with atomics, so the two gradients may differ in their last
-        # bits: continue both chains from the same state
-        p.copy_(tr.params)
-        m.copy_(tr.opt_state[: gpu.param_count])
-        v.copy_(tr.opt_state[gpu.param_count:])
+        gpu.adam_step(p, tr.grad.clone(), m, v, t + 1, 1e-3)
+        gpu.sync()
+        assert torch.equal(tr.params, p)
+        assert torch.equal(tr.opt_state[: gpu.param_count], m)
+        assert torch.equal(tr.opt_state[gpu.param_count:], v)
     assert tr.accepted.item() == acc.item() > 0
 
 
