@@ -102,7 +102,7 @@ def test_autograd_function_matches_library():
     g, mean = gpu.energy_grad(params.detach(), walkers, e)
     # split-K atomics reorder the FP64 sums between calls: equal to rounding
     torch.testing.assert_close(params.grad, g, rtol=1e-10, atol=1e-12)
-    assert abs(float(loss) - float(e.mean())) < 1e-12
+    assert abs(float(loss.detach()) - float(e.mean())) < 1e-12
 
 
 def test_log_psi_vjp_weights():
