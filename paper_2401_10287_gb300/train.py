@@ -26,6 +26,8 @@ class Trainer:
         self.e_mean = torch.empty(1, dtype=torch.float64, device=dev)
         self.accepted = torch.zeros(1, dtype=torch.int64, device=dev)
         self.iteration = 0
+        # the zero fills above run on the current stream; iterations may be enqueued on another
+        torch.cuda.current_stream(dev).synchronize()
 
     def step(self, stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
         """Enqueues one iteration; returns the device tensor holding the mean (clipped) energy."""
@@ -35,9 +37,12 @@ class Trainer:
         return self.e_mean
 
     def run(self, n_iterations: int, stream: Optional[torch.cuda.Stream] = None) -> List[float]:
-        """n iterations; the mean energies are gathered on the device and read back once."""
+        """n iterations; the mean energies are gathered on the device (on the same stream as the
+        iterations) and read back once."""
+        stream = stream if stream is not None else torch.cuda.current_stream(self.walkers.device)
         means = torch.empty(n_iterations, dtype=torch.float64, device=self.walkers.device)
-        for k in range(n_iterations):
-            means[k : k + 1].copy_(self.step(stream))
+        with torch.cuda.stream(stream):
+            for k in range(n_iterations):
+                means[k : k + 1].copy_(self.step(stream))
         self.system.sync(stream=stream)
         return means.cpu().tolist()
