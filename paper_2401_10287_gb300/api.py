@@ -74,6 +74,11 @@ class TrainConfig:
                                  float(self.beta2), float(self.eps))
 
 
+def _check_f64(t: torch.Tensor, n: int, name: str):
+    if t.dtype != torch.float64 or t.numel() != n or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 tensor of {n} elements")
+
+
 def _ptr(t: Optional[torch.Tensor]):
     return None if t is None else C.c_void_p(t.data_ptr())
 
@@ -234,6 +239,7 @@ class System:
             raise ValueError("e_local must be a contiguous float64 tensor")
         B = e_local.shape[0]
         out = torch.empty_like(e_local) if out is None else out
+        _check_f64(out, B, "out")
         stats = torch.empty(2, dtype=torch.float64, device=e_local.device)
         _check(self._lib.fn_clip_local_energy(self._h, _ptr(e_local), B, float(width), _ptr(out), _ptr(stats),
                                               _stream(stream)))
@@ -247,6 +253,12 @@ class System:
         if opt_state is not None and (opt_state.dtype != self.dtype or opt_state.numel() != 2 * self.param_count):
             raise ValueError("opt_state must hold 2 * param_count elements of the blob dtype")
         B = walkers.shape[0]
+        _check_f64(log_psi, B, "log_psi")
+        _check_f64(e_local, B, "e_local")
+        if e_mean is not None:
+            _check_f64(e_mean, 1, "e_mean")
+        if accept_count is not None and (accept_count.dtype != torch.int64 or accept_count.numel() != 1):
+            raise ValueError("accept_count must be a one-element int64 tensor")
         c = cfg.c_struct()
         _check(self._lib.fn_vmc_iteration(self._h, C.byref(c), _ptr(params), _ptr(walkers), B, int(iteration),
                                           _ptr(opt_state), _ptr(grad), _ptr(log_psi), _ptr(e_local), _ptr(e_mean),
