@@ -81,7 +81,15 @@ typedef struct fn_system* fn_system_t;
  * (integer-valued), n_up + n_down electrons (1..32 in total, each spin <= 16),
  * and a network configuration.  The ionic charge t = sum Z - n_up - n_down is
  * derived.  The default electron assignment is Algorithm 1 with partial
- * charges t/M for every atom.  Returns FN_ERR_EMPTY for zero electrons.     */
+ * charges t/M for every atom.  Returns FN_ERR_EMPTY for zero electrons.
+ * The per-walker kernels keep one walker's pair activations (N^2 rows) and its
+ * 2 n_dets determinant matrices in shared memory, so the sizes above combine
+ * into smaller limits on a device with 227 KB per CTA: FN_FP32 reaches 32
+ * electrons, and n_dets 32 at 16 electrons of one spin; FN_FP64 reaches 29
+ * electrons with 2 layers (25 with 8); FN_BF16_MIXED reaches 29 electrons;
+ * FN_FP64 and FN_BF16_MIXED reach n_dets 16 at 16 electrons of one spin.  A
+ * configuration that does not fit returns FN_ERR_UNSUPPORTED, and
+ * fn_last_error() names the stage and the bytes it needs.                   */
 fn_status fn_create_system(const double* h_nuclei, const double* h_charges, int n_nuclei,
                            int n_up, int n_down, const fn_net_config* cfg, fn_system_t* out);
 fn_status fn_destroy_system(fn_system_t sys);

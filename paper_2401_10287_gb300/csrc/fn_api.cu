@@ -288,6 +288,33 @@ static fn_status ensure_workspace(fn_system* s, int B) {
   return FN_OK;
 }
 
+// The per-walker kernels keep one walker's pair activations or determinant matrices in
+// shared memory; a configuration whose largest such block exceeds the device's per-CTA
+// maximum cannot be launched.  Returns the first stage that does not fit (or nullptr) and
+// its byte count.
+static const char* shared_memory_overflow(const fn_system* s, size_t limit, size_t* need) {
+  const int N = s->N, L = s->cfg.n_layers, K = s->cfg.n_dets, nmax = std::max(s->n_up, s->n_dn);
+  const bool bf16 = s->cfg.precision == FN_BF16_MIXED;
+  const int cmp = s->cfg.precision == FN_FP64 ? 8 : 4;
+  const int det = s->cfg.precision == FN_FP32 ? 4 : 8;
+  struct Stage { const char* name; size_t bytes; };
+  const Stage stages[] = {
+      {"two-electron stream, value pass", bf16 ? smem_pair_value_mma(N, L) : smem_pair_value(cmp, N, L)},
+      {"two-electron stream, local-energy pass",
+       bf16 ? smem_pair_full_mma(N, L, pair_full_mma_ib(N)) : smem_pair_full(cmp, N, L, pair_full_ib(N))},
+      {"two-electron stream, gradient", (bf16 && L > 1) ? smem_pair_bwd_mma(N) : 0},
+      {"determinant stage, local energy", smem_det_energy(det, nmax, N, K)},
+      {"determinant stage, value pass", nmax > 8 ? smem_det_value(det, nmax, K, false) : 0},
+      {"determinant stage, gradient", smem_det_value(det, nmax, K, true)},
+  };
+  for (const Stage& st : stages)
+    if (st.bytes > limit) {
+      *need = st.bytes;
+      return st.name;
+    }
+  return nullptr;
+}
+
 static fn_status check_launch(fn_system* s, const char* what) {
   if (s->host_error != FN_OK) {
     const fn_status e = s->host_error;
@@ -352,8 +379,21 @@ fn_status fn_create_system(const double* h_nuclei, const double* h_charges, int 
   fn_status st = ionic_counts(s->charges, nullptr, s->total_charge, &s->counts);
   if (st != FN_OK) { delete s; return st; }
   spin_assign(s->counts, n_up, n_down, &s->elec_atom);
+  int smem_optin = 0;
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+  if (e == cudaSuccess) {
+    size_t need = 0;
+    if (const char* stage = shared_memory_overflow(s, (size_t)smem_optin, &need)) {
+      set_error(std::string(stage) + ": " + std::to_string(s->n_up) + "+" + std::to_string(s->n_dn) +
+                " electrons, " + std::to_string(cfg->n_dets) + " determinants and " + std::to_string(cfg->n_layers) +
+                " layers need " + std::to_string(need) + " bytes of shared memory per CTA; the device allows " +
+                std::to_string(smem_optin));
+      delete s;
+      return FN_ERR_UNSUPPORTED;
+    }
+  }
   if (e == cudaSuccess) e = cudaMalloc(&s->d_nuclei, sizeof(double) * (3 * n_nuclei + n_nuclei));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_elec_atom, sizeof(int) * kMaxElectrons);
   if (e != cudaSuccess) { fn_status r = cuda_status(e, "create_system"); delete s; return r; }

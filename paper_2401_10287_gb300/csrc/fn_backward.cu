@@ -361,7 +361,6 @@ __global__ void __launch_bounds__(128) k_pair_bwd(const Wlk* __restrict__ r, Sha
 // the weight gradient dW = dz^T g^l (pairs as the contraction dimension; the four warps split
 // the 32 x 32 output) and the input gradient dz W (pairs as rows), then one coalesced pass adds
 // dG^{l+1} (residual, l >= 1) and the layer input's spin-mean gradient, as k_pair_bwd does.
-constexpr int kBwdWLd = 40;
 
 template <typename Wlk>
 __global__ void __launch_bounds__(128) k_pair_bwd_mma(const Wlk* __restrict__ r, Shape sh, PairBwdArgs a) {
@@ -705,7 +704,7 @@ void launch_backward(const fn_system* s, const void* walkers, const Shape& sh, c
       a.dG = ws.dG; a.dX = dX; a.ldx = d.ldx; a.col0 = d.d_h;
       ProfScope ps(s->prof, kProfBwdPair, st);
       if (Mode::kMode == FN_BF16_MIXED) {
-        const size_t smem = 2 * 32 * kBwdWLd * 2 + (size_t)2 * ((N * N + 15) & ~15) * 33 * 4;
+        const size_t smem = smem_pair_bwd_mma(N);
         cudaFuncSetAttribute(k_pair_bwd_mma<Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_pair_bwd_mma<Wlk><<<sh.B, 128, smem, st>>>(r, sh, a);
       } else {

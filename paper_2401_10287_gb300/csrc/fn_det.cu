@@ -555,12 +555,10 @@ void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh,
   a.v_nn = s->v_nn;
   a.status = s->ws.status;
   const bool full = sh.T > 1 && e_local != nullptr;
-  const int nmax = std::max(s->n_up, s->n_dn), NC = 3 * s->N, K = s->cfg.n_dets;
+  const int nmax = std::max(s->n_up, s->n_dn), K = s->cfg.n_dets;
   ProfScope ps(s->prof, full ? kProfDetFull : kProfDetValue, st);
   if (full) {
-    const int ST = (int)round_up(2 * K, 32);
-    const size_t smem = sizeof(Det) * ((size_t)2 * nmax * nmax * ST + (size_t)nmax * ST + 4 * K + 4 * K * NC +
-                                       2 * K + K * NC + 2 * K + 128) + sizeof(int) * (size_t)nmax * ST;
+    const size_t smem = smem_det_energy(sizeof(Det), nmax, s->N, K);
     cudaFuncSetAttribute(k_det_energy<Det, Wlk, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_det_energy<Det, Wlk, PhiT><<<sh.B, 128, smem, st>>>((const Wlk*)walkers, s->d_nuclei, sh, a);
   } else if (!keep_inverse && nmax <= 8) {
@@ -568,9 +566,7 @@ void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh,
     k_det_value_small<Det, PhiT><<<(unsigned)((sh.B + per_cta - 1) / per_cta), 128, 0, st>>>(sh, a);
   } else {
     const int threads = (int)round_up(2 * K, 32);
-    const bool inv = keep_inverse;
-    const size_t vsmem = sizeof(Det) * ((size_t)(inv ? 2 : 1) * nmax * nmax * threads + (size_t)nmax * threads +
-                                        5 * K) + sizeof(int) * (size_t)nmax * threads;
+    const size_t vsmem = smem_det_value(sizeof(Det), nmax, K, keep_inverse);
     cudaFuncSetAttribute(k_det_value<Det, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem);
     k_det_value<Det, PhiT><<<sh.B, threads, vsmem, st>>>(sh, a);
   }

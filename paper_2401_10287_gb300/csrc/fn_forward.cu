@@ -244,8 +244,6 @@ struct PairArgs {
   int L, h2;
 };
 
-constexpr int kMaxH2 = 32;
-
 // Stage W_l^T [d_g][h2] and c_l of every pair layer in shared memory.
 template <typename Cmp>
 __device__ void stage_pair_weights(const PairArgs& a, Cmp* sW, Cmp* sc) {
@@ -306,7 +304,6 @@ __device__ __forceinline__ void pair_matvec(const Cmp* __restrict__ sWl, const C
 // their partners j.  Per layer every pair's rows are staged in shared memory; from there
 // the CTA writes the spin means over j (value, Laplacian, d/dr_i) and the d/dr_j slabs
 // (-d/dr_i / n_spin) to the layer input, adjacent columns from adjacent threads.
-constexpr int kPairLanes = 5, kPairGroups = 6;
 
 template <typename Act, typename Cmp, typename Wlk>
 __global__ void __launch_bounds__(256) k_pair_full(const Wlk* __restrict__ r, Shape sh, PairArgs a, int ib) {
@@ -534,7 +531,6 @@ __global__ void k_spin_means_bf16(Shape sh, const __nv_bfloat16* __restrict__ Y,
 // parts and the three leading products are accumulated (about 16 significant bits, the
 // precision the BF16 storage keeps for the pair means).  One CTA per walker, 4 warps over
 // 16-pair row tiles; the pair activations stay in shared memory (FP32) between layers.
-constexpr int kPairWLd = 40;   // bf16 row stride of the staged weights: conflict-free fragment loads
 
 template <typename Wlk>
 __global__ void __launch_bounds__(128) k_pair_value_mma(const Wlk* __restrict__ r, Shape sh, PairArgs a) {
@@ -1109,40 +1105,29 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
       if (l < L - 1) { pa.W[l] = prep + s->prep.W[l]; pa.c[l] = prep + s->prep.c[l]; }
       pa.gstore[l] = (keep && l >= 1) ? ws.gpair[l] : nullptr;
     }
-    const size_t wbytes = sizeof(Cmp) * ((L - 1) * kMaxH2 * kMaxH2 + (L - 1) * kMaxH2);
     ProfScope ps(s->prof, full ? kProfPairFull : kProfPair, st);
     if (full) {
-      // electrons per CTA: the fewest warps per walker with at most 8 warps per CTA
-      const int per_warp = kPairGroups;
-      int ib = 1, best = INT32_MAX;
-      for (int c = 1; c <= sh.N && c * sh.N <= 8 * per_warp; ++c) {
-        const int full = sh.N / c, rem = sh.N % c;
-        const int warps = full * ((c * sh.N + per_warp - 1) / per_warp) + (rem ? (rem * sh.N + per_warp - 1) / per_warp : 0);
-        if (warps <= best) { best = warps; ib = c; }
-      }
-      const int warps = (ib * sh.N + per_warp - 1) / per_warp;
+      const int ib = pair_full_ib(sh.N);
+      const int warps = (ib * sh.N + kPairGroups - 1) / kPairGroups;
       if (Mode::kMode == FN_BF16_MIXED) {
-        // electrons per CTA: at most 256 jet rows (5 per pair)
-        const int ibm = std::max(1, std::min(sh.N, 256 / (5 * sh.N)));
-        const int rows_p = (ibm * sh.N * 5 + 15) & ~15;
-        const size_t smem_m = (size_t)(L - 1) * (2 * 32 * kPairWLd * 2 + 32 * 4) + (size_t)2 * rows_p * 33 * 4;
+        const int ibm = pair_full_mma_ib(sh.N);
+        const size_t smem_m = smem_pair_full_mma(sh.N, L, ibm);
         const int64_t blocks_m = (int64_t)sh.B * ((sh.N + ibm - 1) / ibm);
         cudaFuncSetAttribute(k_pair_full_mma<Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
         k_pair_full_mma<Wlk><<<(unsigned)blocks_m, 256, smem_m, st>>>(r, sh, pa, ibm);
       } else {
-      const size_t smem = wbytes + sizeof(Cmp) * ib * sh.N * 5 * 33;
+      const size_t smem = smem_pair_full(sizeof(Cmp), sh.N, L, ib);
       const int64_t blocks = (int64_t)sh.B * ((sh.N + ib - 1) / ib);
       cudaFuncSetAttribute(k_pair_full<Act, Cmp, Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_pair_full<Act, Cmp, Wlk><<<(unsigned)blocks, 32 * warps, smem, st>>>(r, sh, pa, ib);
       }
     } else {
       if (Mode::kMode == FN_BF16_MIXED) {
-        const int L1 = L - 1, npp = (sh.N * sh.N + 15) & ~15;
-        const size_t smem = (size_t)L1 * (2 * 32 * kPairWLd * 2 + 32 * 4) + (size_t)npp * 33 * 4;
+        const size_t smem = smem_pair_value_mma(sh.N, L);
         cudaFuncSetAttribute(k_pair_value_mma<Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_pair_value_mma<Wlk><<<(unsigned)sh.B, 128, smem, st>>>(r, sh, pa);
       } else {
-        const size_t smem = wbytes + sizeof(Cmp) * sh.N * sh.N * 33;
+        const size_t smem = smem_pair_value(sizeof(Cmp), sh.N, L);
         const int threads = (int)std::min<int64_t>(512, round_up((int64_t)sh.N * sh.N, 32));
         cudaFuncSetAttribute(k_pair_value<Act, Cmp, Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_pair_value<Act, Cmp, Wlk><<<(unsigned)sh.B, threads, smem, st>>>(r, sh, pa);

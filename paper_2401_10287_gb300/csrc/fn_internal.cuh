@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -62,6 +63,60 @@ struct ModeBF16 {
 };
 
 __host__ __device__ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// ---- dynamic shared memory of the per-walker kernels ------------------------------
+// One function per launch; the launchers and fn_create_system both use them, so a
+// configuration whose kernels would need more than the device's per-CTA maximum is
+// rejected when the system is created instead of failing at its first launch.
+constexpr int kMaxH2 = 32;       // widest two-electron stream
+constexpr int kPairLanes = 5, kPairGroups = 6;   // k_pair_full: 5 lanes per pair, 6 pairs per warp
+constexpr int kPairWLd = 40;     // bf16 row stride of staged pair weights: conflict-free fragment loads
+constexpr int kBwdWLd = 40;      // the same for the pair backward
+
+inline size_t pair_weight_bytes(int cmp_bytes, int L) {
+  return (size_t)cmp_bytes * ((L - 1) * kMaxH2 * kMaxH2 + (L - 1) * kMaxH2);
+}
+// k_pair_value (FP32/FP64): staged weights and every pair activation of one walker
+inline size_t smem_pair_value(int cmp_bytes, int N, int L) {
+  return pair_weight_bytes(cmp_bytes, L) + (size_t)cmp_bytes * N * N * 33;
+}
+// k_pair_value_mma (BF16)
+inline size_t smem_pair_value_mma(int N, int L) {
+  return (size_t)(L - 1) * (2 * 32 * kPairWLd * 2 + 32 * 4) + (size_t)((N * N + 15) & ~15) * 33 * 4;
+}
+// k_pair_full (FP32/FP64): electrons per CTA, the fewest warps per walker with at most 8 warps per CTA
+inline int pair_full_ib(int N) {
+  int ib = 1, best = 0x7fffffff;
+  for (int c = 1; c <= N && c * N <= 8 * kPairGroups; ++c) {
+    const int full = N / c, rem = N % c;
+    const int warps = full * ((c * N + kPairGroups - 1) / kPairGroups) + (rem ? (rem * N + kPairGroups - 1) / kPairGroups : 0);
+    if (warps <= best) { best = warps; ib = c; }
+  }
+  return ib;
+}
+inline size_t smem_pair_full(int cmp_bytes, int N, int L, int ib) {
+  return pair_weight_bytes(cmp_bytes, L) + (size_t)cmp_bytes * ib * N * 5 * 33;
+}
+// k_pair_full_mma (BF16): electrons per CTA, at most 256 jet rows (5 per pair)
+inline int pair_full_mma_ib(int N) { return std::max(1, std::min(N, 256 / (5 * N))); }
+inline size_t smem_pair_full_mma(int N, int L, int ibm) {
+  const int rows_p = (ibm * N * 5 + 15) & ~15;
+  return (size_t)(L - 1) * (2 * 32 * kPairWLd * 2 + 32 * 4) + (size_t)2 * rows_p * 33 * 4;
+}
+// k_pair_bwd_mma (BF16)
+inline size_t smem_pair_bwd_mma(int N) { return 2 * 32 * kBwdWLd * 2 + (size_t)2 * ((N * N + 15) & ~15) * 33 * 4; }
+// k_det_energy: every (determinant, spin) matrix of one walker with its 3N tangent traces
+inline size_t smem_det_energy(int det_bytes, int nmax, int N, int K) {
+  const int ST = (int)round_up(2 * K, 32), NC = 3 * N;
+  return (size_t)det_bytes * ((size_t)2 * nmax * nmax * ST + (size_t)nmax * ST + 4 * K + 4 * K * NC + 2 * K + K * NC +
+                              2 * K + 128) + sizeof(int) * (size_t)nmax * ST;
+}
+// k_det_value (value passes with more than 8 electrons of a spin, and the gradient's pass with inverses)
+inline size_t smem_det_value(int det_bytes, int nmax, int K, bool inv) {
+  const int threads = (int)round_up(2 * K, 32);
+  return (size_t)det_bytes * ((size_t)(inv ? 2 : 1) * nmax * nmax * threads + (size_t)nmax * threads + 5 * K) +
+         sizeof(int) * (size_t)nmax * threads;
+}
 
 // ---- geometry of one call ----------------------------------------------------------
 struct Shape {
