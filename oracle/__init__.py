@@ -16,6 +16,9 @@ Modules
             local energy (Eqs. 2-3), finite-difference Laplacian.
   mcmc      Metropolis-Hastings on |psi|^2.
   grad      VMC energy gradient (Eq. 6) by central finite differences.
+  optim     Adam, gradient descent, local-energy clipping and the training iteration.
+  scf       STO-6G (fitted here) UHF and Mulliken charges, the partial charges of
+            Algorithm 1.
 
 Parity status: every function is pinned by tests under ``tests/`` (closed
 forms, invariants, brute force, finite differences, library routines).  The
