@@ -257,6 +257,18 @@ fn_status fn_vmc_iteration(fn_system_t sys, const fn_train_config* cfg, void* d_
                            double* d_log_psi, double* d_e_local, double* d_e_mean, int64_t* d_accept,
                            void* stream);
 
+/* Mulliken partial charges for Algorithm 1 (fn_assign_electrons, fn_init_walkers): the
+ * ionic charge initialisation takes them from a Hartree-Fock calculation in the STO-6G
+ * basis.  Unrestricted Hartree-Fock in STO-6G (Hehre, Stewart & Pople 1969; standard
+ * molecular exponents) for nuclei of H..Ne (integer Z 1..10, at most 20 basis functions:
+ * four first-row atoms), n_up + n_down electrons; q_A = Z_A - sum over the functions mu on A
+ * of (P S)_mu,mu.  Host computation (no device memory, no stream): h_partial_charges [M]
+ * receives the charges (they sum to the ionic charge), h_energy [1] the UHF energy in
+ * hartree (NULL to skip).  FN_ERR_ARG for other elements, FN_ERR_UNSUPPORTED above 20
+ * functions, FN_ERR_NUMERIC if the iterations do not converge.                         */
+fn_status fn_mulliken_charges(const double* h_nuclei, const double* h_charges, int n_nuclei, int n_up,
+                              int n_down, double* h_partial_charges, double* h_energy);
+
 /* Kernel timing: while enabled, every kernel the handle launches is bracketed by a
  * CUDA event pair on its stream (adds a few microseconds per launch).  Enabling or
  * disabling clears the counters.  fn_profile_read waits for the recorded events and

@@ -88,6 +88,19 @@ def _stream(stream: Optional[torch.cuda.Stream]):
     return C.c_void_p(s.cuda_stream)
 
 
+def mulliken_charges(nuclei, charges, n_up: int, n_down: int) -> Tuple[np.ndarray, float]:
+    """(Mulliken partial charges [M], UHF energy) in STO-6G for nuclei of H..Ne: the partial
+    charges Algorithm 1 takes (fn_mulliken_charges, computed on the host)."""
+    lib = _lib.load()
+    nuc = np.ascontiguousarray(np.asarray(nuclei, dtype=np.float64).reshape(-1, 3))
+    z = np.ascontiguousarray(np.asarray(charges, dtype=np.float64))
+    q = np.zeros(z.shape[0])
+    e = np.zeros(1)
+    _check(lib.fn_mulliken_charges(nuc.ctypes.data_as(_lib._D), z.ctypes.data_as(_lib._D), int(z.shape[0]),
+                                   int(n_up), int(n_down), q.ctypes.data_as(_lib._D), e.ctypes.data_as(_lib._D)))
+    return q, float(e[0])
+
+
 class System:
     """A molecule (nuclei, charges, spins) plus a network configuration on the current device."""
 
@@ -123,6 +136,10 @@ class System:
 
     def set_walker_offset(self, offset: int):
         _check(self._lib.fn_set_walker_offset(self._h, int(offset)))
+
+    def mulliken_partial_charges(self) -> np.ndarray:
+        """STO-6G UHF Mulliken charges of this molecule (H..Ne), the input Algorithm 1 takes."""
+        return mulliken_charges(self.nuclei, self.charges, self.n_up, self.n_down)[0]
 
     def assign_electrons(self, partial_charges: Optional[Sequence[float]] = None):
         counts = (C.c_int * self.nuclei.shape[0])()
