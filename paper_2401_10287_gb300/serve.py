@@ -302,6 +302,23 @@ def summarize(results: List[Result], wall_s: float) -> dict:
                            "mean": float(lat.mean()), "max": float(lat.max())}}
 
 
+def shard_requests(requests: List[Request], rank: int, world: int) -> List[Request]:
+    """The requests one GPU serves when the stream is split by job across `world` GPUs (one
+    process per GPU): the i-th arrival goes to GPU i mod world.  Whole jobs move, so no
+    collective runs while serving; each GPU keeps its own admission budget and slots."""
+    order = sorted(requests, key=lambda r: (r.arrival_s, r.job_id))
+    return [r for i, r in enumerate(order) if i % world == rank]
+
+
+def gather_results(results: List[Result], group=None) -> List[Result]:
+    """Every rank's results, on every rank (torch.distributed object all-gather after serving),
+    for a summary of the whole stream."""
+    import torch.distributed as dist
+    parts = [None] * dist.get_world_size(group)
+    dist.all_gather_object(parts, results, group=group)
+    return sorted((r for part in parts for r in part), key=lambda r: r.job_id)
+
+
 def requests_from_jobs(jobs) -> List[Request]:
     """Requests from job descriptions carrying .system (nuclei, charges, spins, name)."""
     out = []
