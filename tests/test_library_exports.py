@@ -17,7 +17,8 @@ def _declared():
 def test_header_declares_entry_points():
     names = _declared()
     for n in ("fn_create_system", "fn_init_walkers", "fn_mcmc_steps", "fn_local_energy", "fn_energy_grad",
-              "fn_log_psi_noalloc", "fn_adam_step", "fn_sgd_step", "fn_clip_local_energy", "fn_vmc_iteration"
+              "fn_log_psi_noalloc", "fn_adam_step", "fn_sgd_step", "fn_clip_local_energy", "fn_vmc_iteration",
+              "fn_mulliken_charges"
               ):
         assert n in names
 
