@@ -356,6 +356,9 @@ def run_mine(args):
     ionis = None
     if args.ionisation and ws == 1:
         ionis = ionisation(P)
+    curve = None
+    if args.h2_curve and ws == 1:
+        curve = h2_curve(P)
     serving = None
     if args.serving_jobs > 0 and ws == 1:
         serving = run_serving(args.serving_jobs, args.serving_budget_gb, args.serving_slots)
@@ -382,6 +385,7 @@ def run_mine(args):
         "bf16_vs_fp32_and_fp64": comparison,
         "training": train,
         "ionisation": ionis,
+        "h2_curve": curve,
         "serving": serving,
         "acceptance": float(acc.item()) / max(1, (args.warmup + 2 * args.steps) * cfg["mcmc_steps"] * B),
     }
@@ -560,6 +564,34 @@ def training(P, sysm, a, cfg, B):
                            "above_exact_mha": float((tail.mean() - H2_EXACT_HA) * 1e3)}}
 
 
+def h2_curve(P, distances=(1.0, 1.2, 1.4, 1.6, 1.8, 2.0, 2.5, 3.0, 4.0), iters: int = 1500, lr: float = 1e-2):
+    """The Fig. 1 workload: H2 trained from random parameters at each internuclear distance
+    (2 layers 32/8, 1 determinant, isotropic envelopes, 4096 walkers, BF16-mixed, Adam, 0.3 bohr
+    proposals, `iters` iterations after 20 sampler-only ones, as in `training`); the energy is
+    the mean E_L of the last 200 iterations.  The exact energy is listed at 1.4 bohr."""
+    import torch
+    a = W.Ansatz(2, 32, 8, 1, "iso")
+    out = []
+    for R in distances:
+        h2 = W.h2(R)
+        g = P.System(h2.nuclei, h2.charges, 1, 1, P.NetConfig.from_ansatz(a, P.BF16_MIXED))
+        p = g.init_params(0)
+        w, _ = g.init_walkers(4096, 1, 1.0)
+        P.Trainer(g, p, w, P.TrainConfig(n_mcmc_steps=10, step_size=0.3, seed=3, optimizer="sgd", lr=0.0)).run(20)
+        tr = P.Trainer(g, p, w, P.TrainConfig(n_mcmc_steps=10, step_size=0.3, seed=2, clip_width=5.0, lr=lr))
+        means = torch.empty(iters, dtype=torch.float64, device="cuda")
+        for k in range(iters):
+            tr.step()
+            means[k] = tr.e_local.mean()
+        g.sync()
+        tail = means[-200:].cpu().numpy()
+        out.append({"bond_bohr": R, "energy_ha": float(tail.mean()),
+                    "stderr_of_iteration_means_ha": float(tail.std() / np.sqrt(tail.size))})
+        g.close()
+    return {"points": out, "exact_at_1.4_bohr_ha": H2_EXACT_HA,
+            "settings": {"iterations": iters, "lr": lr, "walkers": 4096, "precision": "bf16-mixed"}}
+
+
 PAPER_IP_HA = {"FermiNet": 0.2481, "CCSD": 0.2637, "HF": 0.2387}   # Table 1 of the paper
 
 
@@ -642,6 +674,8 @@ def main():
                     help="skip the training-loop measurements (N2 iteration time, H2 trained energy)")
     ap.add_argument("--ionisation", action="store_true",
                     help="train LiH and LiH+ (the paper's Table 1 workload) and report the ionisation potential")
+    ap.add_argument("--h2-curve", action="store_true",
+                    help="train H2 at nine internuclear distances (the paper's Fig. 1 workload)")
     ap.add_argument("--serving-jobs", type=int, default=150,
                     help="jobs of the serving stream to replay after the timed steps (0 to skip)")
     ap.add_argument("--serving-budget-gb", type=float, default=160.0)
