@@ -269,6 +269,14 @@ fn_status fn_vmc_iteration(fn_system_t sys, const fn_train_config* cfg, void* d_
 fn_status fn_mulliken_charges(const double* h_nuclei, const double* h_charges, int n_nuclei, int n_up,
                               int n_down, double* h_partial_charges, double* h_energy);
 
+/* Failure-path self-test: launches one CTA whose threads wait on a shared-memory
+ * mbarrier that nothing arrives at, each wait bounded by wait_us microseconds
+ * (1..100000) of %globaltimer and by an iteration cap.  On expiry the kernel sets the
+ * timeout bit of the device status word and returns, as the tensor-core kernels do when
+ * one of their waits expires; fn_sync then returns FN_ERR_TIMEOUT and clears the bit, and
+ * the context stays usable.  It tests error reporting without a fault or a hang.        */
+fn_status fn_selftest_expired_wait(fn_system_t sys, int wait_us, void* stream);
+
 /* Kernel timing: while enabled, every kernel the handle launches is bracketed by a
  * CUDA event pair on its stream (adds a few microseconds per launch).  Enabling or
  * disabling clears the counters.  fn_profile_read waits for the recorded events and
@@ -279,7 +287,7 @@ int fn_profile_read(fn_system_t sys, int index, const char** name, int64_t* laun
 
 /* Waits for the stream with a deadline (polling, no blocking sync), then reads
  * and clears the device status word.  FN_ERR_TIMEOUT if the deadline passes
- * (work keeps running) or if a tensor-core kernel gave up on a bounded wait,
+ * (work keeps running) or if a kernel gave up on a bounded wait,
  * FN_ERR_NUMERIC if a kernel flagged a numerical error.                     */
 fn_status fn_sync(fn_system_t sys, void* stream, int timeout_ms);
 

@@ -44,6 +44,7 @@ SIGNATURES = {
     "fn_vmc_iteration": (C.c_int, [_P, C.POINTER(TrainConfigC), _P, _P, C.c_int, C.c_int64, _P, _P, _P, _P, _P, _P,
                                    _P]),
     "fn_mulliken_charges": (C.c_int, [_D, _D, C.c_int, C.c_int, C.c_int, _D, _D]),
+    "fn_selftest_expired_wait": (C.c_int, [_P, C.c_int, _P]),
     "fn_profile_enable": (C.c_int, [_P, C.c_int]),
     "fn_profile_read": (C.c_int, [_P, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "fn_sync": (C.c_int, [_P, _P, C.c_int]),

@@ -281,6 +281,11 @@ class System:
                                           _ptr(opt_state), _ptr(grad), _ptr(log_psi), _ptr(e_local), _ptr(e_mean),
                                           _ptr(accept_count), _stream(stream)))
 
+    def selftest_expired_wait(self, wait_us: int = 2000, stream=None):
+        """Enqueues a kernel whose bounded barrier wait expires (fn_selftest_expired_wait);
+        the next sync() raises FnError with FN_ERR_TIMEOUT."""
+        _check(self._lib.fn_selftest_expired_wait(self._h, int(wait_us), _stream(stream)))
+
     def profile_enable(self, enable: bool = True):
         _check(self._lib.fn_profile_enable(self._h, 1 if enable else 0))
 

@@ -667,6 +667,14 @@ fn_status fn_vmc_iteration(fn_system_t s, const fn_train_config* c, void* d_para
   return check_launch(s, "vmc_iteration");
 }
 
+fn_status fn_selftest_expired_wait(fn_system_t s, int wait_us, void* stream) {
+  if (!s || wait_us < 1 || wait_us > 100000) { set_error("invalid argument"); return FN_ERR_ARG; }
+  fn_status st = ensure_workspace(s, 1);   // holds the device status word
+  if (st != FN_OK) return st;
+  launch_expired_wait(s, wait_us, (cudaStream_t)stream);
+  return check_launch(s, "selftest_expired_wait");
+}
+
 fn_status fn_profile_enable(fn_system_t s, int enable) {
   if (!s) { set_error("null system"); return FN_ERR_ARG; }
   if (!s->prof) s->prof = new Profiler();
@@ -705,7 +713,7 @@ fn_status fn_sync(fn_system_t s, void* stream, int timeout_ms) {
   if (word) {
     const int zero = 0;
     cudaMemcpy(s->ws.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
-    set_error(word & kStatusTimeout ? "a tensor-core kernel wait expired (timeout bit)"
+    set_error(word & kStatusTimeout ? "a bounded kernel wait expired (timeout bit)"
               : (word & kStatusSingular ? "all determinants singular for some walker" : "non-finite result"));
     if (word & kStatusTimeout) return FN_ERR_TIMEOUT;
     return FN_ERR_NUMERIC;

@@ -285,5 +285,7 @@ template <class Mode> void launch_sgd(const fn_system* s, void* params, const vo
                                       cudaStream_t st);
 void launch_clip_energy(const fn_system* s, int B, const double* e, double width, double* out, double* stats,
                         cudaStream_t st);
+// Failure-path self-test (fn_selftest.cu): a barrier wait that expires after wait_us.
+void launch_expired_wait(const fn_system* s, int wait_us, cudaStream_t st);
 
 }  // namespace fn
