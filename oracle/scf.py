@@ -13,7 +13,8 @@ H..Ne:
 * one- and two-electron integrals over contracted Cartesian Gaussians (s and p) by the
   McMurchie-Davidson scheme: Hermite expansion coefficients E, Hermite Coulomb
   integrals R and the Boys function F_n(T) = 1F1(n + 1/2; n + 3/2; -T) / (2n + 1);
-* unrestricted Hartree-Fock with a core-Hamiltonian start and DIIS;
+* unrestricted Hartree-Fock: core-Hamiltonian and generalised Wolfsberg-Helmholz starts,
+  damped iterations, then DIIS; the lower converged energy is kept;
 * Mulliken charges q_A = Z_A - sum over basis functions mu on A of (P S)_mu,mu with
   P = P_alpha + P_beta.
 
@@ -311,8 +312,14 @@ def integrals(basis, nuclei, charges):
 
 
 # ---- unrestricted Hartree-Fock ----------------------------------------------------------------
-def uhf(S, H, G, n_alpha, n_beta, e_nn=0.0, tol=1e-11, max_iter=500):
-    """UHF by Roothaan-Hall iterations with DIIS on both spins; returns (energy, Pa, Pb)."""
+def gwh_guess(S, H, k=1.75):
+    """Generalised Wolfsberg-Helmholz start: F_ij = k S_ij (H_ii + H_jj) / 2 off the diagonal."""
+    F = k * S * (np.diag(H)[:, None] + np.diag(H)[None, :]) / 2
+    np.fill_diagonal(F, np.diag(H))
+    return F
+
+
+def _uhf_from(F0, S, H, G, n_alpha, n_beta, e_nn, tol, max_iter, damp_iters):
     s, U = np.linalg.eigh(S)
     X = U @ np.diag(s ** -0.5) @ U.T
 
@@ -321,21 +328,25 @@ def uhf(S, H, G, n_alpha, n_beta, e_nn=0.0, tol=1e-11, max_iter=500):
         C = X @ C
         return C[:, :n_occ] @ C[:, :n_occ].T
 
-    Pa, Pb = density(H, n_alpha), density(H, n_beta)
+    Pa, Pb = density(F0, n_alpha), density(F0, n_beta)
     hist_F, hist_e = [], []
     e_old = None
-    for _ in range(max_iter):
+    for it in range(max_iter):
         J = np.einsum("pqrs,rs->pq", G, Pa + Pb)
         Fa = H + J - np.einsum("prqs,rs->pq", G, Pa)
         Fb = H + J - np.einsum("prqs,rs->pq", G, Pb)
         e = 0.5 * (np.sum((H + Fa) * Pa) + np.sum((H + Fb) * Pb)) + e_nn
         err = np.concatenate([(Fa @ Pa @ S - S @ Pa @ Fa).ravel(), (Fb @ Pb @ S - S @ Pb @ Fb).ravel()])
-        hist_F.append((Fa, Fb))
-        hist_e.append(err)
-        hist_F, hist_e = hist_F[-8:], hist_e[-8:]
         if e_old is not None and abs(e - e_old) < tol and np.max(np.abs(err)) < 1e-8:
             return e, Pa, Pb
         e_old = e
+        if it < damp_iters:                      # damped iterations before extrapolation
+            Pa = 0.5 * (Pa + density(Fa, n_alpha))
+            Pb = 0.5 * (Pb + density(Fb, n_beta))
+            continue
+        hist_F.append((Fa, Fb))
+        hist_e.append(err)
+        hist_F, hist_e = hist_F[-8:], hist_e[-8:]
         m = len(hist_e)
         B = -np.ones((m + 1, m + 1))
         B[m, m] = 0.0
@@ -349,6 +360,19 @@ def uhf(S, H, G, n_alpha, n_beta, e_nn=0.0, tol=1e-11, max_iter=500):
         Fb = sum(ci * f[1] for ci, f in zip(c, hist_F))
         Pa, Pb = density(Fa, n_alpha), density(Fb, n_beta)
     raise RuntimeError("UHF did not converge")
+
+
+def uhf(S, H, G, n_alpha, n_beta, e_nn=0.0, tol=1e-11, max_iter=500, damp_iters=30):
+    """UHF ground state; returns (energy, Pa, Pb).  DIIS from the first iteration can settle on
+    an excited self-consistent solution (N2 in STO-6G: -107.818 instead of -108.541 Ha), so
+    each of two starts (core Hamiltonian, generalised Wolfsberg-Helmholz) runs `damp_iters`
+    damped iterations (P <- (P + P_new) / 2) before DIIS, and the lower energy is kept."""
+    best = None
+    for F0 in (H, gwh_guess(S, H)):
+        res = _uhf_from(F0, S, H, G, n_alpha, n_beta, e_nn, tol, max_iter, damp_iters)
+        if best is None or res[0] < best[0] - 1e-9:
+            best = res
+    return best
 
 
 def mulliken_charges(nuclei, charges, n_alpha, n_beta):

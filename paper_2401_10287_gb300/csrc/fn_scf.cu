@@ -10,8 +10,9 @@
 //   * integrals over contracted Cartesian s and p Gaussians by the Obara-Saika
 //     recurrences (overlap, kinetic energy, nuclear attraction, and the two-electron
 //     vertical recurrence on all four centres);
-//   * unrestricted Hartree-Fock: symmetric orthogonalisation, core-Hamiltonian start,
-//     DIIS on both spins, Jacobi diagonalisation;
+//   * unrestricted Hartree-Fock: symmetric orthogonalisation; core-Hamiltonian and generalised
+//     Wolfsberg-Helmholz starts, damped iterations then DIIS on both spins, the lower converged
+//     energy kept; Jacobi diagonalisation;
 //   * q_A = Z_A - sum over the functions mu on A of (P S)_mu,mu, P = P_alpha + P_beta.
 // A diatomic takes milliseconds; the computation is set-up for the sampler, not part of
 // the per-walker path, and runs once per molecule.
@@ -357,6 +358,95 @@ static bool solve(int n, std::vector<double> A, std::vector<double> b, std::vect
   return true;
 }
 
+// UHF iterations from the starting Fock matrix F0: kDampIters damped steps (P <- (P + P_new) / 2),
+// then DIIS on both spins.  Returns false if not converged in 500 iterations; on success the
+// energy and the total density P_alpha + P_beta.
+constexpr int kDampIters = 30;
+
+static bool scf_from(const Mat& F0, int n, const Mat& S, const Mat& H, const std::vector<double>& G, const Mat& X,
+                     int n_a, int n_b, double e_nn, double* e_out, Mat* P_out) {
+  const size_t n2 = (size_t)n * n;
+  Mat Pa = density(n, F0, X, n_a), Pb = density(n, F0, X, n_b);
+  std::vector<Mat> hF_a, hF_b, hErr;
+  double e_old = 0;
+  for (int it = 0; it < 500; ++it) {
+    Mat Fa = H, Fb = H;
+    for (int p = 0; p < n; ++p)
+      for (int q = 0; q < n; ++q) {
+        double J = 0, Ka = 0, Kb = 0;
+        for (int r = 0; r < n; ++r)
+          for (int s = 0; s < n; ++s) {
+            const double prs = Pa[(size_t)r * n + s] + Pb[(size_t)r * n + s];
+            J += G[(((size_t)p * n + q) * n + r) * n + s] * prs;
+            const double x = G[(((size_t)p * n + r) * n + q) * n + s];
+            Ka += x * Pa[(size_t)r * n + s];
+            Kb += x * Pb[(size_t)r * n + s];
+          }
+        Fa[(size_t)p * n + q] += J - Ka;
+        Fb[(size_t)p * n + q] += J - Kb;
+      }
+    double e = e_nn;
+    for (size_t k = 0; k < n2; ++k) e += 0.5 * ((H[k] + Fa[k]) * Pa[k] + (H[k] + Fb[k]) * Pb[k]);
+    // DIIS error F P S - S P F for both spins
+    const Mat FPSa = matmul(n, matmul(n, Fa, Pa), S), FPSb = matmul(n, matmul(n, Fb, Pb), S);
+    Mat err(2 * n2);
+    double emax = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        err[(size_t)i * n + j] = FPSa[(size_t)i * n + j] - FPSa[(size_t)j * n + i];
+        err[n2 + (size_t)i * n + j] = FPSb[(size_t)i * n + j] - FPSb[(size_t)j * n + i];
+      }
+    for (double v : err) emax = std::max(emax, std::fabs(v));
+    if (it > 0 && std::fabs(e - e_old) < 1e-11 && emax < 1e-8) {
+      P_out->assign(n2, 0.0);
+      for (size_t k = 0; k < n2; ++k) (*P_out)[k] = Pa[k] + Pb[k];
+      *e_out = e;
+      return true;
+    }
+    e_old = e;
+    if (it < kDampIters) {
+      const Mat Na = density(n, Fa, X, n_a), Nb = density(n, Fb, X, n_b);
+      for (size_t k = 0; k < n2; ++k) {
+        Pa[k] = 0.5 * (Pa[k] + Na[k]);
+        Pb[k] = 0.5 * (Pb[k] + Nb[k]);
+      }
+      continue;
+    }
+    hF_a.push_back(Fa);
+    hF_b.push_back(Fb);
+    hErr.push_back(err);
+    if (hErr.size() > 8) {
+      hF_a.erase(hF_a.begin());
+      hF_b.erase(hF_b.begin());
+      hErr.erase(hErr.begin());
+    }
+    const int m = (int)hErr.size();
+    std::vector<double> Bm((size_t)(m + 1) * (m + 1), -1.0), rhs(m + 1, 0.0), c;
+    Bm[(size_t)m * (m + 1) + m] = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        double d = 0;
+        for (size_t k = 0; k < 2 * n2; ++k) d += hErr[i][k] * hErr[j][k];
+        Bm[(size_t)i * (m + 1) + j] = d;
+      }
+    rhs[m] = -1.0;
+    Mat Fa_x(n2, 0.0), Fb_x(n2, 0.0);
+    if (solve(m + 1, Bm, rhs, &c)) {
+      for (int i = 0; i < m; ++i)
+        for (size_t k = 0; k < n2; ++k) {
+          Fa_x[k] += c[i] * hF_a[i][k];
+          Fb_x[k] += c[i] * hF_b[i][k];
+        }
+    } else {
+      Fa_x = Fa;
+      Fb_x = Fb;
+    }
+    Pa = density(n, Fa_x, X, n_a);
+    Pb = density(n, Fb_x, X, n_b);
+  }
+  return false;
+}
+
 static fn_status run(const double* nuc, const double* Z, int M, int n_a, int n_b, double* q_out, double* e_out) {
   std::vector<Shell> bas;
   for (int A = 0; A < M; ++A) {
@@ -428,81 +518,35 @@ static fn_status run(const double* nuc, const double* Z, int M, int n_a, int n_b
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j)
       for (int k = 0; k < n; ++k) X[(size_t)i * n + j] += U[(size_t)i * n + k] * U[(size_t)j * n + k] / std::sqrt(s_ev[k]);
-  Mat Pa = density(n, H, X, n_a), Pb = density(n, H, X, n_b);
-  std::vector<Mat> hF_a, hF_b, hErr;
-  double e_old = 0;
-  for (int it = 0; it < 500; ++it) {
-    Mat Fa = H, Fb = H;
-    for (int p = 0; p < n; ++p)
-      for (int q = 0; q < n; ++q) {
-        double J = 0, Ka = 0, Kb = 0;
-        for (int r = 0; r < n; ++r)
-          for (int s = 0; s < n; ++s) {
-            const double prs = Pa[(size_t)r * n + s] + Pb[(size_t)r * n + s];
-            J += G[(((size_t)p * n + q) * n + r) * n + s] * prs;
-            const double x = G[(((size_t)p * n + r) * n + q) * n + s];
-            Ka += x * Pa[(size_t)r * n + s];
-            Kb += x * Pb[(size_t)r * n + s];
-          }
-        Fa[(size_t)p * n + q] += J - Ka;
-        Fb[(size_t)p * n + q] += J - Kb;
-      }
-    double e = e_nn;
-    for (size_t k = 0; k < n2; ++k) e += 0.5 * ((H[k] + Fa[k]) * Pa[k] + (H[k] + Fb[k]) * Pb[k]);
-    // DIIS error F P S - S P F for both spins
-    const Mat FPSa = matmul(n, matmul(n, Fa, Pa), S), FPSb = matmul(n, matmul(n, Fb, Pb), S);
-    Mat err(2 * n2);
-    double emax = 0;
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        err[(size_t)i * n + j] = FPSa[(size_t)i * n + j] - FPSa[(size_t)j * n + i];
-        err[n2 + (size_t)i * n + j] = FPSb[(size_t)i * n + j] - FPSb[(size_t)j * n + i];
-      }
-    for (double v : err) emax = std::max(emax, std::fabs(v));
-    if (it > 0 && std::fabs(e - e_old) < 1e-11 && emax < 1e-8) {
-      Mat P(n2);
-      for (size_t k = 0; k < n2; ++k) P[k] = Pa[k] + Pb[k];
-      const Mat PS = matmul(n, P, S);
-      for (int A = 0; A < M; ++A) q_out[A] = Z[A];
-      for (int mu = 0; mu < n; ++mu) q_out[bas[mu].atom] -= PS[(size_t)mu * n + mu];
-      if (e_out) *e_out = e;
-      return FN_OK;
+  // Two starts (core Hamiltonian; generalised Wolfsberg-Helmholz, k = 1.75), each with damped
+  // iterations before DIIS: DIIS from the first iteration can settle on an excited
+  // self-consistent solution.  The lower converged energy is the ground state kept.
+  Mat gwh(n2);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      gwh[(size_t)i * n + j] = i == j ? H[(size_t)i * n + i]
+                                      : 1.75 * S[(size_t)i * n + j] * 0.5 * (H[(size_t)i * n + i] + H[(size_t)j * n + j]);
+  bool found = false;
+  double e_best = 0;
+  Mat P_best;
+  for (const Mat* F0 : {&H, &gwh}) {
+    double e;
+    Mat P;
+    if (scf_from(*F0, n, S, H, G, X, n_a, n_b, e_nn, &e, &P) && (!found || e < e_best - 1e-9)) {
+      found = true;
+      e_best = e;
+      P_best = P;
     }
-    e_old = e;
-    hF_a.push_back(Fa);
-    hF_b.push_back(Fb);
-    hErr.push_back(err);
-    if (hErr.size() > 8) {
-      hF_a.erase(hF_a.begin());
-      hF_b.erase(hF_b.begin());
-      hErr.erase(hErr.begin());
-    }
-    const int m = (int)hErr.size();
-    std::vector<double> Bm((size_t)(m + 1) * (m + 1), -1.0), rhs(m + 1, 0.0), c;
-    Bm[(size_t)m * (m + 1) + m] = 0.0;
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) {
-        double d = 0;
-        for (size_t k = 0; k < 2 * n2; ++k) d += hErr[i][k] * hErr[j][k];
-        Bm[(size_t)i * (m + 1) + j] = d;
-      }
-    rhs[m] = -1.0;
-    Mat Fa_x(n2, 0.0), Fb_x(n2, 0.0);
-    if (solve(m + 1, Bm, rhs, &c)) {
-      for (int i = 0; i < m; ++i)
-        for (size_t k = 0; k < n2; ++k) {
-          Fa_x[k] += c[i] * hF_a[i][k];
-          Fb_x[k] += c[i] * hF_b[i][k];
-        }
-    } else {
-      Fa_x = Fa;
-      Fb_x = Fb;
-    }
-    Pa = density(n, Fa_x, X, n_a);
-    Pb = density(n, Fb_x, X, n_b);
   }
-  set_error("Hartree-Fock did not converge in 500 iterations");
-  return FN_ERR_NUMERIC;
+  if (!found) {
+    set_error("Hartree-Fock did not converge in 500 iterations");
+    return FN_ERR_NUMERIC;
+  }
+  const Mat PS = matmul(n, P_best, S);
+  for (int A = 0; A < M; ++A) q_out[A] = Z[A];
+  for (int mu = 0; mu < n; ++mu) q_out[bas[mu].atom] -= PS[(size_t)mu * n + mu];
+  if (e_out) *e_out = e_best;
+  return FN_OK;
 }
 
 }  // namespace scf

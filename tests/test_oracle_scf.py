@@ -186,3 +186,38 @@ def test_lih_cation_charges_match_the_printed_example():
     np.testing.assert_allclose(q, g["charges"], atol=g["tolerance"][0])
     # and Algorithm 1 on them removes the cation's electron from Li
     assert ionic.ionic_electron_counts([3, 1], list(q), 1) == [2, 1]
+
+
+def test_n2_ground_state_has_degenerate_pi_levels():
+    """The D_inf_h ground state occupies both pi_u orbitals at one energy.  An excited
+    self-consistent solution that DIIS from the core guess settles on (-107.818 Ha) breaks this."""
+    import workloads as W
+    s = W.n2()
+    basis = scf.sto6g_basis(s.charges, s.nuclei)
+    S, H, G, e_nn = scf.integrals(basis, s.nuclei, s.charges)
+    e, Pa, Pb = scf.uhf(S, H, G, 7, 7, e_nn)
+    sv, U = np.linalg.eigh(S)
+    X = U @ np.diag(sv ** -0.5) @ U.T
+    F = H + np.einsum("pqrs,rs->pq", G, Pa + Pb) - np.einsum("prqs,rs->pq", G, Pa)
+    eps = np.linalg.eigvalsh(X.T @ F @ X)
+    occ = eps[:7]
+    assert np.min(np.abs(np.subtract.outer(occ, occ)) + 10 * np.eye(7)) < 1e-7     # a degenerate pair
+    assert eps[7] - eps[6] > 0.5                                                    # a clear gap
+    assert e == pytest.approx(-108.5408098, abs=1e-6)
+
+
+@pytest.mark.parametrize("name", ["N2", "CO+"])
+def test_uhf_energy_is_the_lowest_over_random_starts(name):
+    """Damped iterations from randomised starting Fock matrices never reach a lower energy."""
+    nuc = {"N2": [[0, 0, -1.034], [0, 0, 1.034]], "CO+": [[0, 0, 0], [0, 0, 2.132]]}[name]
+    z, na, nb = {"N2": ([7, 7], 7, 7), "CO+": ([6, 8], 7, 6)}[name]
+    nuc = np.asarray(nuc, float)
+    basis = scf.sto6g_basis(z, nuc)
+    S, H, G, e_nn = scf.integrals(basis, nuc, z)
+    e_best, _, _ = scf.uhf(S, H, G, na, nb, e_nn)
+    rs = np.random.default_rng(5)
+    for _ in range(4):
+        A = rs.standard_normal(H.shape)
+        F0 = H + 0.3 * (A + A.T)
+        e, _, _ = scf._uhf_from(F0, S, H, G, na, nb, e_nn, 1e-10, 2000, 2000)
+        assert e >= e_best - 1e-7
