@@ -508,6 +508,7 @@ static fn_status run(const double* nuc, const double* Z, int M, int n_a, int n_b
     for (int B = 0; B < A; ++B) {
       double r2 = 0;
       for (int d = 0; d < 3; ++d) r2 += (nuc[3 * A + d] - nuc[3 * B + d]) * (nuc[3 * A + d] - nuc[3 * B + d]);
+      if (!(r2 > 1e-12)) { set_error("two nuclei at the same position"); return FN_ERR_ARG; }
       e_nn += Z[A] * Z[B] / std::sqrt(r2);
     }
   // X = S^(-1/2)
