@@ -88,3 +88,14 @@ def test_arguments_outside_the_basis_are_refused(P):
     with pytest.raises(P.FnError) as err:                                 # coincident nuclei
         P.mulliken_charges(np.zeros((2, 3)), [1, 1], 1, 1)
     assert err.value.code == 1
+
+
+def test_algorithm1_on_library_charges_of_ions(P):
+    """CO+: C carries the most positive charge, so Algorithm 1 removes the electron from C;
+    OH-: O carries the most negative one and receives the extra electron."""
+    q, _ = P.mulliken_charges(np.array([[0, 0, 0], [0, 0, 2.132]]), [6, 8], 7, 6)
+    assert q[0] > q[1] > 0
+    assert ionic.ionic_electron_counts([6, 8], list(q), 1) == [5, 8]
+    q, _ = P.mulliken_charges(np.array([[0, 0, 0], [0.3, 0.5, 1.7]]), [8, 1], 5, 5)
+    assert q[0] < q[1] < 0
+    assert ionic.ionic_electron_counts([8, 1], list(q), -1) == [9, 1]
