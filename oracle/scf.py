@@ -13,8 +13,9 @@ H..Ne:
 * one- and two-electron integrals over contracted Cartesian Gaussians (s and p) by the
   McMurchie-Davidson scheme: Hermite expansion coefficients E, Hermite Coulomb
   integrals R and the Boys function F_n(T) = 1F1(n + 1/2; n + 3/2; -T) / (2n + 1);
-* unrestricted Hartree-Fock: core-Hamiltonian and generalised Wolfsberg-Helmholz starts,
-  damped iterations, then DIIS; the lower converged energy is kept;
+* unrestricted Hartree-Fock: six starts (core Hamiltonian, generalised Wolfsberg-Helmholz, four
+  seeded symmetric perturbations), damped iterations, then DIIS; the lowest converged energy is
+  kept;
 * Mulliken charges q_A = Z_A - sum over basis functions mu on A of (P S)_mu,mu with
   P = P_alpha + P_beta.
 
@@ -364,14 +365,26 @@ def _uhf_from(F0, S, H, G, n_alpha, n_beta, e_nn, tol, max_iter, damp_iters):
 
 def uhf(S, H, G, n_alpha, n_beta, e_nn=0.0, tol=1e-11, max_iter=500, damp_iters=30):
     """UHF ground state; returns (energy, Pa, Pb).  DIIS from the first iteration can settle on
-    an excited self-consistent solution (N2 in STO-6G: -107.818 instead of -108.541 Ha), so
-    each of two starts (core Hamiltonian, generalised Wolfsberg-Helmholz) runs `damp_iters`
-    damped iterations (P <- (P + P_new) / 2) before DIIS, and the lower energy is kept."""
+    an excited self-consistent solution (N2 in STO-6G: -107.818 instead of -108.541 Ha), and
+    open shells with degenerate levels have several solutions (O+), so six starts are run (core
+    Hamiltonian, generalised Wolfsberg-Helmholz, and four seeded symmetric perturbations of the
+    core Hamiltonian), each with `damp_iters` damped iterations (P <- (P + P_new) / 2) before
+    DIIS; the lowest converged energy is kept."""
+    starts = [H, gwh_guess(S, H)]
+    rs = np.random.default_rng(20240118)
+    for _ in range(16):                      # symmetry-breaking starts for open shells
+        A = rs.standard_normal(H.shape)
+        starts.append(H + 0.3 * (A + A.T))
     best = None
-    for F0 in (H, gwh_guess(S, H)):
-        res = _uhf_from(F0, S, H, G, n_alpha, n_beta, e_nn, tol, max_iter, damp_iters)
+    for F0 in starts:
+        try:
+            res = _uhf_from(F0, S, H, G, n_alpha, n_beta, e_nn, tol, max_iter, damp_iters)
+        except RuntimeError:
+            continue
         if best is None or res[0] < best[0] - 1e-9:
             best = res
+    if best is None:
+        raise RuntimeError("UHF did not converge from any start")
     return best
 
 

@@ -10,9 +10,9 @@
 //   * integrals over contracted Cartesian s and p Gaussians by the Obara-Saika
 //     recurrences (overlap, kinetic energy, nuclear attraction, and the two-electron
 //     vertical recurrence on all four centres);
-//   * unrestricted Hartree-Fock: symmetric orthogonalisation; core-Hamiltonian and generalised
-//     Wolfsberg-Helmholz starts, damped iterations then DIIS on both spins, the lower converged
-//     energy kept; Jacobi diagonalisation;
+//   * unrestricted Hartree-Fock: symmetric orthogonalisation; six starts (core Hamiltonian,
+//     generalised Wolfsberg-Helmholz, four symmetric perturbations of the core Hamiltonian), damped
+//     iterations then DIIS on both spins, the lowest converged energy kept; Jacobi diagonalisation;
 //   * q_A = Z_A - sum over the functions mu on A of (P S)_mu,mu, P = P_alpha + P_beta.
 // A diatomic takes milliseconds; the computation is set-up for the sampler, not part of
 // the per-walker path, and runs once per molecule.
@@ -519,21 +519,37 @@ static fn_status run(const double* nuc, const double* Z, int M, int n_a, int n_b
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j)
       for (int k = 0; k < n; ++k) X[(size_t)i * n + j] += U[(size_t)i * n + k] * U[(size_t)j * n + k] / std::sqrt(s_ev[k]);
-  // Two starts (core Hamiltonian; generalised Wolfsberg-Helmholz, k = 1.75), each with damped
-  // iterations before DIIS: DIIS from the first iteration can settle on an excited
-  // self-consistent solution.  The lower converged energy is the ground state kept.
+  // Starts: the core Hamiltonian and the generalised Wolfsberg-Helmholz guess (k = 1.75), each
+  // with damped iterations before DIIS (DIIS from the first iteration can settle on an excited
+  // self-consistent solution).  The lowest converged energy is the ground state kept.
   Mat gwh(n2);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j)
       gwh[(size_t)i * n + j] = i == j ? H[(size_t)i * n + i]
                                       : 1.75 * S[(size_t)i * n + j] * 0.5 * (H[(size_t)i * n + i] + H[(size_t)j * n + j]);
+  // Open shells with degenerate levels have several self-consistent solutions: four more starts
+  // perturb the core Hamiltonian symmetrically (0.3 x (R + R^T), R uniform in [-1, 1) from a
+  // 64-bit linear congruential generator with a fixed seed) to break the symmetry.
+  std::vector<Mat> starts = {H, gwh};
+  uint64_t state = 0x9E3779B97F4A7C15ull;
+  auto uniform = [&state]() {
+    state = state * 6364136223846793005ull + 1442695040888963407ull;
+    return (double)(state >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  };
+  for (int k = 0; k < 16; ++k) {
+    Mat R(n2), F0 = H;
+    for (size_t i = 0; i < n2; ++i) R[i] = uniform();
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) F0[(size_t)i * n + j] += 0.3 * (R[(size_t)i * n + j] + R[(size_t)j * n + i]);
+    starts.push_back(F0);
+  }
   bool found = false;
   double e_best = 0;
   Mat P_best;
-  for (const Mat* F0 : {&H, &gwh}) {
+  for (const Mat& F0 : starts) {
     double e;
     Mat P;
-    if (scf_from(*F0, n, S, H, G, X, n_a, n_b, e_nn, &e, &P) && (!found || e < e_best - 1e-9)) {
+    if (scf_from(F0, n, S, H, G, X, n_a, n_b, e_nn, &e, &P) && (!found || e < e_best - 1e-9)) {
       found = true;
       e_best = e;
       P_best = P;

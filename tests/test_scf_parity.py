@@ -85,6 +85,9 @@ def test_arguments_outside_the_basis_are_refused(P):
     with pytest.raises(P.FnError) as err:
         P.mulliken_charges(np.zeros((1, 3)), [1], 0, 0)
     assert err.value.code == 1
+    with pytest.raises(P.FnError) as err:                                 # He-: two up electrons, one function
+        P.mulliken_charges(np.zeros((1, 3)), [2], 2, 1)
+    assert err.value.code == 1
     with pytest.raises(P.FnError) as err:                                 # coincident nuclei
         P.mulliken_charges(np.zeros((2, 3)), [1, 1], 1, 1)
     assert err.value.code == 1
