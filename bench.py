@@ -31,11 +31,12 @@ import workloads as W  # noqa: E402
 METRIC = "walker local energies/s (exact Laplacian) BF16 vs FP32; serving p50/p99 ms"
 UNIT = "walker-E_L/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# FP64 and FP32 vector rates derived from unit counts and clocks: 152 SMs x 2.07 GHz x
-# (64 FP64 FMA lanes / 64 per the part's ratio -> 1.25 TFLOP/s nominal FP64;
-#  128 FP32 lanes x 2 flops -> 80.5 TFLOP/s FP32).
-FP64_PEAK_TFLOPS = 1.25
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 and FP32 vector rates derived from unit counts and the maximum SM clock (2.07 GHz):
+# FP64 2 FMA per clock per SM on this part (its nominal 1.25 TFLOP/s), FP32 128 FMA lanes
+# per SM.  bench.py also measures a cuBLAS DGEMM/SGEMM rate on the box (`alu_probe`).
+SM_COUNT, SM_CLOCK_HZ = 152, 2.07e9
+FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_CLOCK_HZ / 1e12
+FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_CLOCK_HZ / 1e12
 
 
 def _peaks():
@@ -202,6 +203,50 @@ def _algorithmic(cls, B, N, a, T_full, act_bytes, launches=1):
     return None, None
 
 
+def _layer_tensor_flops(B, N, a, T):
+    """Tensor-core work of one stream-layer launch as the hot-path table defines it: rows
+    B N T (electrons x tangent slabs) times h1 outputs times the contraction length k_self of
+    the layer's own input [h, mean-up g, mean-down g], 2 FLOP each, averaged over the L
+    launches of one pass.  The spin-mean half of the layer is a per-walker GEMM, not counted
+    here; neither are the extra products of the hi/lo BF16 splits."""
+    M = 2
+    k_self = [4 * M + 8] + [a.h1 + 2 * a.h2] * (a.n_layers - 1)
+    return float(np.mean([2.0 * B * N * T * a.h1 * k for k in k_self]))
+
+
+def _minimal_pass_bytes(B, N, P_count, par_bytes, wlk_bytes):
+    """Irreducible HBM traffic of one local-energy pass: the parameters once and the walkers
+    in, the energies out."""
+    return float(P_count * par_bytes + B * N * 3 * wlk_bytes + B * 8)
+
+
+def alu_probe():
+    """cuBLAS DGEMM and (non-TF32) SGEMM rates on this GPU, 4096^3, best of 3 (context for
+    the derived FP64 and FP32 peaks)."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    for name, dt in (("dgemm_tflops", torch.float64), ("sgemm_tflops", torch.float32)):
+        n = 4096
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        torch.matmul(a, b)
+        best = 1e30
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[name] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    return out
+
+
 def _measured_traffic(cls):
     """DRAM bytes per launch of the layer kernel from the committed ncu capture, valid only while
     the kernel source is the one that was profiled (else None)."""
@@ -324,9 +369,28 @@ def run_mine(args):
     act_bytes = 2 if prec == P.BF16_MIXED else (8 if prec == P.FP64 else 4)
     work, kind = _algorithmic(cls, B, N, a, T_full, act_bytes, launches)
     roof = None
+    probe = alu_probe()
     if work is not None:
         avg_s = total_ms / launches / 1000.0
-        if kind == "bytes":
+        if cls == "layer_full" and prec == P.BF16_MIXED:
+            # tensor-core bound (BF16 contraction); the streamed-bytes view of the same launch
+            # is kept beside it as the HBM figure of this unfused design
+            fl = _layer_tensor_flops(B, N, a, T_full)
+            achieved = fl / avg_s / 1e12
+            pk = peaks["bf16_tflops_sustained"]
+            par_bytes = 8 if prec == P.FP64 else 4
+            roof = {"kernel": cls, "bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                    "frac": achieved / pk,
+                    "traffic": args.traffic if args.traffic is not None else _measured_traffic(cls),
+                    "algorithmic_flop_per_launch": fl,
+                    "flop_definition": "2 B N T h1 k_self per layer launch (mean of the L layers), B N = "
+                                       f"{B * N} electron rows, T = {T_full} slabs",
+                    "peak_source": f"{peak_src} cuBLAS BF16 sustained",
+                    "unfused_traffic": {"bytes_per_launch": work, "achieved_gbs": work / avg_s / 1e9,
+                                        "frac_of_hbm": work / avg_s / 1e9 / peaks["hbm_gbs"],
+                                        "note": "every tangent slab of X_l read and of h_l+1 written once"},
+                    "minimal_bytes_per_pass": _minimal_pass_bytes(B, N, gpu.param_count, par_bytes, 4)}
+        elif kind == "bytes":
             achieved = work / avg_s / 1e9
             pk = peaks["hbm_gbs"]
             roof = {"kernel": cls, "bound": "hbm", "achieved": achieved, "peak": pk, "unit": "GB/s",
@@ -337,12 +401,14 @@ def run_mine(args):
             achieved = work / avg_s / 1e12
             roof = {"kernel": cls, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s (FP64)", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": args.traffic,
-                    "peak_source": "nominal FP64 rate of the part (measured DFMA probe: 1.20)"}
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2.07 GHz; cuBLAS DGEMM measured "
+                                   f"{probe['dgemm_tflops']:.2f} TFLOP/s"}
         else:
             achieved = work / avg_s / 1e12
             roof = {"kernel": cls, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                     "unit": "TFLOP/s (FP32)", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": args.traffic,
-                    "peak_source": "derived from unit counts and the 2.07 GHz clock"}
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz; cuBLAS SGEMM measured "
+                                   f"{probe['sgemm_tflops']:.2f} TFLOP/s"}
     cb = None
     if not args.no_cpu_baseline and ws == 1:
         cb = cpu_baseline(args.precision)
@@ -362,6 +428,9 @@ def run_mine(args):
     serving = None
     if args.serving_jobs > 0 and ws == 1:
         serving = run_serving(args.serving_jobs, args.serving_budget_gb, args.serving_slots)
+    workloads = None
+    if ws == 1 and not args.no_compare:
+        workloads = other_workloads(P)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -387,6 +456,8 @@ def run_mine(args):
         "ionisation": ionis,
         "h2_curve": curve,
         "serving": serving,
+        "workloads": workloads,
+        "alu_probe": probe,
         "acceptance": float(acc.item()) / max(1, (args.warmup + 2 * args.steps) * cfg["mcmc_steps"] * B),
     }
     print(json.dumps(line), flush=True)
@@ -446,6 +517,52 @@ def compare_modes(P, sysm, a, cfg, B, bf16_ms):
                                   "mean_energy_fp64_ha": e64m, "bias_mha": float(d.mean() * 1e3),
                                   "bias_stderr_mha": float(d.std() / np.sqrt(B) * 1e3),
                                   "median_abs_de_ha": float(np.median(np.abs(d)))}}
+
+
+def other_workloads(P):
+    """Rates of the other specified workloads, outside the timed region (CUDA events, median):
+      H2 FP64 (2 layers 32/8, 1 determinant, isotropic envelopes, 256 walkers, init std 1,
+        seed 0): 20 Metropolis steps of 0.02 bohr then the local energy, as one workload
+        pass, and the local-energy call alone;
+      LiH+ and LiH- FP32 (4 layers 128/16, 8 determinants, anisotropic envelopes, 4096 walkers
+        from Algorithm 1, init std 0.5, seed 4): local energy and the Eq. 6 energy gradient,
+        walker gradients per second of one energy_grad call."""
+    out = {}
+    cfg = W.H2_SMALL
+    sysm = W.h2()
+    g = P.System(sysm.nuclei, sysm.charges, 1, 1, P.NetConfig.from_ansatz(cfg["ansatz"], P.FP64))
+    p = g.init_params(cfg["seed"])
+    B = cfg["walkers"]
+
+    def h2_pass():
+        w, _ = g.init_walkers(B, cfg["seed"], cfg["init_std"])
+        lp, _ = g.log_psi(p, w)
+        g.mcmc_steps(p, w, lp, cfg["mcmc_steps"], cfg["step_size"], cfg["seed"])
+        g.local_energy(p, w)
+    h2_pass()
+    w, _ = g.init_walkers(B, cfg["seed"], cfg["init_std"])
+    pass_ms = _time_calls(h2_pass, 10)
+    le_ms = _time_calls(lambda: g.local_energy(p, w), 20)
+    out["h2_fp64_256"] = {"pass_ms": pass_ms, "pass": "init + log psi + 20 Metropolis steps + E_L",
+                          "walker_e_l_per_s_pass": B / pass_ms * 1e3, "local_energy_ms": le_ms,
+                          "walker_e_l_per_s": B / le_ms * 1e3}
+    g.close()
+    cfg = W.LIH_IONS
+    for charge in cfg["charges"]:
+        sysm = W.lih(charge)
+        g = P.System(sysm.nuclei, sysm.charges, sysm.n_up, sysm.n_down, P.NetConfig.from_ansatz(cfg["ansatz"], P.FP32))
+        p = g.init_params(cfg["seed"])
+        w, counts = g.init_walkers(cfg["walkers"], cfg["seed"], cfg["init_std"], sysm.partial_charges)
+        e, _, _ = g.local_energy(p, w)
+        g.energy_grad(p, w, e)
+        le_ms = _time_calls(lambda: g.local_energy(p, w), 10)
+        gr_ms = _time_calls(lambda: g.energy_grad(p, w, e), 10)
+        out[f"{sysm.name}_fp32_4096"] = {"algorithm1_counts": counts, "local_energy_ms": le_ms,
+                                         "walker_e_l_per_s": cfg["walkers"] / le_ms * 1e3,
+                                         "energy_grad_ms": gr_ms,
+                                         "walker_gradients_per_s": cfg["walkers"] / gr_ms * 1e3}
+        g.close()
+    return out
 
 
 def _time_calls(fn, reps):
@@ -652,7 +769,8 @@ def run_serving(n_jobs: int, budget_gb: float, slots: int):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     out = serve.summarize(res, wall)
-    out.update({"stream": f"first {n_jobs} jobs of the 1000-job Poisson stream (50/s, seed 4)",
+    out.update({"stream": (f"first {n_jobs} jobs of " if n_jobs < 1000 else "") +
+                          "the 1000-job Poisson stream (50/s, seed 4)",
                 "slots": slots, "memory_budget_gb": budget_gb,
                 "peak_admitted_gb": round(srv.peak_footprint / (1 << 30), 2),
                 "max_concurrent_jobs": srv.max_concurrent, "evictions": srv.evictions})
@@ -676,7 +794,7 @@ def main():
                     help="train LiH and LiH+ (the paper's Table 1 workload) and report the ionisation potential")
     ap.add_argument("--h2-curve", action="store_true",
                     help="train H2 at nine internuclear distances (the paper's Fig. 1 workload)")
-    ap.add_argument("--serving-jobs", type=int, default=150,
+    ap.add_argument("--serving-jobs", type=int, default=1000,
                     help="jobs of the serving stream to replay after the timed steps (0 to skip)")
     ap.add_argument("--serving-budget-gb", type=float, default=160.0)
     ap.add_argument("--serving-slots", type=int, default=8)

@@ -183,8 +183,12 @@ fn_status fn_log_psi_vjp(fn_system_t sys, const void* d_params, const void* d_wa
  * process exits; the array's address is looked up on the first call made on each
  * device (cudaGetSymbolAddress), so make that first call before any stream capture.
  * Calls share the array: two calls whose work overlaps on the GPU race, so order them
- * on one stream.  A batch whose scratch exceeds 64 MiB returns FN_ERR_ARG, with the
- * walker count that fits in fn_last_error().  The handle's own workspace is untouched.
+ * on one stream.  Each call writes every part of the array it reads, so what an earlier
+ * call (of any system) left there never reaches the result.  A batch whose scratch
+ * exceeds 64 MiB returns FN_ERR_ARG, with the walker count that fits in fn_last_error().
+ * The handle's own workspace is untouched; errors found on the device (non-finite or
+ * singular results, an expired bounded wait) are recorded in the handle's status word
+ * and reported by the next fn_sync, as for fn_log_psi.
  * The method has no counterpart of this entry point; it is a deployment variant.  */
 fn_status fn_log_psi_noalloc(fn_system_t sys, const void* d_params, const void* d_walkers,
                              int n_walkers, double* d_log_psi, int8_t* d_sign, void* stream);

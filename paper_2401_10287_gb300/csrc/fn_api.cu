@@ -232,7 +232,6 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
   const size_t o_g16 = take(bf16 ? (size_t)sh.R * std::max<int64_t>(h1, s->prep.ldWT) * 2 : 0);
   const size_t o_t16a = take(bf16 ? (size_t)std::max(max_k, h1) * sh.R * 2 : 0);
   const size_t o_t16b = take(bf16 ? (size_t)std::max<int64_t>(h1, KN) * sh.R * 2 : 0);
-  const size_t o_status = take(sizeof(int) * 4);
   const size_t o_counter = take(sizeof(int64_t) * 4);
   if (ws && ws->base) {
     char* b = (char*)ws->base;
@@ -244,7 +243,7 @@ static size_t workspace_layout(fn_system* s, int B, Workspace* ws) {
     ws->prep16 = b + o_prep16; ws->walk2 = b + o_walk2; ws->lp2 = (double*)(b + o_lp2);
     ws->scratch_d = (double*)(b + o_scr); ws->dX = b + o_dX; ws->dH = b + o_dH; ws->dZ = b + o_dZ;
     ws->dZw = b + o_dZw; ws->dHbar = b + o_dHbar; ws->dG = b + o_dG; ws->dPhi = b + o_dPhi;
-    ws->gradc = b + o_gradc; ws->dP = b + o_dP; ws->orbP = (float*)(b + o_orbP); ws->envv = (float*)(b + o_envv); ws->status = (int*)(b + o_status); ws->counter = (int64_t*)(b + o_counter);
+    ws->gradc = b + o_gradc; ws->dP = b + o_dP; ws->orbP = (float*)(b + o_orbP); ws->envv = (float*)(b + o_envv); ws->status = s->d_status; ws->counter = (int64_t*)(b + o_counter);
     ws->g16 = b + o_g16; ws->t16a = b + o_t16a; ws->t16b = b + o_t16b;
   }
   return off;
@@ -394,10 +393,14 @@ fn_status fn_create_system(const double* h_nuclei, const double* h_charges, int 
       return FN_ERR_UNSUPPORTED;
     }
   }
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_nuclei, sizeof(double) * (3 * n_nuclei + n_nuclei));
+  // nuclei [M][3], charges [M] and the device status word (4 ints) in one allocation
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_nuclei, sizeof(double) * (3 * n_nuclei + n_nuclei) + 4 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&s->d_elec_atom, sizeof(int) * kMaxElectrons);
   if (e != cudaSuccess) { fn_status r = cuda_status(e, "create_system"); delete s; return r; }
   s->d_charges = s->d_nuclei + 3 * n_nuclei;
+  s->d_status = (int*)(s->d_nuclei + 4 * n_nuclei);
+  e = cudaMemset(s->d_status, 0, 4 * sizeof(int));
+  if (e != cudaSuccess) { fn_status r = cuda_status(e, "create_system status word"); fn_destroy_system(s); return r; }
   e = cudaMemcpy(s->d_nuclei, h_nuclei, sizeof(double) * 3 * n_nuclei, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_charges, h_charges, sizeof(double) * n_nuclei, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->d_elec_atom, s->elec_atom.data(), sizeof(int) * s->N, cudaMemcpyHostToDevice);
@@ -706,13 +709,12 @@ fn_status fn_sync(fn_system_t s, void* stream, int timeout_ms) {
     if (timeout_ms >= 0 && el > timeout_ms) { set_error("fn_sync deadline passed"); return FN_ERR_TIMEOUT; }
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
-  if (!s->ws.base) return FN_OK;
   int word = 0;
-  cudaError_t e = cudaMemcpy(&word, s->ws.status, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpy(&word, s->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_status(e, "status read");
   if (word) {
     const int zero = 0;
-    cudaMemcpy(s->ws.status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(s->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
     set_error(word & kStatusTimeout ? "a bounded kernel wait expired (timeout bit)"
               : (word & kStatusSingular ? "all determinants singular for some walker" : "non-finite result"));
     if (word & kStatusTimeout) return FN_ERR_TIMEOUT;

@@ -34,6 +34,10 @@ __global__ void k_prep(const Par* __restrict__ blob, const CopyDesc* __restrict_
   const int64_t n = (int64_t)d.rows * d.cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / d.cols, c = e % d.cols;
+    if (d.to16 == 3) {
+      prep16[d.dst + r * d.d_rs + c * d.d_cs] = __float2bfloat16_rn(0.f);
+      continue;
+    }
     const Par v = blob[d.src + r * d.s_rs + c * d.s_cs];
     if (d.to16) {
       const __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
@@ -68,6 +72,11 @@ static std::vector<CopyDesc> build_descs(const fn_system* s, bool with16) {
         v.push_back({d.off_V + 3 * d.d_h, f_in, 1, p.Vs16[l] + d.d_h + ox, 2 * d.ldx, 1, h1, 2 * d.d_g, part});
         v.push_back({d.off_V + d.d_h, f_in, 1, p.U16[l] + ou, 4 * d.d_h, 1, h1, 2 * d.d_h, part});
       }
+      // zero padding between k_self and ldx of both parts: the tensor-core B tiles read these
+      // columns against zero-filled A columns, so they must hold finite values
+      if (d.ldx > d.k_self)
+        for (int part = 0; part < 2; ++part)
+          v.push_back({0, 0, 0, p.Vs16[l] + part * d.ldx + d.k_self, 2 * d.ldx, 1, h1, d.ldx - d.k_self, 3});
     }
   }
   const int ns[2] = {s->n_up, s->n_dn};
@@ -82,6 +91,10 @@ static std::vector<CopyDesc> build_descs(const fn_system* s, bool with16) {
           v.push_back({s->off_w[a], 1, h1, p.W16T + (a ? (int64_t)K * ns[0] : 0) + (part == 2 ? p.ldWT : 0),
                        2 * p.ldWT, 1, h1, K * ns[a], part});
         }
+  if (with16 && p.ldWT > K * (ns[0] + ns[1]))
+    for (int part = 0; part < 2; ++part)
+      v.push_back({0, 0, 0, p.W16T + part * p.ldWT + K * (ns[0] + ns[1]), 2 * p.ldWT, 1, h1,
+                   p.ldWT - K * (ns[0] + ns[1]), 3});
   if (with16)
     for (int l = 0; l < L; ++l) {
       const LayerDims& d = s->layer[l];

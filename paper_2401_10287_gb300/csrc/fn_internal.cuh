@@ -165,7 +165,8 @@ struct CopyDesc {
   int64_t src, s_rs, s_cs;   // source offset and strides (row, col) in the blob
   int64_t dst, d_rs, d_cs;   // destination offset and strides
   int rows, cols;
-  int to16;                  // 0: Cmp array; 1: bf16 array, bf16(v); 2: bf16 array, bf16(v - bf16(v))
+  int to16;                  // 0: Cmp array; 1: bf16 array, bf16(v); 2: bf16 array, bf16(v - bf16(v));
+                             // 3: bf16 array, zero (padding columns; the source is not read)
 };
 
 struct Workspace {
@@ -201,7 +202,7 @@ struct Workspace {
   void* g16 = nullptr;           // [R][max(h1, ldWT)] bf16 copy of dZ or dP
   void* t16a = nullptr;          // [max(k_self, h1)][R] bf16 transposed activations (X_l^T, h_L^T)
   void* t16b = nullptr;          // [max(h1, K N)][R] bf16 transposed gradients (dZ^T, dP^T)
-  int* status = nullptr;         // device status word
+  int* status = nullptr;         // device status word (the handle's d_status)
   int64_t* counter = nullptr;    // scratch counter
 };
 
@@ -225,6 +226,7 @@ struct fn_system {
   // small device constants
   double* d_nuclei = nullptr;    // [M][3]
   double* d_charges = nullptr;   // [M]
+  int* d_status = nullptr;       // device status word (kStatus* bits), read and cleared by fn_sync
   int* d_elec_atom = nullptr;    // [N]
   void* d_descs = nullptr;       // parameter-preparation copy descriptors
   int n_descs = 0;

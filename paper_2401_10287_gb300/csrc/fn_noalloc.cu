@@ -11,9 +11,13 @@
 // library, for the life of the process.  Its device address is looked up once per device
 // (cudaGetSymbolAddress with that device current) on the first call made on that device,
 // so that first call should come before any stream capture.
-// All calls share the array, so two calls whose work overlaps on the GPU race; a later
-// call sees whatever the previous one left, and everything that must start at zero is
-// cleared by each call.
+// All calls share the array, so two calls whose work overlaps on the GPU race.  A call
+// sees whatever the previous one left there; every buffer of the array is written before
+// it is read (the parameter preparation writes the zero padding of the BF16 weight
+// matrices itself), so no leftover value reaches a result.  Errors found on the device
+// (a non-finite or singular result, a bounded wait that expired) go to the handle's own
+// status word, which lives outside the array, and fn_sync reports them as it does for
+// fn_log_psi.
 #include <mutex>
 
 #include "fn_internal.cuh"
@@ -72,7 +76,6 @@ static size_t value_pass_layout(const fn_system* s, int B, unsigned char* base, 
   const size_t o_prep = take((size_t)s->prep.total * sizeof(Cmp));
   const size_t o_prep16 = take((size_t)s->prep.total16 * sizeof(__nv_bfloat16));
   const size_t o_envv = take(Mode::kMode == FN_BF16_MIXED ? (size_t)sh.R * s->cfg.n_dets * s->N * sizeof(float) : 0);
-  const size_t o_status = take(sizeof(int) * 4);
   if (base && ws) {
     *ws = Workspace();
     for (int l = 0; l < L; ++l) {
@@ -84,7 +87,7 @@ static size_t value_pass_layout(const fn_system* s, int B, unsigned char* base, 
     ws->Phi = base + o_Phi;
     ws->prep = base + o_prep;
     ws->prep16 = base + o_prep16;
-    ws->status = (int*)(base + o_status);
+    ws->status = s->d_status;            // kernels report into the handle's word, read by fn_sync
     ws->envv = (float*)(base + o_envv);
     ws->base = base;
     ws->bytes = off;
@@ -110,9 +113,6 @@ static fn_status log_psi_noalloc(fn_system* s, const void* params, const void* w
   if (r != FN_OK) return r;
   Workspace arena;
   value_pass_layout<Mode>(s, B, (unsigned char*)base, &arena);
-  // the status word must start at zero; the activation buffers are fully written before read
-  cudaError_t e = cudaMemsetAsync(arena.status, 0, sizeof(int) * 4, st);
-  if (e != cudaSuccess) return cuda_status(e, "clearing the no-allocation status word");
   // run the value pass of fn_log_psi against the arena, leaving the handle's own workspace untouched
   const Workspace saved = s->ws;
   Profiler* saved_prof = s->prof;
