@@ -193,6 +193,28 @@ fn_status fn_log_psi_vjp(fn_system_t sys, const void* d_params, const void* d_wa
 fn_status fn_log_psi_noalloc(fn_system_t sys, const void* d_params, const void* d_walkers,
                              int n_walkers, double* d_log_psi, int8_t* d_sign, void* stream);
 
+/* ---- Eq. 1 estimator and Eq. 6 weights from summable moments ------------------------
+ * The VMC energy is the mean local energy over the sampled walkers (Eq. 1); its error bar
+ * follows from their variance.  The moments [count, sum E_L, sum E_L^2] (FP64) add up over
+ * batches and devices, so a batch split across GPUs all-reduces these three numbers (a sum)
+ * and then forms the statistics or the Eq. 6 weights from the global moments.            */
+
+/* d_moments [3] double <- [n_walkers, sum E_L, sum E_L^2] of d_e_local [n_walkers] double
+ * (one CTA, fixed summation order).                                                      */
+fn_status fn_energy_moments(fn_system_t sys, const double* d_e_local, int n_walkers, double* d_moments,
+                            void* stream);
+
+/* d_stats [3] double <- [count, mean = sum / count, variance = sum2 / count - mean^2 (>= 0)]
+ * from d_moments [3] (Eq. 1; the standard error is sqrt(variance / count)).  A non-finite
+ * mean or variance sets the numeric bit reported by fn_sync.                               */
+fn_status fn_energy_stats(fn_system_t sys, const double* d_moments, double* d_stats, void* stream);
+
+/* Eq. 6 weights with the mean and count of d_moments [3] (e.g. all-reduced over devices):
+ * d_weights[w] = 2 (d_e_local[w] - sum / count) / count, [n_walkers] double; the input of
+ * fn_log_psi_vjp.                                                                           */
+fn_status fn_energy_weights(fn_system_t sys, const double* d_e_local, int n_walkers, const double* d_moments,
+                            double* d_weights, void* stream);
+
 /* ---- VMC training loop ------------------------------------------------------------
  * The training phase of the method updates the parameters with the Eq. 6 gradient
  * between rounds of the electron sampler.  The method names no optimiser: the library

@@ -38,6 +38,9 @@ SIGNATURES = {
     "fn_energy_grad": (C.c_int, [_P, _P, _P, _P, C.c_int, _P, _P, _P]),
     "fn_log_psi_noalloc": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P]),
     "fn_log_psi_vjp": (C.c_int, [_P, _P, _P, _P, C.c_int, _P, _P]),
+    "fn_energy_moments": (C.c_int, [_P, _P, C.c_int, _P, _P]),
+    "fn_energy_stats": (C.c_int, [_P, _P, _P, _P]),
+    "fn_energy_weights": (C.c_int, [_P, _P, C.c_int, _P, _P, _P]),
     "fn_adam_step": (C.c_int, [_P, _P, _P, _P, _P, C.c_int64, C.c_double, C.c_double, C.c_double, C.c_double, _P]),
     "fn_sgd_step": (C.c_int, [_P, _P, _P, C.c_double, _P]),
     "fn_clip_local_energy": (C.c_int, [_P, _P, C.c_int, C.c_double, _P, _P, _P]),

@@ -234,6 +234,29 @@ class System:
                                         _stream(stream)))
         return g
 
+    def energy_moments(self, e_local, stream=None) -> torch.Tensor:
+        """[count, sum E_L, sum E_L^2] (float64, on the device); sums over batches and devices."""
+        _check_f64(e_local, e_local.numel(), "e_local")
+        mom = torch.empty(3, dtype=torch.float64, device=e_local.device)
+        _check(self._lib.fn_energy_moments(self._h, _ptr(e_local), int(e_local.numel()), _ptr(mom), _stream(stream)))
+        return mom
+
+    def energy_stats(self, moments, stream=None) -> torch.Tensor:
+        """[count, mean, variance] of the local energies (Eq. 1) from (possibly summed) moments."""
+        _check_f64(moments, 3, "moments")
+        st = torch.empty(3, dtype=torch.float64, device=moments.device)
+        _check(self._lib.fn_energy_stats(self._h, _ptr(moments), _ptr(st), _stream(stream)))
+        return st
+
+    def energy_weights(self, e_local, moments, stream=None) -> torch.Tensor:
+        """Eq. 6 weights 2 (E_L - mean) / count with the mean and count of `moments`."""
+        _check_f64(e_local, e_local.numel(), "e_local")
+        _check_f64(moments, 3, "moments")
+        w = torch.empty_like(e_local)
+        _check(self._lib.fn_energy_weights(self._h, _ptr(e_local), int(e_local.numel()), _ptr(moments), _ptr(w),
+                                           _stream(stream)))
+        return w
+
     def _check_blob(self, *tensors):
         for t in tensors:
             if t.dtype != self.dtype or t.numel() != self.param_count or not t.is_contiguous():

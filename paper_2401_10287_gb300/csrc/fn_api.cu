@@ -262,29 +262,32 @@ static size_t workspace_bytes(fn_system* s, int B) {
   return dispatch(s, [&](auto m) { return workspace_layout<decltype(m)>(s, B, nullptr); });
 }
 
-static fn_status ensure_workspace(fn_system* s, int B) {
+// The workspace grows in stream order: the new block is allocated and cleared on the call's
+// stream and the old one is freed there (cudaMallocAsync / cudaFreeAsync), so growing never
+// waits for the device and never stalls work of other handles on other streams.
+static fn_status ensure_workspace(fn_system* s, int B, cudaStream_t st) {
+  s->last_stream = (void*)st;
+  s->stream_seen = true;
   if (B <= s->ws.cap_B && s->ws.base) return FN_OK;
   cudaError_t e = cudaSetDevice(s->device);
   if (e != cudaSuccess) return cuda_status(e, "cudaSetDevice");
-  if (s->ws.base) {
-    e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) return cuda_status(e, "cudaDeviceSynchronize");
-    cudaFree(s->ws.base);
-    s->ws.base = nullptr;
-  }
   const size_t bytes = workspace_bytes(s, B);
-  e = cudaMalloc(&s->ws.base, bytes);
-  if (e != cudaSuccess) {
-    s->ws.base = nullptr;
-    s->ws.cap_B = 0;
-    return cuda_status(e, "workspace allocation");
-  }
-  e = cudaMemset(s->ws.base, 0, bytes);
-  if (e != cudaSuccess) return cuda_status(e, "workspace clear");
+  void* p = nullptr;
+  e = cudaMallocAsync(&p, bytes, st);
+  if (e != cudaSuccess) return cuda_status(e, "workspace allocation");
+  e = cudaMemsetAsync(p, 0, bytes, st);
+  if (e != cudaSuccess) { cudaFreeAsync(p, st); return cuda_status(e, "workspace clear"); }
+  if (s->ws.base) cudaFreeAsync(s->ws.base, st);
+  s->ws.base = p;
   s->ws.bytes = bytes;
   s->ws.cap_B = B;
   dispatch(s, [&](auto m) { return workspace_layout<decltype(m)>(s, B, &s->ws); });
   return FN_OK;
+}
+
+static void note_stream(fn_system* s, void* st) {
+  s->last_stream = st;
+  s->stream_seen = true;
 }
 
 // The per-walker kernels keep one walker's pair activations or determinant matrices in
@@ -302,7 +305,7 @@ static const char* shared_memory_overflow(const fn_system* s, size_t limit, size
       {"two-electron stream, local-energy pass",
        bf16 ? smem_pair_full_mma(N, L, pair_full_mma_ib(N)) : smem_pair_full(cmp, N, L, pair_full_ib(N))},
       {"two-electron stream, gradient", (bf16 && L > 1) ? smem_pair_bwd_mma(N) : 0},
-      {"determinant stage, local energy", smem_det_energy(det, nmax, N, K)},
+      {"determinant stage, local energy", smem_det_energy(det, nmax, N, K, bf16)},
       {"determinant stage, value pass", nmax > 8 ? smem_det_value(det, nmax, K, false) : 0},
       {"determinant stage, gradient", smem_det_value(det, nmax, K, true)},
   };
@@ -393,17 +396,22 @@ fn_status fn_create_system(const double* h_nuclei, const double* h_charges, int 
       return FN_ERR_UNSUPPORTED;
     }
   }
-  // nuclei [M][3], charges [M] and the device status word (4 ints) in one allocation
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_nuclei, sizeof(double) * (3 * n_nuclei + n_nuclei) + 4 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_elec_atom, sizeof(int) * kMaxElectrons);
-  if (e != cudaSuccess) { fn_status r = cuda_status(e, "create_system"); delete s; return r; }
+  // nuclei [M][3], charges [M] and the device status word (4 ints) in one allocation; the
+  // handle's device buffers are stream-ordered allocations made on the per-thread stream (no
+  // ordering with other streams), waited for here, and freed in stream order by
+  // fn_destroy_system
+  const cudaStream_t pst = cudaStreamPerThread;
+  if (e == cudaSuccess) e = cudaMallocAsync(&s->d_nuclei, sizeof(double) * (3 * n_nuclei + n_nuclei) + 4 * sizeof(int), pst);
+  if (e == cudaSuccess) e = cudaMallocAsync(&s->d_elec_atom, sizeof(int) * kMaxElectrons, pst);
+  if (e != cudaSuccess) { fn_status r = cuda_status(e, "create_system"); fn_destroy_system(s); return r; }
   s->d_charges = s->d_nuclei + 3 * n_nuclei;
   s->d_status = (int*)(s->d_nuclei + 4 * n_nuclei);
-  e = cudaMemset(s->d_status, 0, 4 * sizeof(int));
-  if (e != cudaSuccess) { fn_status r = cuda_status(e, "create_system status word"); fn_destroy_system(s); return r; }
-  e = cudaMemcpy(s->d_nuclei, h_nuclei, sizeof(double) * 3 * n_nuclei, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(s->d_charges, h_charges, sizeof(double) * n_nuclei, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(s->d_elec_atom, s->elec_atom.data(), sizeof(int) * s->N, cudaMemcpyHostToDevice);
+  e = cudaMemsetAsync(s->d_status, 0, 4 * sizeof(int), pst);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_nuclei, h_nuclei, sizeof(double) * 3 * n_nuclei, cudaMemcpyHostToDevice, pst);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_charges, h_charges, sizeof(double) * n_nuclei, cudaMemcpyHostToDevice, pst);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_elec_atom, s->elec_atom.data(), sizeof(int) * s->N, cudaMemcpyHostToDevice, pst);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(pst);
   if (e != cudaSuccess) { fn_status r = cuda_status(e, "create_system copy"); fn_destroy_system(s); return r; }
   st = upload_prep_descs(s);
   if (st != FN_OK) { fn_destroy_system(s); return st; }
@@ -414,13 +422,21 @@ fn_status fn_create_system(const double* h_nuclei, const double* h_charges, int 
   return FN_OK;
 }
 
+// The device buffers are freed in stream order on the stream of the handle's latest call
+// (its work there finishes first); the host does not wait.  Work of this handle enqueued on
+// other streams must be ordered before that stream by the caller, as for every call.
 fn_status fn_destroy_system(fn_system_t s) {
   if (!s) return FN_OK;
-  if (s->ws.base || s->d_nuclei) cudaDeviceSynchronize();
-  if (s->ws.base) cudaFree(s->ws.base);
-  if (s->d_nuclei) cudaFree(s->d_nuclei);
-  if (s->d_elec_atom) cudaFree(s->d_elec_atom);
-  if (s->d_descs) cudaFree(s->d_descs);
+  const cudaStream_t st = s->stream_seen ? (cudaStream_t)s->last_stream : cudaStreamPerThread;
+  void* bufs[4] = {s->ws.base, s->d_nuclei, s->d_elec_atom, s->d_descs};
+  for (void* p : bufs) {
+    if (!p) continue;
+    if (cudaFreeAsync(p, st) != cudaSuccess) {
+      cudaGetLastError();
+      cudaDeviceSynchronize();
+      cudaFree(p);
+    }
+  }
   delete s->prof;
   delete s;
   return FN_OK;
@@ -456,6 +472,7 @@ fn_status fn_assign_electrons(fn_system_t s, const double* partial, int* counts_
 
 fn_status fn_init_params(fn_system_t s, uint64_t seed, void* d_params, void* stream) {
   if (!s || !d_params) { set_error("null argument"); return FN_ERR_ARG; }
+  note_stream(s, stream);
   dispatch(s, [&](auto m) { launch_init_params<decltype(m)>(s, seed, d_params, (cudaStream_t)stream); return 0; });
   return check_launch(s, "init_params");
 }
@@ -468,6 +485,7 @@ fn_status fn_init_walkers(fn_system_t s, int B, uint64_t seed, double init_std, 
     if (st != FN_OK) return st;
   }
   if (counts_out) std::memcpy(counts_out, s->counts.data(), sizeof(int) * s->M);
+  note_stream(s, stream);
   dispatch(s, [&](auto m) { launch_init_walkers<decltype(m)>(s, B, seed, init_std, d_walkers, (cudaStream_t)stream); return 0; });
   return check_launch(s, "init_walkers");
 }
@@ -475,7 +493,7 @@ fn_status fn_init_walkers(fn_system_t s, int B, uint64_t seed, double init_std, 
 fn_status fn_log_psi(fn_system_t s, const void* d_params, const void* d_walkers, int B,
                      double* d_log_psi, int8_t* d_sign, void* stream) {
   if (!s || !d_params || !d_walkers || B < 1 || !d_log_psi) { set_error("invalid argument"); return FN_ERR_ARG; }
-  fn_status st = ensure_workspace(s, B);
+  fn_status st = ensure_workspace(s, B, (cudaStream_t)stream);
   if (st != FN_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
   dispatch(s, [&](auto m) {
@@ -492,7 +510,7 @@ fn_status fn_log_psi(fn_system_t s, const void* d_params, const void* d_walkers,
 fn_status fn_local_energy(fn_system_t s, const void* d_params, const void* d_walkers, int B,
                           double* d_e_local, double* d_log_psi, int8_t* d_sign, void* stream) {
   if (!s || !d_params || !d_walkers || B < 1 || !d_e_local) { set_error("invalid argument"); return FN_ERR_ARG; }
-  fn_status st = ensure_workspace(s, B);
+  fn_status st = ensure_workspace(s, B, (cudaStream_t)stream);
   if (st != FN_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
   dispatch(s, [&](auto m) {
@@ -513,7 +531,7 @@ fn_status fn_mcmc_steps(fn_system_t s, const void* d_params, void* d_walkers, do
     set_error("invalid argument"); return FN_ERR_ARG;
   }
   if (n_steps == 0) return FN_OK;
-  fn_status st = ensure_workspace(s, B);
+  fn_status st = ensure_workspace(s, B, (cudaStream_t)stream);
   if (st != FN_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
   dispatch(s, [&](auto m) {
@@ -537,7 +555,7 @@ fn_status fn_energy_grad(fn_system_t s, const void* d_params, const void* d_walk
   if (!s || !d_params || !d_walkers || !d_e_local || !d_grad || B < 1) {
     set_error("invalid argument"); return FN_ERR_ARG;
   }
-  fn_status st = ensure_workspace(s, B);
+  fn_status st = ensure_workspace(s, B, (cudaStream_t)stream);
   if (st != FN_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
   dispatch(s, [&](auto m) {
@@ -558,7 +576,7 @@ fn_status fn_log_psi_vjp(fn_system_t s, const void* d_params, const void* d_walk
   if (!s || !d_params || !d_walkers || !d_weights || !d_grad || B < 1) {
     set_error("invalid argument"); return FN_ERR_ARG;
   }
-  fn_status st = ensure_workspace(s, B);
+  fn_status st = ensure_workspace(s, B, (cudaStream_t)stream);
   if (st != FN_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
   dispatch(s, [&](auto m) {
@@ -583,7 +601,7 @@ fn_status fn_adam_step(fn_system_t s, void* d_params, const void* d_grad, void* 
   if (!s || !d_params || !d_grad || !d_m || !d_v || t < 1 || !adam_args_ok(lr, beta1, beta2, eps)) {
     set_error("invalid argument"); return FN_ERR_ARG;
   }
-  fn_status st = ensure_workspace(s, 1);   // holds the device status word
+  fn_status st = ensure_workspace(s, 1, (cudaStream_t)stream);   // holds the device status word
   if (st != FN_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
   dispatch(s, [&](auto m) {
@@ -595,7 +613,7 @@ fn_status fn_adam_step(fn_system_t s, void* d_params, const void* d_grad, void* 
 
 fn_status fn_sgd_step(fn_system_t s, void* d_params, const void* d_grad, double lr, void* stream) {
   if (!s || !d_params || !d_grad || !std::isfinite(lr)) { set_error("invalid argument"); return FN_ERR_ARG; }
-  fn_status st = ensure_workspace(s, 1);
+  fn_status st = ensure_workspace(s, 1, (cudaStream_t)stream);
   if (st != FN_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
   dispatch(s, [&](auto m) {
@@ -610,7 +628,7 @@ fn_status fn_clip_local_energy(fn_system_t s, const double* d_e_local, int B, do
   if (!s || !d_e_local || !d_e_clipped || B < 1 || !std::isfinite(width)) {
     set_error("invalid argument"); return FN_ERR_ARG;
   }
-  fn_status st = ensure_workspace(s, 1);
+  fn_status st = ensure_workspace(s, 1, (cudaStream_t)stream);
   if (st != FN_OK) return st;
   launch_clip_energy(s, B, d_e_local, width, d_e_clipped, d_stats, (cudaStream_t)stream);
   return check_launch(s, "clip_local_energy");
@@ -625,7 +643,7 @@ fn_status fn_vmc_iteration(fn_system_t s, const fn_train_config* c, void* d_para
       (c->optimizer == FN_OPT_ADAM && (!d_opt_state || !adam_args_ok(c->lr, c->beta1, c->beta2, c->eps)))) {
     set_error("invalid argument"); return FN_ERR_ARG;
   }
-  fn_status st = ensure_workspace(s, B);
+  fn_status st = ensure_workspace(s, B, (cudaStream_t)stream);
   if (st != FN_OK) return st;
   cudaStream_t cs = (cudaStream_t)stream;
   const size_t par_bytes = s->cfg.precision == FN_FP64 ? sizeof(double) : sizeof(float);
@@ -670,9 +688,31 @@ fn_status fn_vmc_iteration(fn_system_t s, const fn_train_config* c, void* d_para
   return check_launch(s, "vmc_iteration");
 }
 
+fn_status fn_energy_moments(fn_system_t s, const double* d_e_local, int B, double* d_moments, void* stream) {
+  if (!s || !d_e_local || !d_moments || B < 1) { set_error("invalid argument"); return FN_ERR_ARG; }
+  note_stream(s, stream);
+  launch_energy_moments(s, B, d_e_local, d_moments, (cudaStream_t)stream);
+  return check_launch(s, "energy_moments");
+}
+
+fn_status fn_energy_stats(fn_system_t s, const double* d_moments, double* d_stats, void* stream) {
+  if (!s || !d_moments || !d_stats) { set_error("invalid argument"); return FN_ERR_ARG; }
+  note_stream(s, stream);
+  launch_energy_stats(s, d_moments, d_stats, (cudaStream_t)stream);
+  return check_launch(s, "energy_stats");
+}
+
+fn_status fn_energy_weights(fn_system_t s, const double* d_e_local, int B, const double* d_moments, double* d_weights,
+                            void* stream) {
+  if (!s || !d_e_local || !d_moments || !d_weights || B < 1) { set_error("invalid argument"); return FN_ERR_ARG; }
+  note_stream(s, stream);
+  launch_energy_weights_from(s, B, d_e_local, d_moments, d_weights, (cudaStream_t)stream);
+  return check_launch(s, "energy_weights");
+}
+
 fn_status fn_selftest_expired_wait(fn_system_t s, int wait_us, void* stream) {
   if (!s || wait_us < 1 || wait_us > 100000) { set_error("invalid argument"); return FN_ERR_ARG; }
-  fn_status st = ensure_workspace(s, 1);   // holds the device status word
+  fn_status st = ensure_workspace(s, 1, (cudaStream_t)stream);   // holds the device status word
   if (st != FN_OK) return st;
   launch_expired_wait(s, wait_us, (cudaStream_t)stream);
   return check_launch(s, "selftest_expired_wait");
@@ -709,12 +749,14 @@ fn_status fn_sync(fn_system_t s, void* stream, int timeout_ms) {
     if (timeout_ms >= 0 && el > timeout_ms) { set_error("fn_sync deadline passed"); return FN_ERR_TIMEOUT; }
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
+  // the status word is read and cleared in the order of this stream (already drained)
   int word = 0;
-  cudaError_t e = cudaMemcpy(&word, s->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpyAsync(&word, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   if (e != cudaSuccess) return cuda_status(e, "status read");
   if (word) {
-    const int zero = 0;
-    cudaMemcpy(s->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemsetAsync(s->d_status, 0, sizeof(int), cs);
+    cudaStreamSynchronize(cs);
     set_error(word & kStatusTimeout ? "a bounded kernel wait expired (timeout bit)"
               : (word & kStatusSingular ? "all determinants singular for some walker" : "non-finite result"));
     if (word & kStatusTimeout) return FN_ERR_TIMEOUT;

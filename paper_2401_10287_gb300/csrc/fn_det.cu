@@ -15,6 +15,8 @@
 //   * E_L = -1/2 (|grad|^2 + lap) + V_ee + V_ne + V_nn (Eqs. 2-3).
 // All of it runs in the Det type (FP64 in the FP64 and BF16-mixed modes).
 #include <algorithm>
+#include <climits>
+#include <type_traits>
 
 #include "fn_device.cuh"
 #include "fn_internal.cuh"
@@ -54,6 +56,13 @@ template <> __device__ __forceinline__ double widen<double, float>(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// Pivot search key: |v| as an unsigned integer (the bit patterns of non-negative IEEE
+// numbers order like their values), so the comparisons leave the FP64 pipe alone.
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned int abs_key(float v) { return __float_as_uint(v) & 0x7FFFFFFFu; }
+
 template <typename Det>
 __device__ void thread_lu(Det* A, int n, int ST, int* perm, Det* rcp, Det* ld_out, Det* sign_out) {
   Det sgn = 1, mant = 1;
@@ -62,12 +71,12 @@ __device__ void thread_lu(Det* A, int n, int ST, int* perm, Det* rcp, Det* ld_ou
   for (int i = 0; i < n; ++i) perm[i * ST] = i;
   for (int c = 0; c < n; ++c) {
     int piv = c;
-    Det best = f_abs(A[(c * n + c) * ST]);
+    auto best = abs_key(A[(c * n + c) * ST]);
     for (int r = c + 1; r < n; ++r) {
-      const Det v = f_abs(A[(r * n + c) * ST]);
+      const auto v = abs_key(A[(r * n + c) * ST]);
       if (v > best) { best = v; piv = r; }
     }
-    if (!(best > (Det)0)) { singular = true; break; }
+    if (best == 0) { singular = true; break; }
     if (piv != c) {
       for (int j = 0; j < n; ++j) {
         const Det t = A[(c * n + j) * ST];
@@ -192,6 +201,94 @@ __device__ __forceinline__ void tangent_item(const Det* Cm, int ST, const PhiT* 
   }
 }
 
+// ---- double-FP32 tangent products (BF16-mixed mode) -------------------------------------
+// In the BF16-mixed mode the orbital tangents D are FP32 values and C = A^-1 is FP64.  The
+// products B = C D, g = tr B and q = tr(B^2) are evaluated in double-FP32 arithmetic on the
+// FP32 pipe, which on this part runs 64 times as many operations per clock as the FP64
+// pipe: C = c_hi + c_lo (two FP32 values, 48 significant bits), every D entry is exact in
+// FP32, each product c_hi d is split exactly by an FMA (Dekker's two-product), sums are
+// accumulated with Knuth's error-free two-sum and the small terms (c_lo d, the rounding
+// errors) in a second FP32 word.  The result carries about 46 significant bits, converted to
+// FP64 at the end; the LU, the inverse and every later step stay FP64.
+__device__ __forceinline__ void ff_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (sh, sl) += (xh, xl) * (yh, yl) * scale, scale = 1 or 2 (exact)
+__device__ __forceinline__ void ff_fma_acc(float xh, float xl, float yh, float yl, float scale, float& sh,
+                                           float& sl) {
+  const float p = __fmul_rn(xh, yh);
+  float pe = __fmaf_rn(xh, yh, -p);
+  pe = __fmaf_rn(xh, yl, __fmaf_rn(xl, yh, pe));
+  float s, e;
+  ff_two_sum(sh, __fmul_rn(p, scale), s, e);
+  sh = s;
+  sl = __fadd_rn(sl, __fmaf_rn(pe, scale, e));
+}
+
+template <int NN>
+__device__ __forceinline__ void tangent_item_ff(const float* __restrict__ Ch, const float* __restrict__ Cl, int ST,
+                                                const float* __restrict__ D, double* g_out, double* q_out) {
+  float bh[NN][NN], bl[NN][NN];
+#pragma unroll
+  for (int i = 0; i < NN; ++i)
+#pragma unroll
+    for (int j = 0; j < NN; ++j) { bh[i][j] = 0.f; bl[i][j] = 0.f; }
+#pragma unroll
+  for (int m = 0; m < NN; ++m) {
+    float d[NN];
+#pragma unroll
+    for (int j = 0; j < NN; ++j) d[j] = D[m * NN + j];
+#pragma unroll
+    for (int i = 0; i < NN; ++i) {
+      const float ch = Ch[(i * NN + m) * ST], cl = Cl[(i * NN + m) * ST];
+#pragma unroll
+      for (int j = 0; j < NN; ++j) {
+        const float p = __fmul_rn(ch, d[j]);
+        const float pe = __fmaf_rn(ch, d[j], -p);
+        float s, e;
+        ff_two_sum(bh[i][j], p, s, e);
+        bh[i][j] = s;
+        bl[i][j] = __fmaf_rn(cl, d[j], __fadd_rn(bl[i][j], __fadd_rn(e, pe)));
+      }
+    }
+  }
+  float gh = 0.f, gl = 0.f, qh = 0.f, ql = 0.f;
+#pragma unroll
+  for (int i = 0; i < NN; ++i) {
+    float s, e;
+    ff_two_sum(gh, bh[i][i], s, e);
+    gh = s;
+    gl = __fadd_rn(gl, __fadd_rn(e, bl[i][i]));
+    ff_fma_acc(bh[i][i], bl[i][i], bh[i][i], bl[i][i], 1.f, qh, ql);
+#pragma unroll
+    for (int j = i + 1; j < NN; ++j) ff_fma_acc(bh[i][j], bl[i][j], bh[j][i], bl[j][i], 2.f, qh, ql);
+  }
+  *g_out = (double)gh + (double)gl;
+  *q_out = (double)qh + (double)ql;
+}
+
+template <typename Det, typename PhiT>
+__device__ __forceinline__ bool tangent_item_split(const float* Ch, const float* Cl, int ST, const PhiT* D, int n,
+                                                   Det* g, Det* q) {
+  if constexpr (std::is_same<Det, double>::value && std::is_same<PhiT, float>::value) {
+    switch (n) {
+      case 1: tangent_item_ff<1>(Ch, Cl, ST, D, g, q); return true;
+      case 2: tangent_item_ff<2>(Ch, Cl, ST, D, g, q); return true;
+      case 3: tangent_item_ff<3>(Ch, Cl, ST, D, g, q); return true;
+      case 4: tangent_item_ff<4>(Ch, Cl, ST, D, g, q); return true;
+      case 5: tangent_item_ff<5>(Ch, Cl, ST, D, g, q); return true;
+      case 6: tangent_item_ff<6>(Ch, Cl, ST, D, g, q); return true;
+      case 7: tangent_item_ff<7>(Ch, Cl, ST, D, g, q); return true;
+      case 8: tangent_item_ff<8>(Ch, Cl, ST, D, g, q); return true;
+      default: return false;
+    }
+  }
+  return false;
+}
+
 // Local-energy pass: one CTA per walker.  Threads 0..2K-1 factorise and invert the
 // (determinant, spin) blocks; then every thread takes (block, coordinate) items
 // g_t = tr(C d_t A), q_t = tr((C d_t A)^2) and tr(C lap A); then the determinant terms
@@ -218,6 +315,10 @@ __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, c
   Det* rho = lapk + K;                                   // [K]
   Det* red = rho + K;                                    // [128]
   int* perm = (int*)(red + 128);                         // [nmax][ST]
+  // double-FP32 copies of C (BF16-mixed mode): [nmax^2][ST] high words, then low words
+  constexpr bool kSplit = std::is_same<Det, double>::value && std::is_same<PhiT, float>::value;
+  float* Ch = (float*)(perm + (int64_t)nmax * ST);
+  float* Cl = Ch + (int64_t)nmax * nmax * ST;
   const PhiT* Phi = (const PhiT*)a.Phi + (int64_t)w * a.PW;
   const int64_t blk_off[2] = {0, (int64_t)K * T * ns[0] * ns[0]};
   // value slabs of every block, interleaved by block (thread 2k + spin)
@@ -238,6 +339,14 @@ __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, c
       thread_lu<Det>(A + tid, n, ST, perm + tid, rcp + tid, ld2 + tid, sg2 + tid);
       if (sg2[tid] != 0) thread_inverse<Det>(A + tid, perm + tid, rcp + tid, n, ST, C + tid);
       else for (int e = 0; e < n * n; ++e) C[(int64_t)e * ST + tid] = 0;
+      if (kSplit && n <= 8) {
+        for (int e = 0; e < n * n; ++e) {
+          const double c = (double)C[(int64_t)e * ST + tid];
+          const float ch = __double2float_rn(c);
+          Ch[(int64_t)e * ST + tid] = ch;
+          Cl[(int64_t)e * ST + tid] = __double2float_rn(c - (double)ch);
+        }
+      }
     }
   }
   __syncthreads();
@@ -255,7 +364,7 @@ __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, c
     const PhiT* D = Phi + blk_off[sp] + (int64_t)k * T * n * n + (int64_t)t * n * n;
     if (tr < NC) {
       Det g, q;
-      tangent_item<Det, PhiT>(Cm, ST, D, n, &g, &q);
+      if (!tangent_item_split<Det, PhiT>(Ch + p, Cl + p, ST, D, n, &g, &q)) tangent_item<Det, PhiT>(Cm, ST, D, n, &g, &q);
       gt[p * NC + tr] = g;
       qt[p * NC + tr] = q;
     } else {
@@ -419,14 +528,14 @@ __global__ void k_det_value(Shape sh, DetArgs a) {
 template <int NN, int C, typename Det>
 struct LuStep {
   static __device__ __forceinline__ void run(Det (&a)[NN][NN], Det& sgn, Det& mant, int& expo, bool& singular) {
-    Det best = f_abs(a[C][C]);
+    auto best = abs_key(a[C][C]);
     int piv = C;
 #pragma unroll
     for (int r = C + 1; r < NN; ++r) {
-      const Det v = f_abs(a[r][C]);
+      const auto v = abs_key(a[r][C]);
       if (v > best) { best = v; piv = r; }
     }
-    if (!(best > (Det)0)) singular = true;
+    if (best == 0) singular = true;
 #pragma unroll
     for (int r = C + 1; r < NN; ++r) {
       const bool sw = r == piv;
@@ -461,44 +570,45 @@ struct LuStep<NN, NN, Det> {
 };
 
 template <int NN, typename Det, typename PhiT>
-__device__ __forceinline__ void lu_regs(const PhiT* __restrict__ Ag, Det* ld_out, Det* sign_out) {
+__device__ __forceinline__ void lu_regs(const PhiT* __restrict__ Ag, Det* mant_out, int* expo_out) {
   Det a[NN][NN];
 #pragma unroll
   for (int i = 0; i < NN; ++i)
 #pragma unroll
-    for (int j = 0; j < NN; ++j) a[i][j] = (Det)Ag[i * NN + j];
+    for (int j = 0; j < NN; ++j) a[i][j] = widen<Det, PhiT>(Ag[i * NN + j]);
   Det sgn = 1, mant = 1;
   int expo = 0;
   bool singular = false;
   LuStep<NN, 0, Det>::run(a, sgn, mant, expo, singular);
-  if (singular) {
-    *ld_out = 0;
-    *sign_out = 0;
-    return;
-  }
-  *sign_out = mant < 0 ? -sgn : sgn;
-  *ld_out = f_log(f_abs(mant)) + (Det)expo * (Det)0.6931471805599453;
+  *mant_out = singular ? (Det)0 : sgn * mant;
+  *expo_out = singular ? 0 : expo;
 }
 
+// det A = mant 2^expo with |mant| in [1/2, 1) (mant = 0 for a singular block)
 template <typename Det, typename PhiT>
-__device__ __forceinline__ void lu_regs_any(const PhiT* Ag, int n, Det* ld, Det* sg) {
+__device__ __forceinline__ void lu_regs_any(const PhiT* Ag, int n, Det* mant, int* expo) {
   switch (n) {
-    case 1: lu_regs<1, Det, PhiT>(Ag, ld, sg); break;
-    case 2: lu_regs<2, Det, PhiT>(Ag, ld, sg); break;
-    case 3: lu_regs<3, Det, PhiT>(Ag, ld, sg); break;
-    case 4: lu_regs<4, Det, PhiT>(Ag, ld, sg); break;
-    case 5: lu_regs<5, Det, PhiT>(Ag, ld, sg); break;
-    case 6: lu_regs<6, Det, PhiT>(Ag, ld, sg); break;
-    case 7: lu_regs<7, Det, PhiT>(Ag, ld, sg); break;
-    default: lu_regs<8, Det, PhiT>(Ag, ld, sg); break;
+    case 1: lu_regs<1, Det, PhiT>(Ag, mant, expo); break;
+    case 2: lu_regs<2, Det, PhiT>(Ag, mant, expo); break;
+    case 3: lu_regs<3, Det, PhiT>(Ag, mant, expo); break;
+    case 4: lu_regs<4, Det, PhiT>(Ag, mant, expo); break;
+    case 5: lu_regs<5, Det, PhiT>(Ag, mant, expo); break;
+    case 6: lu_regs<6, Det, PhiT>(Ag, mant, expo); break;
+    case 7: lu_regs<7, Det, PhiT>(Ag, mant, expo); break;
+    default: lu_regs<8, Det, PhiT>(Ag, mant, expo); break;
   }
 }
 
 // Value pass without the backward seed, blocks of at most 8 x 8: one thread per
-// (determinant, spin) block, 128 / (2K) walkers per CTA, no shared-memory staging.
+// (determinant, spin) block, 128 / (2K) walkers per CTA, no shared-memory staging.  Each
+// block's determinant is kept as mantissa x 2^exponent; a walker's K terms
+// D_k = det A_k,up det A_k,down are summed after scaling by 2^(e_k - max e), so that
+// log|psi| = log|S| + (max e) ln 2 takes one logarithm per walker and no exponential
+// (the same signed log-sum-exp, without forming log|D_k|).
 template <typename Det, typename PhiT>
-__global__ void __launch_bounds__(128) k_det_value_small(Shape sh, DetArgs a) {
-  __shared__ Det ld2[128], sg2[128];
+__global__ void __launch_bounds__(128, 3) k_det_value_small(Shape sh, DetArgs a) {
+  __shared__ Det mt2[128];
+  __shared__ int ex2[128];
   const int K = a.K, NM = 2 * K;
   const int per_cta = 128 / NM;
   const int wl = threadIdx.x / NM, p = threadIdx.x % NM;
@@ -507,30 +617,30 @@ __global__ void __launch_bounds__(128) k_det_value_small(Shape sh, DetArgs a) {
   if (wl < per_cta && w < sh.B) {
     const int k = p >> 1, sp = p & 1, n = ns[sp];
     if (n == 0) {
-      ld2[threadIdx.x] = 0;
-      sg2[threadIdx.x] = 1;
+      mt2[threadIdx.x] = (Det)1;
+      ex2[threadIdx.x] = 0;
     } else {
       const PhiT* A = (const PhiT*)a.Phi + (int64_t)w * a.PW + (sp ? (int64_t)K * ns[0] * ns[0] : 0) +
                       (int64_t)k * n * n;
-      lu_regs_any<Det, PhiT>(A, n, ld2 + threadIdx.x, sg2 + threadIdx.x);
+      lu_regs_any<Det, PhiT>(A, n, mt2 + threadIdx.x, ex2 + threadIdx.x);
     }
   }
   __syncthreads();
   if (threadIdx.x < per_cta) {
     const int w2 = blockIdx.x * per_cta + threadIdx.x;
     if (w2 < sh.B) {
-      const Det* l = ld2 + threadIdx.x * NM;
-      const Det* g = sg2 + threadIdx.x * NM;
-      Det m = -INFINITY;
+      const Det* mt = mt2 + threadIdx.x * NM;
+      const int* ex = ex2 + threadIdx.x * NM;
+      int emax = INT_MIN;
       for (int k = 0; k < K; ++k)
-        if (g[2 * k] * g[2 * k + 1] != 0 && l[2 * k] + l[2 * k + 1] > m) m = l[2 * k] + l[2 * k + 1];
+        if (mt[2 * k] * mt[2 * k + 1] != 0 && ex[2 * k] + ex[2 * k + 1] > emax) emax = ex[2 * k] + ex[2 * k + 1];
       Det S = 0;
       for (int k = 0; k < K; ++k) {
-        const Det sk = g[2 * k] * g[2 * k + 1];
-        if (sk != 0) S += sk * f_exp(l[2 * k] + l[2 * k + 1] - m);
+        const Det mk = mt[2 * k] * mt[2 * k + 1];
+        if (mk != 0) S += ldexp(mk, ex[2 * k] + ex[2 * k + 1] - emax);
       }
-      const double lpsi = (double)(m + f_log(f_abs(S)));
       const int sgn = S > 0 ? 1 : (S < 0 ? -1 : 0);
+      const double lpsi = sgn == 0 ? (double)f_log(f_abs(S)) : (double)(f_log(f_abs(S)) + (Det)emax * (Det)0.6931471805599453);
       if (a.log_psi) a.log_psi[w2] = lpsi;
       if (a.sign) a.sign[w2] = (int8_t)sgn;
       if (sgn == 0) atomicOr(a.status, kStatusSingular);
@@ -558,7 +668,8 @@ void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh,
   const int nmax = std::max(s->n_up, s->n_dn), K = s->cfg.n_dets;
   ProfScope ps(s->prof, full ? kProfDetFull : kProfDetValue, st);
   if (full) {
-    const size_t smem = smem_det_energy(sizeof(Det), nmax, s->N, K);
+    const size_t smem = smem_det_energy(sizeof(Det), nmax, s->N, K,
+                                        std::is_same<Det, double>::value && std::is_same<PhiT, float>::value);
     cudaFuncSetAttribute(k_det_energy<Det, Wlk, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_det_energy<Det, Wlk, PhiT><<<sh.B, 128, smem, st>>>((const Wlk*)walkers, s->d_nuclei, sh, a);
   } else if (!keep_inverse && nmax <= 8) {

@@ -120,9 +120,10 @@ static std::vector<CopyDesc> build_descs(const fn_system* s, bool with16) {
 
 fn_status upload_prep_descs(fn_system* s) {
   std::vector<CopyDesc> v = build_descs(s, s->cfg.precision == FN_BF16_MIXED);
-  cudaError_t e = cudaMalloc(&s->d_descs, sizeof(CopyDesc) * v.size());
+  cudaError_t e = cudaMallocAsync(&s->d_descs, sizeof(CopyDesc) * v.size(), cudaStreamPerThread);
   if (e == cudaSuccess)
-    e = cudaMemcpy(s->d_descs, v.data(), sizeof(CopyDesc) * v.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(s->d_descs, v.data(), sizeof(CopyDesc) * v.size(), cudaMemcpyHostToDevice, cudaStreamPerThread);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamPerThread);
   if (e != cudaSuccess) return cuda_status(e, "parameter descriptor upload");
   s->n_descs = (int)v.size();
   return FN_OK;

@@ -105,11 +105,13 @@ inline size_t smem_pair_full_mma(int N, int L, int ibm) {
 }
 // k_pair_bwd_mma (BF16)
 inline size_t smem_pair_bwd_mma(int N) { return 2 * 32 * kBwdWLd * 2 + (size_t)2 * ((N * N + 15) & ~15) * 33 * 4; }
-// k_det_energy: every (determinant, spin) matrix of one walker with its 3N tangent traces
-inline size_t smem_det_energy(int det_bytes, int nmax, int N, int K) {
+// k_det_energy: every (determinant, spin) matrix of one walker with its 3N tangent traces;
+// with split = true (BF16-mixed mode) also the double-FP32 copy of every inverse
+inline size_t smem_det_energy(int det_bytes, int nmax, int N, int K, bool split = false) {
   const int ST = (int)round_up(2 * K, 32), NC = 3 * N;
   return (size_t)det_bytes * ((size_t)2 * nmax * nmax * ST + (size_t)nmax * ST + 4 * K + 4 * K * NC + 2 * K + K * NC +
-                              2 * K + 128) + sizeof(int) * (size_t)nmax * ST;
+                              2 * K + 128) + sizeof(int) * (size_t)nmax * ST +
+         (split ? sizeof(float) * 2 * (size_t)nmax * nmax * ST : 0);
 }
 // k_det_value (value passes with more than 8 electrons of a spin, and the gradient's pass with inverses)
 inline size_t smem_det_value(int det_bytes, int nmax, int K, bool inv) {
@@ -230,6 +232,8 @@ struct fn_system {
   int* d_elec_atom = nullptr;    // [N]
   void* d_descs = nullptr;       // parameter-preparation copy descriptors
   int n_descs = 0;
+  void* last_stream = nullptr;   // stream of the latest call that enqueued work (frees are ordered on it)
+  bool stream_seen = false;
   fn::Profiler* prof = nullptr;  // kernel-class timing (fn_profile_enable)
   fn_status host_error = FN_OK;  // set by a launcher that could not enqueue its kernel
 };
@@ -287,6 +291,11 @@ template <class Mode> void launch_sgd(const fn_system* s, void* params, const vo
                                       cudaStream_t st);
 void launch_clip_energy(const fn_system* s, int B, const double* e, double width, double* out, double* stats,
                         cudaStream_t st);
+// Eq. 1 statistics and Eq. 6 weights from summable moments [count, sum E_L, sum E_L^2] (fn_optim.cu).
+void launch_energy_moments(const fn_system* s, int B, const double* e, double* mom, cudaStream_t st);
+void launch_energy_stats(const fn_system* s, const double* mom, double* stats, cudaStream_t st);
+void launch_energy_weights_from(const fn_system* s, int B, const double* e, const double* mom, double* w,
+                                cudaStream_t st);
 // Failure-path self-test (fn_selftest.cu): a barrier wait that expires after wait_us.
 void launch_expired_wait(const fn_system* s, int wait_us, cudaStream_t st);
 

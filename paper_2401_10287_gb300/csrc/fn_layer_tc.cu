@@ -250,6 +250,7 @@ struct TcArgs {
   // split weights: columns [0, k) hold bf16(W), columns [bsplit, bsplit + k) hold
   // bf16(W - bf16(W)); every k-block is multiplied by both (0 = no split)
   int bsplit;
+  int stages;            // A ring depth of the resident-weight layer kernel
 };
 
 
@@ -778,6 +779,369 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+
+// ---- stream layer with the weights resident in shared memory ----------------------------
+// The layer's split weights for this CTA's nt output columns (hi and lo parts of every
+// k-block, nkb x 2 x nt x 128 B: 160 KB at k_self = 320, nt = 128) are loaded by TMA once
+// per CTA; the ring then carries only the A tiles (16 KB per k-block), as many stages as
+// the remaining shared memory holds.  The epilogue reads the residual (the layer input's
+// first h1 columns of the same rows, just loaded through L2 for the A operand) and the
+// walker's mean-field row with plain vector loads issued before the accumulator wait, and
+// processes 32 columns per tensor-memory round trip (accumulator, h and sum z^2 loaded
+// together under one wait).
+struct ResLayout {
+  uint32_t b_bytes;      // resident weights
+  int stages;            // A ring depth
+  size_t total;          // dynamic shared memory of the launch
+};
+
+__host__ __device__ inline ResLayout res_layout(int nkb, int nt, int stages) {
+  ResLayout l;
+  l.b_bytes = (uint32_t)nkb * 2u * (uint32_t)nt * 128u;
+  l.stages = stages;
+  l.total = 1024 + (size_t)l.b_bytes + (size_t)stages * 128 * 128 + 8 * (2 * (size_t)stages + 6) + 16;
+  return l;
+}
+
+// Wait for the tensor-memory loads in flight; the registers are operands so that no use of
+// them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld48(uint32_t (&a)[16], uint32_t (&b)[16], uint32_t (&c)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+                 "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]),
+                 "+r"(a[15]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]),
+                 "+r"(b[7]), "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]),
+                 "+r"(b[14]), "+r"(b[15]), "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3]), "+r"(c[4]), "+r"(c[5]),
+                 "+r"(c[6]), "+r"(c[7]), "+r"(c[8]), "+r"(c[9]), "+r"(c[10]), "+r"(c[11]), "+r"(c[12]),
+                 "+r"(c[13]), "+r"(c[14]), "+r"(c[15])
+               :
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+__device__ __forceinline__ float2 bf2_to_f2(uint32_t u) {
+  return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+__device__ __forceinline__ uint32_t f2_to_bf2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *(const uint32_t*)&h;
+}
+
+// 16 columns [cb, cb + 16) of this thread's row: accumulator (and h, sum z^2 for the
+// tangent and Laplacian slabs) already in registers; m = the mean-field row piece, res the
+// residual piece (8 bf16 per uint4).  Returns the 16 outputs packed as bf16 pairs.
+template <int KIND>
+__device__ __forceinline__ void res_piece(const uint32_t (&acc)[16], uint32_t (&hv)[16], uint32_t (&sq)[16],
+                                          const float4 (&m)[4], const uint4 (&res)[2], uint32_t (&o)[8],
+                                          float (&outf)[16]) {
+  const uint32_t* rr = (const uint32_t*)res;
+  if (KIND == 0) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float mv = j % 4 == 0 ? m[j / 4].x : (j % 4 == 1 ? m[j / 4].y : (j % 4 == 2 ? m[j / 4].z : m[j / 4].w));
+      const float h = tanh_fast(__uint_as_float(acc[j]) + mv);
+      hv[j] = __float_as_uint(h);
+      sq[j] = 0u;
+      const float2 r2 = bf2_to_f2(rr[j >> 1]);
+      outf[j] = h + ((j & 1) ? r2.y : r2.x);
+    }
+#pragma unroll
+    for (int p = 0; p < 8; ++p) o[p] = f2_to_bf2(outf[2 * p], outf[2 * p + 1]);
+  } else {
+    const uint64_t m1 = pack_f2(-1.f, -1.f), m2 = pack_f2(-2.f, -2.f);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      const float4 m4 = m[p >> 1];
+      const uint64_t z2 = add_f2(pack_f2(__uint_as_float(acc[2 * p]), __uint_as_float(acc[2 * p + 1])),
+                                 (p & 1) ? pack_f2(m4.z, m4.w) : pack_f2(m4.x, m4.y));
+      const uint64_t h2 = pack_f2(__uint_as_float(hv[2 * p]), __uint_as_float(hv[2 * p + 1]));
+      const uint64_t s2 = pack_f2(__uint_as_float(sq[2 * p]), __uint_as_float(sq[2 * p + 1]));
+      const uint64_t nd2 = fma_f2(h2, h2, m1);                  // -(1 - h^2)
+      uint64_t w2;
+      if (KIND == 1) {
+        w2 = z2;
+        float s0, s1;
+        unpack_f2(fma_f2(z2, z2, s2), s0, s1);
+        sq[2 * p] = __float_as_uint(s0);
+        sq[2 * p + 1] = __float_as_uint(s1);
+      } else {
+        w2 = fma_f2(mul_f2(h2, s2), m2, z2);                    // z - 2 h sum z^2
+      }
+      const float2 r2 = bf2_to_f2(rr[p]);
+      float a0, a1;
+      unpack_f2(sub_f2(pack_f2(r2.x, r2.y), mul_f2(nd2, w2)), a0, a1);
+      o[p] = f2_to_bf2(a0, a1);
+    }
+  }
+}
+
+template <bool FULL>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_layer_res(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int nt = a.nt, nkb = a.nkb;
+  const uint32_t bytesA = 128 * 128, bytesB = (uint32_t)nt * 128;
+  const ResLayout lay = res_layout(nkb, nt, a.stages);
+  const int NS = lay.stages;
+  unsigned char* sB = base;                                   // [nkb][hi, lo] weight tiles
+  unsigned char* sA = sB + lay.b_bytes;                       // NS A tiles
+  uint64_t* bars = (uint64_t*)(sA + (size_t)NS * bytesA);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + NS;
+  uint64_t* accf = bars + 2 * NS;
+  uint64_t* acce = accf + 2;
+  uint64_t* bfull = acce + 2;
+  uint64_t* mma_done = bfull + 1;
+  uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Shape& sh = a.sh;
+  const int ctile = blockIdx.x;
+  const int my_tiles = a.tiles > (int)blockIdx.y ? (a.tiles - 1 - (int)blockIdx.y) / (int)gridDim.y + 1 : 0;
+  const int T = sh.T;
+  const int n_items = my_tiles * T;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(accf + b, 1); mbar_init(acce + b, kEpiWarps); }
+    mbar_init(bfull, 1);
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint64_t deadline = globaltimer() + kWaitNs * 8 * (uint64_t)(my_tiles > 0 ? my_tiles : 1);
+
+  if (warp == 0) {
+    if (lane == 0 && n_items > 0) {
+      // the CTA's weights, once
+      mbar_expect_tx(bfull, lay.b_bytes);
+      for (int kb = 0; kb < nkb; ++kb)
+        for (int part = 0; part < 2; ++part)
+          tma_load_2d(sB + (size_t)(kb * 2 + part) * bytesB, &tmB, bfull, part * a.bsplit + kb * kBlockK, ctile * nt);
+      int issued = 0;
+      bool ok = true;
+      for (int item = 0; item < n_items && ok; ++item) {
+        const int tile = (int)blockIdx.y + (item / T) * (int)gridDim.y, t = item % T;
+        const int arow = (int)(t * sh.R + (int64_t)tile * 128);
+        const int lo_row = (int)(a.alo_row + (int64_t)t * sh.R + (int64_t)tile * 128);
+        const int lf = lo_first<kEpiLayer>(a, t, 0, nkb);
+        const int n_k = nkb + (nkb - lf);
+        for (int kk = 0; kk < n_k; ++kk, ++issued) {
+          const bool lo = kk >= nkb;
+          const int kb = lo ? lf + (kk - nkb) : kk;
+          const int stage = issued % NS;
+          const uint32_t round = (uint32_t)(issued / NS);
+          if (*abort_flag || !mbar_wait(empty + stage, (round & 1u) ^ 1u, deadline)) { ok = false; break; }
+          mbar_expect_tx(full + stage, bytesA);
+          tma_load_2d(sA + (size_t)stage * bytesA, &tmA, full + stage, kb * kBlockK, lo ? lo_row : arow);
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(a.status, kStatusTimeout);
+      }
+      // wait (bounded) for the copies still in flight before the CTA can exit
+      const uint64_t dl2 = globaltimer() + kWaitNs;
+      mbar_wait(bfull, 0u, dl2);
+      for (int q = issued > NS ? issued - NS : 0; q < issued; ++q)
+        mbar_wait(full + (q % NS), (uint32_t)((q / NS) & 1), dl2);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(128, nt);
+      int consumed = 0;
+      bool ok = n_items == 0 || (!*abort_flag && mbar_wait(bfull, 0u, deadline));
+      for (int item = 0; item < n_items && ok; ++item) {
+        const int buf = item & 1;
+        const uint32_t use = (uint32_t)(item >> 1);
+        if (*abort_flag || !mbar_wait(acce + buf, (use & 1u) ^ 1u, deadline)) { ok = false; break; }
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * nt);
+        const int t = item % T;
+        const int lf = lo_first<kEpiLayer>(a, t, 0, nkb);
+        const int n_k = nkb + (nkb - lf);
+        for (int kk = 0; kk < n_k; ++kk, ++consumed) {
+          const bool lo = kk >= nkb;
+          const int kb = lo ? lf + (kk - nkb) : kk;
+          const int parts = lo ? 1 : 2;
+          const int stage = consumed % NS;
+          const uint32_t round = (uint32_t)(consumed / NS);
+          if (*abort_flag || !mbar_wait(full + stage, round & 1u, deadline)) { ok = false; break; }
+          fence_after();
+          const uint64_t da = sdesc(smem_u32(sA + (size_t)stage * bytesA));
+          for (int part = 0; part < parts; ++part) {
+            const uint64_t db = sdesc(smem_u32(sB + (size_t)(kb * 2 + part) * bytesB));
+#pragma unroll
+            for (int k4 = 0; k4 < kBlockK / 16; ++k4)
+              mma_bf16(d, da + (uint64_t)(2 * k4), db + (uint64_t)(2 * k4), idesc,
+                       (kk != 0 || k4 != 0 || part != 0) ? 1u : 0u);
+          }
+          mma_commit(empty + stage);
+        }
+        if (ok) mma_commit(accf + buf);
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(a.status, kStatusTimeout);
+      }
+      mma_commit(mma_done);
+      mbar_wait(mma_done, 0u, globaltimer() + kWaitNs);
+    }
+  } else {
+    const int q = warp & 3;                       // TMEM lane quarter this warp may access
+    const int r = q * 32 + lane;
+    const int ehalf = (warp - 2) >> 2;            // column half: chunks cc with cc % 2 == ehalf
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const int nchunks = nt / 32;
+    const int n0 = ctile * nt;
+    const int wl = r / sh.N;
+    const int64_t yslab = sh.R * a.ldy;
+    for (int item = 0; item < n_items; ++item) {
+      const int t = item % T;
+      const int tile = (int)blockIdx.y + (item / T) * (int)gridDim.y;
+      const int buf = item & 1;
+      const uint32_t use = (uint32_t)(item >> 1);
+      const int64_t row = (int64_t)tile * 128 + r;
+      const int w = tile * sh.wpt + wl;
+      const bool valid = wl < sh.wpt && w < sh.B;
+      const int kind = t == 0 ? 0 : (t < T - 1 ? 1 : 2);
+      // residual pieces of this thread's (up to) two chunks, loaded before the wait
+      uint4 res[2][4];
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const int cc = 2 * it + ehalf;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) res[it][v] = make_uint4(0u, 0u, 0u, 0u);
+        if (a.residual && valid && cc < nchunks) {
+          const uint4* xp = (const uint4*)(a.X + t * sh.R * (int64_t)a.ldx + row * a.ldx + n0 + cc * 32);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) res[it][v] = __ldg(xp + v);
+        }
+      }
+      const float* mrow = a.Mterm + ((int64_t)t * sh.B + min(w, sh.B - 1)) * a.h1 + n0;
+      bool ok = !*abort_flag && mbar_wait(accf + buf, use & 1u, deadline);
+      if (epilogue_any(!ok)) {
+        if (threadIdx.x == 64) {
+          *abort_flag = 1;
+          atomicOr(a.status, kStatusTimeout);
+        }
+        break;
+      }
+      fence_after();
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const int cc = 2 * it + ehalf;
+        if (cc >= nchunks) break;                 // warp-uniform
+        const int cb = cc * 32;
+        const int col0 = n0 + cb;
+        __nv_bfloat16* yrow = a.Y + t * yslab + row * a.ldy + col0;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          // mean-field row piece (L1/L2) and the tensor-memory loads in flight together
+          float4 m[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) m[v] = __ldg((const float4*)(mrow + cb + hh * 16) + v);
+          uint32_t acc[16], hv[16], sq[16];
+          tmem_ld16_nowait(tmem + lane_base + (uint32_t)(buf * nt + cb + hh * 16), acc);
+          if (FULL && kind != 0) {
+            tmem_ld16_nowait(tmem + lane_base + (uint32_t)(2 * nt + cb + hh * 16), hv);
+            tmem_ld16_nowait(tmem + lane_base + (uint32_t)(3 * nt + cb + hh * 16), sq);
+          }
+          tmem_wait_ld48(acc, hv, sq);
+          const uint4 rp[2] = {res[it][2 * hh], res[it][2 * hh + 1]};
+          uint32_t o[8];
+          float outf[16];
+          if (kind == 0) res_piece<0>(acc, hv, sq, m, rp, o, outf);
+          else if (kind == 1) res_piece<1>(acc, hv, sq, m, rp, o, outf);
+          else res_piece<2>(acc, hv, sq, m, rp, o, outf);
+          if (valid && col0 < a.h1) {
+            uint4* yo = (uint4*)(yrow + hh * 16);
+            if (kind == 0 && a.residual && a.alo_row > 0) {
+              // the value slab's residual is a pair: add its low part (slab T of X)
+              const uint4* xl = (const uint4*)(a.X + (int64_t)T * sh.R * a.ldx + row * a.ldx + col0 + hh * 16);
+#pragma unroll
+              for (int v = 0; v < 2; ++v) {
+                const uint4 u = xl[v];
+                const uint32_t* uu = (const uint32_t*)&u;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const float2 f = bf2_to_f2(uu[e]);
+                  outf[8 * v + 2 * e] += f.x;
+                  outf[8 * v + 2 * e + 1] += f.y;
+                }
+              }
+#pragma unroll
+              for (int p = 0; p < 8; ++p) o[p] = f2_to_bf2(outf[2 * p], outf[2 * p + 1]);
+            }
+            yo[0] = make_uint4(o[0], o[1], o[2], o[3]);
+            yo[1] = make_uint4(o[4], o[5], o[6], o[7]);
+            if (kind == 0) {
+              if (a.alo_row > 0) {
+                uint32_t ol[8];
+#pragma unroll
+                for (int p = 0; p < 8; ++p) ol[p] = f2_to_bf2(bf16_rem(outf[2 * p]), bf16_rem(outf[2 * p + 1]));
+                uint4* yl = (uint4*)(a.Y + (int64_t)T * yslab + row * a.ldy + col0 + hh * 16);
+                yl[0] = make_uint4(ol[0], ol[1], ol[2], ol[3]);
+                yl[1] = make_uint4(ol[4], ol[5], ol[6], ol[7]);
+              }
+              if (a.act_out) {
+                float4* ao = (float4*)(a.act_out + row * a.h1 + col0 + hh * 16);
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                  ao[v] = make_float4(__uint_as_float(hv[4 * v]), __uint_as_float(hv[4 * v + 1]),
+                                      __uint_as_float(hv[4 * v + 2]), __uint_as_float(hv[4 * v + 3]));
+              }
+            }
+          }
+          if (FULL) {
+            if (!valid) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) { hv[j] = 0u; sq[j] = 0u; }
+            }
+            if (kind == 0) {
+              tmem_st16(tmem + lane_base + (uint32_t)(2 * nt + cb + hh * 16), hv);
+              tmem_st16(tmem + lane_base + (uint32_t)(3 * nt + cb + hh * 16), sq);
+            } else if (kind == 1) {
+              tmem_st16(tmem + lane_base + (uint32_t)(3 * nt + cb + hh * 16), sq);
+            }
+          }
+        }
+        if (FULL) tmem_wait_st();
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce + buf);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+  }
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------------------------------
@@ -895,6 +1259,23 @@ bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, int lo
   const bool full = sh.T > 1;
   a.tmem_cols = pow2_cols(full ? 4 * nt : 2 * nt);
   a.tiles = sh.tiles;
+  // weights resident in shared memory when they fit beside an A ring of two or more stages
+  const uint32_t b_bytes = tc::res_layout(a.nkb, nt, 0).b_bytes;
+  int stages = 0;
+  while (stages < 8 && tc::res_layout(a.nkb, nt, stages + 1).total <= kMaxDynamicSmem) ++stages;
+  if (b_bytes > 0 && stages >= 2) {
+    a.stages = stages;
+    const size_t smem = tc::res_layout(a.nkb, nt, stages).total;
+    const dim3 grid = persistent_grid(h1 / nt, sh.tiles);
+    if (full) {
+      cudaFuncSetAttribute(tc::k_layer_res<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      tc::k_layer_res<true><<<grid, tc::kThreads, smem, st>>>(ta, tb, a);
+    } else {
+      cudaFuncSetAttribute(tc::k_layer_res<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      tc::k_layer_res<false><<<grid, tc::kThreads, smem, st>>>(ta, tb, a);
+    }
+    return true;
+  }
   launch_tc<tc::kEpiLayer>(ta, tb, a, persistent_grid(h1 / nt, sh.tiles), full, st);
   return true;
 }

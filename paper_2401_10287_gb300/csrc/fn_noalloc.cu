@@ -108,6 +108,8 @@ static fn_status log_psi_noalloc(fn_system* s, const void* params, const void* w
               " walkers of this system)");
     return FN_ERR_ARG;
   }
+  s->last_stream = (void*)st;          // the handle's small buffers are in use on this stream
+  s->stream_seen = true;
   void* base = nullptr;
   fn_status r = scratch_address(&base);
   if (r != FN_OK) return r;

@@ -203,6 +203,72 @@ void launch_clip_energy(const fn_system* s, int B, const double* e, double width
   k_clip_energy<<<1, kClipThreads, 0, st>>>(B, e, width, out, stats, s->ws.status);
 }
 
+// ---- Eq. 1 estimator and the Eq. 6 weights ------------------------------------------------
+// The VMC energy is the mean local energy over the walkers (Eq. 1) and its statistical
+// error follows from their variance; Eq. 6 weights every walker by 2 (E_L - mean) / count.
+// The moments [count, sum E_L, sum E_L^2] add up across batches (and across devices), so a
+// batch split over several GPUs sums them (one all-reduce of three numbers) before the
+// statistics or the weights are formed.  One CTA, FP64, fixed summation order.
+constexpr int kStatThreads = 1024;
+
+__global__ void __launch_bounds__(kStatThreads) k_energy_moments(int B, const double* __restrict__ e,
+                                                                  double* __restrict__ mom) {
+  __shared__ double s1[kStatThreads], s2[kStatThreads];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < B; i += kStatThreads) {
+    const double x = e[i];
+    a += x;
+    b += x * x;
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int off = kStatThreads / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) {
+      s1[threadIdx.x] += s1[threadIdx.x + off];
+      s2[threadIdx.x] += s2[threadIdx.x + off];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    mom[0] = (double)B;
+    mom[1] = s1[0];
+    mom[2] = s2[0];
+  }
+}
+
+__global__ void k_energy_stats(const double* __restrict__ mom, double* __restrict__ stats, int* __restrict__ status) {
+  const double n = mom[0], mean = mom[1] / n;
+  const double var = fmax(0.0, mom[2] / n - mean * mean);
+  stats[0] = n;
+  stats[1] = mean;
+  stats[2] = var;
+  if (!isfinite(mean) || !isfinite(var)) atomicOr(status, kStatusNonFinite);
+}
+
+__global__ void k_energy_weights_from(int B, const double* __restrict__ e, const double* __restrict__ mom,
+                                      double* __restrict__ w) {
+  const double n = mom[0], mean = mom[1] / n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B; i += gridDim.x * blockDim.x)
+    w[i] = 2.0 * (e[i] - mean) / n;
+}
+
+void launch_energy_moments(const fn_system* s, int B, const double* e, double* mom, cudaStream_t st) {
+  ProfScope ps(s->prof, kProfOptim, st);
+  k_energy_moments<<<1, kStatThreads, 0, st>>>(B, e, mom);
+}
+
+void launch_energy_stats(const fn_system* s, const double* mom, double* stats, cudaStream_t st) {
+  ProfScope ps(s->prof, kProfOptim, st);
+  k_energy_stats<<<1, 1, 0, st>>>(mom, stats, s->d_status);
+}
+
+void launch_energy_weights_from(const fn_system* s, int B, const double* e, const double* mom, double* w,
+                                cudaStream_t st) {
+  ProfScope ps(s->prof, kProfOptim, st);
+  k_energy_weights_from<<<elementwise_grid(s, B), 256, 0, st>>>(B, e, mom, w);
+}
+
 #define FN_INST_OPTIM(M)                                                                                        \
   template void launch_adam<M>(const fn_system*, void*, const void*, void*, void*, int64_t, double, double,      \
                                double, double, cudaStream_t);                                                    \

@@ -8,8 +8,9 @@ is a sum over all walkers:
     E_bar = sum_r sum_w E_L / sum_r B_r
     g     = sum_r sum_w 2 (E_L,w - E_bar) / B_total * d log|psi_w| / d theta
 
-so each rank all-reduces [sum E_L, B_r], forms its weights with the global mean and
-count, computes its shard's weighted gradient (fn_log_psi_vjp) and all-reduces it.
+so each rank all-reduces the moments [B_r, sum E_L, sum E_L^2] (fn_energy_moments), forms its
+weights from the global moments (fn_energy_weights), computes its shard's weighted gradient
+(fn_log_psi_vjp) and all-reduces it.
 
 A training iteration (``train_step``) adds two things:
 * clipping uses the window of the whole batch: every rank gathers all ranks' local energies
@@ -23,18 +24,24 @@ import torch
 import torch.distributed as dist
 
 
-def global_mean_and_count(e_local: torch.Tensor, group=None):
-    """(global mean E_L, global walker count) by one all-reduce of [sum, count]."""
-    stats = torch.stack([e_local.to(torch.float64).sum(),
-                         torch.tensor(float(e_local.numel()), dtype=torch.float64, device=e_local.device)])
-    dist.all_reduce(stats, group=group)
-    return stats[0] / stats[1], stats[1]
+def global_moments(system, e_local: torch.Tensor, group=None) -> torch.Tensor:
+    """[total count, sum E_L, sum E_L^2] over every rank: the library's moments of this rank's
+    energies (fn_energy_moments), summed by one all-reduce of three numbers."""
+    mom = system.energy_moments(e_local.to(torch.float64).contiguous())
+    dist.all_reduce(mom, group=group)
+    return mom
 
 
-def energy_weights(e_local: torch.Tensor, group=None) -> torch.Tensor:
-    """Per-walker weights 2 (E_L,w - E_bar) / B_total of Eq. 6 with the global mean and count."""
-    mean, count = global_mean_and_count(e_local, group)
-    return 2.0 * (e_local.to(torch.float64) - mean) / count
+def global_mean_and_count(system, e_local: torch.Tensor, group=None):
+    """(global mean E_L, global walker count) from the all-reduced moments (fn_energy_stats)."""
+    stats = system.energy_stats(global_moments(system, e_local, group))
+    return stats[1], stats[0]
+
+
+def energy_weights(system, e_local: torch.Tensor, group=None) -> torch.Tensor:
+    """Per-walker weights 2 (E_L,w - E_bar) / B_total of Eq. 6 with the global mean and count
+    (fn_energy_weights on the all-reduced moments)."""
+    return system.energy_weights(e_local.to(torch.float64).contiguous(), global_moments(system, e_local, group))
 
 
 def allreduce_gradient(grad: torch.Tensor, group=None) -> torch.Tensor:
@@ -45,7 +52,7 @@ def allreduce_gradient(grad: torch.Tensor, group=None) -> torch.Tensor:
 
 def energy_gradient(system, params, walkers, e_local, group=None):
     """Eq. 6 gradient of the whole data-parallel batch, computed shard-wise."""
-    w = energy_weights(e_local, group)
+    w = energy_weights(system, e_local, group)
     g = system.log_psi_vjp(params, walkers, w)
     return allreduce_gradient(g, group)
 

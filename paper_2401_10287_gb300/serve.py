@@ -114,7 +114,8 @@ class LibraryBackend:
         handle.busy = False
 
     def destroy(self, key: str, handle):
-        self.torch.cuda.synchronize()
+        # the library frees the handle's device memory in the order of the handle's last
+        # stream; nothing here waits for the device
         self.handles[key].remove(handle)
         handle.close()
 
@@ -151,14 +152,16 @@ class LibraryBackend:
         h, req, st = job.handle, job.req, job.state
         with torch.cuda.stream(stream):
             e, _, _ = h.local_energy(self.params[req.key], st["walkers"], stream=stream)
-            stats = torch.stack([e.mean(), e.var(unbiased=False), st["accepted"].to(torch.float64)[0]])
-            host = torch.empty(3, dtype=torch.float64, pin_memory=True)
-            host.copy_(stats, non_blocking=True)
+            # Eq. 1: mean local energy and its variance, in the library
+            stats = h.energy_stats(h.energy_moments(e, stream=stream), stream=stream)
+            host = torch.empty(4, dtype=torch.float64, pin_memory=True)
+            host[:3].copy_(stats, non_blocking=True)
+            host[3:].copy_(st["accepted"], non_blocking=True)
         st["host"] = host
         return self._mark(stream)
 
     def collect(self, job: _Active):
-        m, v, acc = (float(x) for x in job.state["host"])
+        _, m, v, acc = (float(x) for x in job.state["host"])
         req = job.req
         return m, math.sqrt(max(v, 0.0) / req.n_walkers), acc / max(1, req.mcmc_steps * req.n_walkers)
 

@@ -21,6 +21,22 @@ def _data():
     return e, dlogpsi
 
 
+class _Moments:
+    """CPU stand-in for the library's Eq. 1 / Eq. 6 calls (fn_energy_moments, fn_energy_stats,
+    fn_energy_weights, whose GPU versions are tested against numpy in tests/test_gpu_stats.py):
+    the test here is the exchange, not the arithmetic."""
+
+    def energy_moments(self, e):
+        return torch.stack([torch.tensor(float(e.numel()), dtype=torch.float64), e.sum(), (e * e).sum()])
+
+    def energy_stats(self, m):
+        mean = m[1] / m[0]
+        return torch.stack([m[0], mean, m[2] / m[0] - mean * mean])
+
+    def energy_weights(self, e, m):
+        return 2.0 * (e - m[1] / m[0]) / m[0]
+
+
 def _worker(rank, world, port, out_path):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -28,10 +44,11 @@ def _worker(rank, world, port, out_path):
     e, d = _data()
     lo, hi = (0, 20) if rank == 0 else (20, 37)
     e_l = torch.tensor(e[lo:hi])
-    w = dp.energy_weights(e_l)
+    sysm = _Moments()
+    w = dp.energy_weights(sysm, e_l)
     g = torch.tensor(w.numpy() @ d[lo:hi])       # the shard's weighted gradient (what fn_log_psi_vjp returns)
     dp.allreduce_gradient(g)
-    mean, count = dp.global_mean_and_count(e_l)
+    mean, count = dp.global_mean_and_count(sysm, e_l)
     if rank == 0:
         np.save(out_path, np.concatenate([g.numpy(), [mean.item(), count.item()]]))
     dist.barrier()

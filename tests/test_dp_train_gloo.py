@@ -56,6 +56,12 @@ class CpuStandIn:
     def sgd_step(self, params, g, lr):
         params.sub_(lr * g)
 
+    def energy_moments(self, e):
+        return torch.stack([torch.tensor(float(e.numel()), dtype=torch.float64), e.sum(), (e * e).sum()])
+
+    def energy_weights(self, e, m):
+        return 2.0 * (e - m[1] / m[0]) / m[0]
+
 
 def _walkers():
     return torch.from_numpy(np.random.default_rng(7).standard_normal((B, N, 3)))
