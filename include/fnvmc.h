@@ -193,6 +193,28 @@ fn_status fn_log_psi_vjp(fn_system_t sys, const void* d_params, const void* d_wa
 fn_status fn_log_psi_noalloc(fn_system_t sys, const void* d_params, const void* d_walkers,
                              int n_walkers, double* d_log_psi, int8_t* d_sign, void* stream);
 
+/* ---- Eq. 5 pretraining -------------------------------------------------------------------
+ * Before the energy is optimised, the method fits the network's orbitals to Hartree-Fock
+ * orbitals at the sampled positions (Eq. 5): L = (1/B) sum_w sum_spin sum_{k,i,j}
+ * (Phi_kij - Phi^HF_ij)^2, k the determinant, i the orbital, j the electron of that spin,
+ * B the walkers; the same occupied UHF orbital i (STO-6G, in order of orbital energy, signed
+ * so that its largest-magnitude coefficient is positive) is the target of every determinant. */
+
+/* Runs unrestricted Hartree-Fock in STO-6G for the system (nuclei H..Ne, at most 20 basis
+ * functions, the system's n_up and n_down) on the host and keeps its occupied orbitals on the
+ * device for fn_pretrain_grad.  h_energy [1] receives the UHF energy (NULL to skip).
+ * FN_ERR_ARG for other elements, FN_ERR_UNSUPPORTED above 20 functions or when occupied
+ * levels are degenerate (the target is then not unique), FN_ERR_NUMERIC if it does not
+ * converge.  Synchronous; call it once per system.                                          */
+fn_status fn_pretrain_setup(fn_system_t sys, double* h_energy);
+
+/* Eq. 5 loss of the walkers and its parameter gradient: the value-only forward pass, the
+ * HF orbitals at every electron, dL/dPhi, and the hand-written reverse pass of fn_energy_grad
+ * from that seed.  d_grad [fn_param_count] blob dtype; d_loss [1] double (NULL to skip).
+ * FN_ERR_ARG if fn_pretrain_setup was not called.                                           */
+fn_status fn_pretrain_grad(fn_system_t sys, const void* d_params, const void* d_walkers, int n_walkers,
+                           void* d_grad, double* d_loss, void* stream);
+
 /* ---- Eq. 1 estimator and Eq. 6 weights from summable moments ------------------------
  * The VMC energy is the mean local energy over the sampled walkers (Eq. 1); its error bar
  * follows from their variance.  The moments [count, sum E_L, sum E_L^2] (FP64) add up over

@@ -38,6 +38,8 @@ SIGNATURES = {
     "fn_energy_grad": (C.c_int, [_P, _P, _P, _P, C.c_int, _P, _P, _P]),
     "fn_log_psi_noalloc": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P]),
     "fn_log_psi_vjp": (C.c_int, [_P, _P, _P, _P, C.c_int, _P, _P]),
+    "fn_pretrain_setup": (C.c_int, [_P, _D]),
+    "fn_pretrain_grad": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, _P]),
     "fn_energy_moments": (C.c_int, [_P, _P, C.c_int, _P, _P]),
     "fn_energy_stats": (C.c_int, [_P, _P, _P, _P]),
     "fn_energy_weights": (C.c_int, [_P, _P, C.c_int, _P, _P, _P]),

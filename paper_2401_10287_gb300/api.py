@@ -234,6 +234,23 @@ class System:
                                         _stream(stream)))
         return g
 
+    def pretrain_setup(self) -> float:
+        """UHF/STO-6G of this molecule on the host; its occupied orbitals become the Eq. 5
+        targets of pretrain_grad.  Returns the UHF energy."""
+        e = np.zeros(1)
+        _check(self._lib.fn_pretrain_setup(self._h, e.ctypes.data_as(_lib._D)))
+        return float(e[0])
+
+    def pretrain_grad(self, params, walkers, stream=None):
+        """(gradient of the Eq. 5 loss [param_count] blob dtype, loss [1] float64)."""
+        self._check_walkers(params, walkers)
+        B = walkers.shape[0]
+        g = torch.empty(self.param_count, dtype=self.dtype, device=walkers.device)
+        loss = torch.empty(1, dtype=torch.float64, device=walkers.device)
+        _check(self._lib.fn_pretrain_grad(self._h, _ptr(params), _ptr(walkers), B, _ptr(g), _ptr(loss),
+                                          _stream(stream)))
+        return g, loss
+
     def energy_moments(self, e_local, stream=None) -> torch.Tensor:
         """[count, sum E_L, sum E_L^2] (float64, on the device); sums over batches and devices."""
         _check_f64(e_local, e_local.numel(), "e_local")

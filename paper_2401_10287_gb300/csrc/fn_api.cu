@@ -428,7 +428,7 @@ fn_status fn_create_system(const double* h_nuclei, const double* h_charges, int 
 fn_status fn_destroy_system(fn_system_t s) {
   if (!s) return FN_OK;
   const cudaStream_t st = s->stream_seen ? (cudaStream_t)s->last_stream : cudaStreamPerThread;
-  void* bufs[4] = {s->ws.base, s->d_nuclei, s->d_elec_atom, s->d_descs};
+  void* bufs[5] = {s->ws.base, s->d_nuclei, s->d_elec_atom, s->d_descs, s->d_hf};
   for (void* p : bufs) {
     if (!p) continue;
     if (cudaFreeAsync(p, st) != cudaSuccess) {
@@ -686,6 +686,30 @@ fn_status fn_vmc_iteration(fn_system_t s, const fn_train_config* c, void* d_para
     return 0;
   });
   return check_launch(s, "vmc_iteration");
+}
+
+fn_status fn_pretrain_setup(fn_system_t s, double* h_energy) {
+  if (!s) { set_error("null system"); return FN_ERR_ARG; }
+  return upload_hf_state(s, h_energy);
+}
+
+fn_status fn_pretrain_grad(fn_system_t s, const void* d_params, const void* d_walkers, int B, void* d_grad,
+                           double* d_loss, void* stream) {
+  if (!s || !d_params || !d_walkers || !d_grad || B < 1) { set_error("invalid argument"); return FN_ERR_ARG; }
+  if (!s->d_hf) { set_error("fn_pretrain_setup has not been called for this system"); return FN_ERR_ARG; }
+  fn_status st = ensure_workspace(s, B, (cudaStream_t)stream);
+  if (st != FN_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  dispatch(s, [&](auto m) {
+    using Mode = decltype(m);
+    const Shape sh = make_shape(s, B, 1);
+    launch_prep_params<Mode>(s, d_params, cs);
+    launch_forward<Mode>(s, d_walkers, sh, true, cs);
+    launch_pretrain_seed<Mode>(s, d_walkers, sh, d_loss, cs);
+    launch_backward<Mode>(s, d_walkers, sh, s->ws.scratch_d, d_grad, cs);
+    return 0;
+  });
+  return check_launch(s, "pretrain_grad");
 }
 
 fn_status fn_energy_moments(fn_system_t s, const double* d_e_local, int B, double* d_moments, void* stream) {

@@ -232,6 +232,8 @@ struct fn_system {
   int* d_elec_atom = nullptr;    // [N]
   void* d_descs = nullptr;       // parameter-preparation copy descriptors
   int n_descs = 0;
+  double* d_hf = nullptr;        // UHF state for the Eq. 5 pretraining loss (fn_pretrain_setup)
+  int hf_nbf = 0;                // its basis functions (0: not set up)
   void* last_stream = nullptr;   // stream of the latest call that enqueued work (frees are ordered on it)
   bool stream_seen = false;
   fn::Profiler* prof = nullptr;  // kernel-class timing (fn_profile_enable)
@@ -291,6 +293,10 @@ template <class Mode> void launch_sgd(const fn_system* s, void* params, const vo
                                       cudaStream_t st);
 void launch_clip_energy(const fn_system* s, int B, const double* e, double width, double* out, double* stats,
                         cudaStream_t st);
+// Eq. 5 pretraining (fn_pretrain.cu, fn_scf.cu): UHF state upload, the loss and its seeds.
+fn_status upload_hf_state(fn_system* s, double* e_out);
+template <class Mode> void launch_pretrain_seed(const fn_system* s, const void* walkers, const Shape& sh,
+                                                double* loss, cudaStream_t st);
 // Eq. 1 statistics and Eq. 6 weights from summable moments [count, sum E_L, sum E_L^2] (fn_optim.cu).
 void launch_energy_moments(const fn_system* s, int B, const double* e, double* mom, cudaStream_t st);
 void launch_energy_stats(const fn_system* s, const double* mom, double* stats, cudaStream_t st);

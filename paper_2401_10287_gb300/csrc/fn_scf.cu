@@ -364,7 +364,8 @@ static bool solve(int n, std::vector<double> A, std::vector<double> b, std::vect
 constexpr int kDampIters = 30;
 
 static bool scf_from(const Mat& F0, int n, const Mat& S, const Mat& H, const std::vector<double>& G, const Mat& X,
-                     int n_a, int n_b, double e_nn, double* e_out, Mat* P_out) {
+                     int n_a, int n_b, double e_nn, double* e_out, Mat* P_out, Mat* Fa_out = nullptr,
+                     Mat* Fb_out = nullptr) {
   const size_t n2 = (size_t)n * n;
   Mat Pa = density(n, F0, X, n_a), Pb = density(n, F0, X, n_b);
   std::vector<Mat> hF_a, hF_b, hErr;
@@ -401,6 +402,8 @@ static bool scf_from(const Mat& F0, int n, const Mat& S, const Mat& H, const std
       P_out->assign(n2, 0.0);
       for (size_t k = 0; k < n2; ++k) (*P_out)[k] = Pa[k] + Pb[k];
       *e_out = e;
+      if (Fa_out) *Fa_out = Fa;
+      if (Fb_out) *Fb_out = Fb;
       return true;
     }
     e_old = e;
@@ -447,7 +450,40 @@ static bool scf_from(const Mat& F0, int n, const Mat& S, const Mat& H, const std
   return false;
 }
 
-static fn_status run(const double* nuc, const double* Z, int M, int n_a, int n_b, double* q_out, double* e_out) {
+// Occupied UHF orbitals of the converged state (the targets of the Eq. 5 pretraining loss):
+// the eigenvectors of each spin's Fock matrix in the orthogonalised basis, the n_occ lowest in
+// order of orbital energy, back-transformed (C = X C'), each signed so that its
+// largest-magnitude coefficient is positive.
+struct HfOrbitals {
+  std::vector<Shell> basis;
+  Mat C[2];              // [nbf][n_occ] per spin
+  int n_occ[2] = {0, 0};
+  double energy = 0;
+};
+
+static bool occupied_orbitals(int n, const Mat& F, const Mat& X, int n_occ, Mat* C_out) {
+  const Mat Fp = matmul(n, matmul(n, X, F, true), X);
+  std::vector<double> e;
+  Mat Cp;
+  jacobi(n, Fp, &e, &Cp);
+  const Mat C = matmul(n, X, Cp);
+  // a degenerate highest occupied level, or degenerate occupied levels, make the target not unique
+  if (n_occ > 0 && n_occ < n && std::fabs(e[n_occ] - e[n_occ - 1]) < 1e-8) return false;
+  for (int o = 1; o < n_occ; ++o)
+    if (std::fabs(e[o] - e[o - 1]) < 1e-8) return false;
+  C_out->assign((size_t)n * n_occ, 0.0);
+  for (int o = 0; o < n_occ; ++o) {
+    int big = 0;
+    for (int mu = 1; mu < n; ++mu)
+      if (std::fabs(C[(size_t)mu * n + o]) > std::fabs(C[(size_t)big * n + o])) big = mu;
+    const double sg = C[(size_t)big * n + o] < 0 ? -1.0 : 1.0;
+    for (int mu = 0; mu < n; ++mu) (*C_out)[(size_t)mu * n_occ + o] = sg * C[(size_t)mu * n + o];
+  }
+  return true;
+}
+
+static fn_status run(const double* nuc, const double* Z, int M, int n_a, int n_b, double* q_out, double* e_out,
+                     HfOrbitals* orb = nullptr) {
   std::vector<Shell> bas;
   for (int A = 0; A < M; ++A) {
     const int z = (int)std::lround(Z[A]);
@@ -545,28 +581,81 @@ static fn_status run(const double* nuc, const double* Z, int M, int n_a, int n_b
   }
   bool found = false;
   double e_best = 0;
-  Mat P_best;
+  Mat P_best, Fa_best, Fb_best;
   for (const Mat& F0 : starts) {
     double e;
-    Mat P;
-    if (scf_from(F0, n, S, H, G, X, n_a, n_b, e_nn, &e, &P) && (!found || e < e_best - 1e-9)) {
+    Mat P, Fa, Fb;
+    if (scf_from(F0, n, S, H, G, X, n_a, n_b, e_nn, &e, &P, &Fa, &Fb) && (!found || e < e_best - 1e-9)) {
       found = true;
       e_best = e;
       P_best = P;
+      Fa_best = Fa;
+      Fb_best = Fb;
     }
   }
   if (!found) {
     set_error("Hartree-Fock did not converge in 500 iterations");
     return FN_ERR_NUMERIC;
   }
-  const Mat PS = matmul(n, P_best, S);
-  for (int A = 0; A < M; ++A) q_out[A] = Z[A];
-  for (int mu = 0; mu < n; ++mu) q_out[bas[mu].atom] -= PS[(size_t)mu * n + mu];
+  if (q_out) {
+    const Mat PS = matmul(n, P_best, S);
+    for (int A = 0; A < M; ++A) q_out[A] = Z[A];
+    for (int mu = 0; mu < n; ++mu) q_out[bas[mu].atom] -= PS[(size_t)mu * n + mu];
+  }
   if (e_out) *e_out = e_best;
+  if (orb) {
+    orb->basis = bas;
+    orb->energy = e_best;
+    orb->n_occ[0] = n_a;
+    orb->n_occ[1] = n_b;
+    if (!occupied_orbitals(n, Fa_best, X, n_a, &orb->C[0]) || !occupied_orbitals(n, Fb_best, X, n_b, &orb->C[1])) {
+      set_error("degenerate occupied Hartree-Fock levels: the pretraining target is not unique");
+      return FN_ERR_UNSUPPORTED;
+    }
+  }
+  return FN_OK;
+}
+
+// Uploads the UHF state of the system (STO-6G, the system's own n_up / n_down) for the Eq. 5
+// pretraining loss: per basis function 18 doubles (centre, Cartesian powers, six exponents,
+// six weights), then C_up [nbf][n_up] and C_down [nbf][n_down].
+fn_status upload_hf_state(fn_system* s, double* e_out) {
+  for (int m = 0; m < s->M; ++m) {
+    const double z = s->charges[m];
+    if (!(z >= 1.0 && z <= 10.0)) {
+      set_error("STO-6G Hartree-Fock is provided for H..Ne (integer Z from 1 to 10)");
+      return FN_ERR_ARG;
+    }
+  }
+  HfOrbitals orb;
+  fn_status st = run(s->nuclei.data(), s->charges.data(), s->M, s->n_up, s->n_dn, nullptr, e_out, &orb);
+  if (st != FN_OK) return st;
+  const int nbf = (int)orb.basis.size();
+  std::vector<double> buf;
+  for (const Shell& f : orb.basis) {
+    for (int d = 0; d < 3; ++d) buf.push_back(f.c[d]);
+    for (int d = 0; d < 3; ++d) buf.push_back((double)f.l[d]);
+    for (int k = 0; k < 6; ++k) buf.push_back(f.a[k]);
+    for (int k = 0; k < 6; ++k) buf.push_back(f.w[k]);
+  }
+  for (int q = 0; q < 2; ++q) buf.insert(buf.end(), orb.C[q].begin(), orb.C[q].end());
+  if (s->d_hf) {
+    cudaFreeAsync(s->d_hf, cudaStreamPerThread);
+    s->d_hf = nullptr;
+  }
+  cudaError_t e = cudaMallocAsync(&s->d_hf, sizeof(double) * buf.size(), cudaStreamPerThread);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->d_hf, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, cudaStreamPerThread);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamPerThread);
+  if (e != cudaSuccess) return cuda_status(e, "Hartree-Fock state upload");
+  s->hf_nbf = nbf;
   return FN_OK;
 }
 
 }  // namespace scf
+
+fn_status upload_hf_state(fn_system* s, double* e_out) { return scf::upload_hf_state(s, e_out); }
+
 }  // namespace fn
 
 extern "C" fn_status fn_mulliken_charges(const double* h_nuclei, const double* h_charges, int n_nuclei, int n_up,
