@@ -106,8 +106,10 @@ inline size_t smem_pair_full_mma(int N, int L, int ibm) {
 // k_pair_bwd_mma (BF16)
 inline size_t smem_pair_bwd_mma(int N) { return 2 * 32 * kBwdWLd * 2 + (size_t)2 * ((N * N + 15) & ~15) * 33 * 4; }
 // k_det_energy: every (determinant, spin) matrix of one walker with its 3N tangent traces;
-// with split = true (BF16-mixed mode) also the double-FP32 copy of every inverse
+// with split = true (BF16-mixed mode) also the double-FP32 copy of every inverse of at most
+// 8 x 8 (larger blocks keep the FP64 products)
 inline size_t smem_det_energy(int det_bytes, int nmax, int N, int K, bool split = false) {
+  split = split && nmax <= 8;
   const int ST = (int)round_up(2 * K, 32), NC = 3 * N;
   return (size_t)det_bytes * ((size_t)2 * nmax * nmax * ST + (size_t)nmax * ST + 4 * K + 4 * K * NC + 2 * K + K * NC +
                               2 * K + 128) + sizeof(int) * (size_t)nmax * ST +

@@ -792,16 +792,34 @@ __global__ void __launch_bounds__(kThreads, 1)
 struct ResLayout {
   uint32_t b_bytes;      // resident weights
   int stages;            // A ring depth
+  uint32_t mt_bytes;     // M[t] staging: [2][wpt][nt + 4] floats
+  uint32_t y_bytes;      // output staging of the TMA stores: 1 KB per epilogue warp
   size_t total;          // dynamic shared memory of the launch
 };
 
-__host__ __device__ inline ResLayout res_layout(int nkb, int nt, int stages) {
+__host__ __device__ inline ResLayout res_layout(int nkb, int nt, int stages, int wpt) {
   ResLayout l;
   l.b_bytes = (uint32_t)nkb * 2u * (uint32_t)nt * 128u;
   l.stages = stages;
-  l.total = 1024 + (size_t)l.b_bytes + (size_t)stages * 128 * 128 + 8 * (2 * (size_t)stages + 6) + 16;
+  // rounded up to 128 B: the output staging after it is the source of TMA stores, which
+  // must start on a 128-byte boundary
+  l.mt_bytes = (2u * (uint32_t)wpt * (uint32_t)(nt + 4) * 4u + 127u) & ~127u;
+  l.y_bytes = (uint32_t)kEpiWarps * 1024u;
+  l.total = 1024 + (size_t)l.b_bytes + (size_t)stages * 128 * 128 + l.mt_bytes + l.y_bytes +
+            8 * (2 * (size_t)stages + 6) + 16;
   return l;
 }
+
+// Tile store shared -> global through the tensor map (bulk group of the issuing thread).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"((uint64_t)map),
+               "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Wait for the tensor-memory loads in flight; the registers are operands so that no use of
 // them can be scheduled before the wait.
@@ -836,66 +854,31 @@ __device__ __forceinline__ uint32_t f2_to_bf2(float a, float b) {
   return *(const uint32_t*)&h;
 }
 
-// 16 columns [cb, cb + 16) of this thread's row: accumulator (and h, sum z^2 for the
-// tangent and Laplacian slabs) already in registers; m = the mean-field row piece, res the
-// residual piece (8 bf16 per uint4).  Returns the 16 outputs packed as bf16 pairs.
-template <int KIND>
-__device__ __forceinline__ void res_piece(const uint32_t (&acc)[16], uint32_t (&hv)[16], uint32_t (&sq)[16],
-                                          const float4 (&m)[4], const uint4 (&res)[2], uint32_t (&o)[8],
-                                          float (&outf)[16]) {
-  const uint32_t* rr = (const uint32_t*)res;
-  if (KIND == 0) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float mv = j % 4 == 0 ? m[j / 4].x : (j % 4 == 1 ? m[j / 4].y : (j % 4 == 2 ? m[j / 4].z : m[j / 4].w));
-      const float h = tanh_fast(__uint_as_float(acc[j]) + mv);
-      hv[j] = __float_as_uint(h);
-      sq[j] = 0u;
-      const float2 r2 = bf2_to_f2(rr[j >> 1]);
-      outf[j] = h + ((j & 1) ? r2.y : r2.x);
-    }
-#pragma unroll
-    for (int p = 0; p < 8; ++p) o[p] = f2_to_bf2(outf[2 * p], outf[2 * p + 1]);
-  } else {
-    const uint64_t m1 = pack_f2(-1.f, -1.f), m2 = pack_f2(-2.f, -2.f);
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      const float4 m4 = m[p >> 1];
-      const uint64_t z2 = add_f2(pack_f2(__uint_as_float(acc[2 * p]), __uint_as_float(acc[2 * p + 1])),
-                                 (p & 1) ? pack_f2(m4.z, m4.w) : pack_f2(m4.x, m4.y));
-      const uint64_t h2 = pack_f2(__uint_as_float(hv[2 * p]), __uint_as_float(hv[2 * p + 1]));
-      const uint64_t s2 = pack_f2(__uint_as_float(sq[2 * p]), __uint_as_float(sq[2 * p + 1]));
-      const uint64_t nd2 = fma_f2(h2, h2, m1);                  // -(1 - h^2)
-      uint64_t w2;
-      if (KIND == 1) {
-        w2 = z2;
-        float s0, s1;
-        unpack_f2(fma_f2(z2, z2, s2), s0, s1);
-        sq[2 * p] = __float_as_uint(s0);
-        sq[2 * p + 1] = __float_as_uint(s1);
-      } else {
-        w2 = fma_f2(mul_f2(h2, s2), m2, z2);                    // z - 2 h sum z^2
-      }
-      const float2 r2 = bf2_to_f2(rr[p]);
-      float a0, a1;
-      unpack_f2(sub_f2(pack_f2(r2.x, r2.y), mul_f2(nd2, w2)), a0, a1);
-      o[p] = f2_to_bf2(a0, a1);
-    }
-  }
-}
+// Threads of the resident-weight layer kernel: warpgroup 0 (producer warp, MMA warp, two idle
+// warps) gives registers back (setmaxnreg) to the two epilogue warpgroups, whose threads keep
+// h and sum z^2 of their 64 columns in registers across the slabs of a tile.
+constexpr int kResThreads = 384;
+constexpr int kResRegsLow = 40;        // warpgroup 0 after setmaxnreg.dec
+constexpr int kResRegsHigh = 232;      // epilogue warpgroups after setmaxnreg.inc
+// The launch holds 384 x 168 registers (ptxas gives 168 per thread at 384 threads, one CTA per
+// SM); the split must not exceed it: 128 x 40 + 256 x 232 = 64512 = 384 x 168.
+static_assert(128 * kResRegsLow + 256 * kResRegsHigh <= kResThreads * 168, "register split above the launch");
 
 template <bool FULL>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_layer_res(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+__global__ void __launch_bounds__(kResThreads, 1)
+    k_layer_res(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const __grid_constant__ CUtensorMap tmY, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int nt = a.nt, nkb = a.nkb;
   const uint32_t bytesA = 128 * 128, bytesB = (uint32_t)nt * 128;
-  const ResLayout lay = res_layout(nkb, nt, a.stages);
+  const ResLayout lay = res_layout(nkb, nt, a.stages, a.sh.wpt);
   const int NS = lay.stages;
-  unsigned char* sB = base;                                   // [nkb][hi, lo] weight tiles
+  unsigned char* sB = base;                                   // [nkb][hi rows, lo rows] weight tiles
   unsigned char* sA = sB + lay.b_bytes;                       // NS A tiles
-  uint64_t* bars = (uint64_t*)(sA + (size_t)NS * bytesA);
+  float* mts = (float*)(sA + (size_t)NS * bytesA);            // [2][wpt][nt + 4] M[t] rows
+  uint4* ystage = (uint4*)((unsigned char*)mts + lay.mt_bytes);   // [8 warps][32 rows][2] x 16 B
+  uint64_t* bars = (uint64_t*)((unsigned char*)ystage + lay.y_bytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + NS;
   uint64_t* accf = bars + 2 * NS;
@@ -932,30 +915,34 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_slot;
   const uint64_t deadline = globaltimer() + kWaitNs * 8 * (uint64_t)(my_tiles > 0 ? my_tiles : 1);
 
-  if (warp == 0) {
-    if (lane == 0 && n_items > 0) {
-      // the CTA's weights, once
+  if (warp < 4) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kResRegsLow));
+    if (warp == 0 && lane == 0 && n_items > 0) {
+      // the CTA's weights, once: k-block kb holds W_hi rows then W_lo rows (2 nt rows)
       mbar_expect_tx(bfull, lay.b_bytes);
       for (int kb = 0; kb < nkb; ++kb)
         for (int part = 0; part < 2; ++part)
           tma_load_2d(sB + (size_t)(kb * 2 + part) * bytesB, &tmB, bfull, part * a.bsplit + kb * kBlockK, ctile * nt);
-      int issued = 0;
+      // ring position (stage, phase) and item (tile, t) advance by increments: no division
+      int issued = 0, stage = 0;
+      uint32_t phase = 0;
       bool ok = true;
+      int tile = (int)blockIdx.y, t = 0;
       for (int item = 0; item < n_items && ok; ++item) {
-        const int tile = (int)blockIdx.y + (item / T) * (int)gridDim.y, t = item % T;
         const int arow = (int)(t * sh.R + (int64_t)tile * 128);
         const int lo_row = (int)(a.alo_row + (int64_t)t * sh.R + (int64_t)tile * 128);
         const int lf = lo_first<kEpiLayer>(a, t, 0, nkb);
         const int n_k = nkb + (nkb - lf);
-        for (int kk = 0; kk < n_k; ++kk, ++issued) {
+        for (int kk = 0; kk < n_k; ++kk) {
           const bool lo = kk >= nkb;
           const int kb = lo ? lf + (kk - nkb) : kk;
-          const int stage = issued % NS;
-          const uint32_t round = (uint32_t)(issued / NS);
-          if (*abort_flag || !mbar_wait(empty + stage, (round & 1u) ^ 1u, deadline)) { ok = false; break; }
+          if (*abort_flag || !mbar_wait(empty + stage, phase ^ 1u, deadline)) { ok = false; break; }
           mbar_expect_tx(full + stage, bytesA);
           tma_load_2d(sA + (size_t)stage * bytesA, &tmA, full + stage, kb * kBlockK, lo ? lo_row : arow);
+          ++issued;
+          if (++stage == NS) { stage = 0; phase ^= 1u; }
         }
+        if (++t == T) { t = 0; tile += (int)gridDim.y; }
       }
       if (!ok) {
         *abort_flag = 1;
@@ -966,40 +953,39 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(bfull, 0u, dl2);
       for (int q = issued > NS ? issued - NS : 0; q < issued; ++q)
         mbar_wait(full + (q % NS), (uint32_t)((q / NS) & 1), dl2);
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(128, nt);
-      int consumed = 0;
+    } else if (warp == 1 && lane == 0) {
+      // one MMA of N = 2 nt multiplies the A tile by the stacked [hi; lo] weight rows of a
+      // k-block: accumulator columns [0, nt) get A W_hi, [nt, 2 nt) get A W_lo; two
+      // accumulators of 2 nt columns alternate between items
+      const uint32_t idesc = idesc_bf16(128, 2 * nt);
+      int stage = 0;
+      uint32_t phase = 0;
+      int t = 0;
       bool ok = n_items == 0 || (!*abort_flag && mbar_wait(bfull, 0u, deadline));
+      const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
       for (int item = 0; item < n_items && ok; ++item) {
         const int buf = item & 1;
         const uint32_t use = (uint32_t)(item >> 1);
         if (*abort_flag || !mbar_wait(acce + buf, (use & 1u) ^ 1u, deadline)) { ok = false; break; }
         fence_after();
-        const uint32_t d = tmem + (uint32_t)(buf * nt);
-        const int t = item % T;
+        const uint32_t d = tmem + (uint32_t)(buf * 2 * nt);
         const int lf = lo_first<kEpiLayer>(a, t, 0, nkb);
         const int n_k = nkb + (nkb - lf);
-        for (int kk = 0; kk < n_k; ++kk, ++consumed) {
+        for (int kk = 0; kk < n_k; ++kk) {
           const bool lo = kk >= nkb;
           const int kb = lo ? lf + (kk - nkb) : kk;
-          const int parts = lo ? 1 : 2;
-          const int stage = consumed % NS;
-          const uint32_t round = (uint32_t)(consumed / NS);
-          if (*abort_flag || !mbar_wait(full + stage, round & 1u, deadline)) { ok = false; break; }
+          if (*abort_flag || !mbar_wait(full + stage, phase, deadline)) { ok = false; break; }
           fence_after();
-          const uint64_t da = sdesc(smem_u32(sA + (size_t)stage * bytesA));
-          for (int part = 0; part < parts; ++part) {
-            const uint64_t db = sdesc(smem_u32(sB + (size_t)(kb * 2 + part) * bytesB));
+          const uint64_t da = sdesc(sA_u + (uint32_t)stage * bytesA);
+          const uint64_t db = sdesc(sB_u + (uint32_t)(kb * 2) * bytesB);
 #pragma unroll
-            for (int k4 = 0; k4 < kBlockK / 16; ++k4)
-              mma_bf16(d, da + (uint64_t)(2 * k4), db + (uint64_t)(2 * k4), idesc,
-                       (kk != 0 || k4 != 0 || part != 0) ? 1u : 0u);
-          }
+          for (int k4 = 0; k4 < kBlockK / 16; ++k4)
+            mma_bf16(d, da + (uint64_t)(2 * k4), db + (uint64_t)(2 * k4), idesc, (kk != 0 || k4 != 0) ? 1u : 0u);
           mma_commit(empty + stage);
+          if (++stage == NS) { stage = 0; phase ^= 1u; }
         }
         if (ok) mma_commit(accf + buf);
+        if (++t == T) t = 0;
       }
       if (!ok) {
         *abort_flag = 1;
@@ -1009,77 +995,91 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(mma_done, 0u, globaltimer() + kWaitNs);
     }
   } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kResRegsHigh));
     const int q = warp & 3;                       // TMEM lane quarter this warp may access
     const int r = q * 32 + lane;
-    const int ehalf = (warp - 2) >> 2;            // column half: chunks cc with cc % 2 == ehalf
+    const int ehalf = (warp - 4) >> 2;            // column half: chunks cc with cc % 2 == ehalf
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const int nchunks = nt / 32;
     const int n0 = ctile * nt;
     const int wl = r / sh.N;
+    const int ethread = threadIdx.x - 128;
     const int64_t yslab = sh.R * a.ldy;
+    uint4* ystg = ystage + (warp - 4) * 64;
+    // the 16-column pieces of this thread: chunk cc = 2 (pc / 2) + ehalf (where it exists), half pc % 2
+    const int npieces = (ehalf < nchunks ? 2 : 0) + (2 + ehalf < nchunks ? 2 : 0);
+    // h = tanh z of the value slab and the running sum of z^2 over the tangent slabs, for this
+    // thread's row and columns, kept across the slabs of a tile
+    float hreg[4][16], sreg[4][16];
+    if (n_items > 0) stage_mterm(a, 0, (int)blockIdx.y, n0, mts, ethread);
+    int tile = (int)blockIdx.y, t = 0;
     for (int item = 0; item < n_items; ++item) {
-      const int t = item % T;
-      const int tile = (int)blockIdx.y + (item / T) * (int)gridDim.y;
       const int buf = item & 1;
       const uint32_t use = (uint32_t)(item >> 1);
       const int64_t row = (int64_t)tile * 128 + r;
       const int w = tile * sh.wpt + wl;
       const bool valid = wl < sh.wpt && w < sh.B;
       const int kind = t == 0 ? 0 : (t < T - 1 ? 1 : 2);
-      // residual pieces of this thread's (up to) two chunks, loaded before the wait
-      uint4 res[2][4];
+      // residual pieces (the layer input's columns of this thread), loaded before the wait
+      uint4 res[4][2];
+      const bool has_res = a.residual && valid;
+      const uint4* xres = (const uint4*)(a.X + t * sh.R * (int64_t)a.ldx + row * a.ldx + n0);
 #pragma unroll
-      for (int it = 0; it < 2; ++it) {
-        const int cc = 2 * it + ehalf;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) res[it][v] = make_uint4(0u, 0u, 0u, 0u);
-        if (a.residual && valid && cc < nchunks) {
-          const uint4* xp = (const uint4*)(a.X + t * sh.R * (int64_t)a.ldx + row * a.ldx + n0 + cc * 32);
-#pragma unroll
-          for (int v = 0; v < 4; ++v) res[it][v] = __ldg(xp + v);
+      for (int pc = 0; pc < 4; ++pc) {
+        res[pc][0] = make_uint4(0u, 0u, 0u, 0u);
+        res[pc][1] = make_uint4(0u, 0u, 0u, 0u);
+        if (pc < npieces && has_res) {
+          const int cb = (2 * (pc >> 1) + ehalf) * 32 + (pc & 1) * 16;
+          res[pc][0] = __ldg(xres + cb / 8);
+          res[pc][1] = __ldg(xres + cb / 8 + 1);
         }
       }
-      const float* mrow = a.Mterm + ((int64_t)t * sh.B + min(w, sh.B - 1)) * a.h1 + n0;
+      cp_async_wait_all();
       bool ok = !*abort_flag && mbar_wait(accf + buf, use & 1u, deadline);
+      // (the barrier also publishes every thread's staged M[t] copies)
       if (epilogue_any(!ok)) {
-        if (threadIdx.x == 64) {
+        if (ethread == 0) {
           *abort_flag = 1;
           atomicOr(a.status, kStatusTimeout);
         }
         break;
       }
       fence_after();
+      // the next item's M[t] rows into the other buffer (its readers passed the barrier)
+      int tile1 = tile, t1 = t + 1;
+      if (t1 == T) { t1 = 0; tile1 += (int)gridDim.y; }
+      if (item + 1 < n_items) stage_mterm(a, t1, tile1, n0, mts + ((item + 1) & 1) * sh.wpt * (nt + 4), ethread);
+      const float* mrow = mts + ((item & 1) * sh.wpt + min(wl, sh.wpt - 1)) * (nt + 4);
+      const uint32_t accb = tmem + lane_base + (uint32_t)(buf * 2 * nt);
 #pragma unroll
-      for (int it = 0; it < 2; ++it) {
-        const int cc = 2 * it + ehalf;
-        if (cc >= nchunks) break;                 // warp-uniform
-        const int cb = cc * 32;
+      for (int pc = 0; pc < 4; ++pc) {
+        if (pc >= npieces) break;                 // warp-uniform
+        const int cb = (2 * (pc >> 1) + ehalf) * 32 + (pc & 1) * 16;
         const int col0 = n0 + cb;
-        __nv_bfloat16* yrow = a.Y + t * yslab + row * a.ldy + col0;
+        uint32_t ah[16], al[16], unused[16];
+        tmem_ld16_nowait(accb + (uint32_t)cb, ah);
+        tmem_ld16_nowait(accb + (uint32_t)(nt + cb), al);
+        float4 m[4];
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          // mean-field row piece (L1/L2) and the tensor-memory loads in flight together
-          float4 m[4];
-#pragma unroll
-          for (int v = 0; v < 4; ++v) m[v] = __ldg((const float4*)(mrow + cb + hh * 16) + v);
-          uint32_t acc[16], hv[16], sq[16];
-          tmem_ld16_nowait(tmem + lane_base + (uint32_t)(buf * nt + cb + hh * 16), acc);
-          if (FULL && kind != 0) {
-            tmem_ld16_nowait(tmem + lane_base + (uint32_t)(2 * nt + cb + hh * 16), hv);
-            tmem_ld16_nowait(tmem + lane_base + (uint32_t)(3 * nt + cb + hh * 16), sq);
-          }
-          tmem_wait_ld48(acc, hv, sq);
-          const uint4 rp[2] = {res[it][2 * hh], res[it][2 * hh + 1]};
-          uint32_t o[8];
+        for (int v = 0; v < 4; ++v) m[v] = *((const float4*)(mrow + cb) + v);
+        tmem_wait_ld48(ah, al, unused);
+        const uint32_t* rr = (const uint32_t*)res[pc];
+        uint32_t o[8];
+        if (kind == 0) {
           float outf[16];
-          if (kind == 0) res_piece<0>(acc, hv, sq, m, rp, o, outf);
-          else if (kind == 1) res_piece<1>(acc, hv, sq, m, rp, o, outf);
-          else res_piece<2>(acc, hv, sq, m, rp, o, outf);
-          if (valid && col0 < a.h1) {
-            uint4* yo = (uint4*)(yrow + hh * 16);
-            if (kind == 0 && a.residual && a.alo_row > 0) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float mv = (j & 3) == 0 ? m[j >> 2].x : ((j & 3) == 1 ? m[j >> 2].y : ((j & 3) == 2 ? m[j >> 2].z : m[j >> 2].w));
+            const float h = tanh_fast(__uint_as_float(ah[j]) + __uint_as_float(al[j]) + mv);
+            if (FULL) { hreg[pc][j] = h; sreg[pc][j] = 0.f; }
+            const float2 r2 = bf2_to_f2(rr[j >> 1]);
+            outf[j] = h + ((j & 1) ? r2.y : r2.x);
+            al[j] = __float_as_uint(h);           // h of this piece, for act_out
+          }
+          if (valid) {
+            if (a.residual && a.alo_row > 0) {
               // the value slab's residual is a pair: add its low part (slab T of X)
-              const uint4* xl = (const uint4*)(a.X + (int64_t)T * sh.R * a.ldx + row * a.ldx + col0 + hh * 16);
+              const uint4* xl = (const uint4*)(a.X + (int64_t)T * sh.R * a.ldx + row * a.ldx + col0);
 #pragma unroll
               for (int v = 0; v < 2; ++v) {
                 const uint4 u = xl[v];
@@ -1091,48 +1091,73 @@ __global__ void __launch_bounds__(kThreads, 1)
                   outf[8 * v + 2 * e + 1] += f.y;
                 }
               }
-#pragma unroll
-              for (int p = 0; p < 8; ++p) o[p] = f2_to_bf2(outf[2 * p], outf[2 * p + 1]);
             }
+#pragma unroll
+            for (int p = 0; p < 8; ++p) o[p] = f2_to_bf2(outf[2 * p], outf[2 * p + 1]);
+            uint4* yo = (uint4*)(a.Y + t * yslab + row * a.ldy + col0);
             yo[0] = make_uint4(o[0], o[1], o[2], o[3]);
             yo[1] = make_uint4(o[4], o[5], o[6], o[7]);
-            if (kind == 0) {
-              if (a.alo_row > 0) {
-                uint32_t ol[8];
+            if (a.alo_row > 0) {
 #pragma unroll
-                for (int p = 0; p < 8; ++p) ol[p] = f2_to_bf2(bf16_rem(outf[2 * p]), bf16_rem(outf[2 * p + 1]));
-                uint4* yl = (uint4*)(a.Y + (int64_t)T * yslab + row * a.ldy + col0 + hh * 16);
-                yl[0] = make_uint4(ol[0], ol[1], ol[2], ol[3]);
-                yl[1] = make_uint4(ol[4], ol[5], ol[6], ol[7]);
-              }
-              if (a.act_out) {
-                float4* ao = (float4*)(a.act_out + row * a.h1 + col0 + hh * 16);
+              for (int p = 0; p < 8; ++p) o[p] = f2_to_bf2(bf16_rem(outf[2 * p]), bf16_rem(outf[2 * p + 1]));
+              uint4* yl = (uint4*)(a.Y + (int64_t)T * yslab + row * a.ldy + col0);
+              yl[0] = make_uint4(o[0], o[1], o[2], o[3]);
+              yl[1] = make_uint4(o[4], o[5], o[6], o[7]);
+            }
+            if (a.act_out) {
+              float4* ao = (float4*)(a.act_out + row * a.h1 + col0);
 #pragma unroll
-                for (int v = 0; v < 4; ++v)
-                  ao[v] = make_float4(__uint_as_float(hv[4 * v]), __uint_as_float(hv[4 * v + 1]),
-                                      __uint_as_float(hv[4 * v + 2]), __uint_as_float(hv[4 * v + 3]));
-              }
+              for (int v = 0; v < 4; ++v)
+                ao[v] = make_float4(__uint_as_float(al[4 * v]), __uint_as_float(al[4 * v + 1]),
+                                    __uint_as_float(al[4 * v + 2]), __uint_as_float(al[4 * v + 3]));
             }
           }
-          if (FULL) {
-            if (!valid) {
+        } else if (FULL) {
+          // tangent slab: out = res + (1 - h^2) z, sum z^2 += z^2; Laplacian slab:
+          // out = res + (1 - h^2) (z - 2 h sum z^2); packed two-lane FP32 arithmetic
+          const uint64_t m1 = pack_f2(-1.f, -1.f), m2 = pack_f2(-2.f, -2.f);
 #pragma unroll
-              for (int j = 0; j < 16; ++j) { hv[j] = 0u; sq[j] = 0u; }
+          for (int p = 0; p < 8; ++p) {
+            const float4 m4 = m[p >> 1];
+            const uint64_t z2 = add_f2(add_f2(pack_f2(__uint_as_float(ah[2 * p]), __uint_as_float(ah[2 * p + 1])),
+                                              pack_f2(__uint_as_float(al[2 * p]), __uint_as_float(al[2 * p + 1]))),
+                                       (p & 1) ? pack_f2(m4.z, m4.w) : pack_f2(m4.x, m4.y));
+            const uint64_t h2 = pack_f2(hreg[pc][2 * p], hreg[pc][2 * p + 1]);
+            const uint64_t s2 = pack_f2(sreg[pc][2 * p], sreg[pc][2 * p + 1]);
+            const uint64_t nd2 = fma_f2(h2, h2, m1);              // -(1 - h^2)
+            uint64_t w2;
+            if (kind == 1) {
+              w2 = z2;
+              unpack_f2(fma_f2(z2, z2, s2), sreg[pc][2 * p], sreg[pc][2 * p + 1]);
+            } else {
+              w2 = fma_f2(mul_f2(h2, s2), m2, z2);                // z - 2 h sum z^2
             }
-            if (kind == 0) {
-              tmem_st16(tmem + lane_base + (uint32_t)(2 * nt + cb + hh * 16), hv);
-              tmem_st16(tmem + lane_base + (uint32_t)(3 * nt + cb + hh * 16), sq);
-            } else if (kind == 1) {
-              tmem_st16(tmem + lane_base + (uint32_t)(3 * nt + cb + hh * 16), sq);
-            }
+            const float2 r2 = bf2_to_f2(rr[p]);
+            float a0, a1;
+            unpack_f2(sub_f2(pack_f2(r2.x, r2.y), mul_f2(nd2, w2)), a0, a1);
+            o[p] = valid ? f2_to_bf2(a0, a1) : 0u;  // rows without an electron are written as zero
+          }
+          // the warp's 32 rows x 16 columns go out as one TMA tile store (coalesced) from a
+          // 1 KB staging buffer; its previous store must have finished reading the buffer
+          if (lane == 0) bulk_wait_read0();
+          __syncwarp();
+          ystg[2 * lane] = make_uint4(o[0], o[1], o[2], o[3]);
+          ystg[2 * lane + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(&tmY, ystg, col0, (int)(t * sh.R + (int64_t)tile * 128 + q * 32));
+            bulk_commit();
           }
         }
-        if (FULL) tmem_wait_st();
       }
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acce + buf);
+      if (++t == T) { t = 0; tile += (int)gridDim.y; }
     }
+    cp_async_wait_all();
+    if (lane == 0) bulk_wait0();          // the output stores have completed
   }
   fence_before();
   __syncthreads();
@@ -1170,6 +1195,20 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t cols, int64_t row
   cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// 2-D bf16 tensor map for tile stores: box 16 columns x 32 rows, no swizzle.
+static bool make_store_map(CUtensorMap* m, const void* base, int64_t cols, int64_t rows, int64_t ld) {
+  auto enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {16, 32};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -1260,19 +1299,25 @@ bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, int lo
   a.tmem_cols = pow2_cols(full ? 4 * nt : 2 * nt);
   a.tiles = sh.tiles;
   // weights resident in shared memory when they fit beside an A ring of two or more stages
-  const uint32_t b_bytes = tc::res_layout(a.nkb, nt, 0).b_bytes;
+  const uint32_t b_bytes = tc::res_layout(a.nkb, nt, 0, sh.wpt).b_bytes;
   int stages = 0;
-  while (stages < 8 && tc::res_layout(a.nkb, nt, stages + 1).total <= kMaxDynamicSmem) ++stages;
+  while (stages < 8 && tc::res_layout(a.nkb, nt, stages + 1, sh.wpt).total <= kMaxDynamicSmem) ++stages;
   if (b_bytes > 0 && stages >= 2) {
     a.stages = stages;
-    const size_t smem = tc::res_layout(a.nkb, nt, stages).total;
+    // two accumulators of 2 nt columns (A W_hi | A W_lo); h and sum z^2 live in registers
+    a.tmem_cols = pow2_cols(4 * nt);
+    // output tiles of 16 columns x 32 rows (tangent slabs), no swizzle
+    CUtensorMap ty;
+    const int64_t y_rows = (int64_t)(sh.T > 1 ? sh.T : 2) * sh.R;
+    if (!make_store_map(&ty, Y, ldy, y_rows, ldy)) return false;
+    const size_t smem = tc::res_layout(a.nkb, nt, stages, sh.wpt).total;
     const dim3 grid = persistent_grid(h1 / nt, sh.tiles);
     if (full) {
       cudaFuncSetAttribute(tc::k_layer_res<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      tc::k_layer_res<true><<<grid, tc::kThreads, smem, st>>>(ta, tb, a);
+      tc::k_layer_res<true><<<grid, tc::kResThreads, smem, st>>>(ta, tb, ty, a);
     } else {
       cudaFuncSetAttribute(tc::k_layer_res<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      tc::k_layer_res<false><<<grid, tc::kThreads, smem, st>>>(ta, tb, a);
+      tc::k_layer_res<false><<<grid, tc::kResThreads, smem, st>>>(ta, tb, ty, a);
     }
     return true;
   }
