@@ -649,6 +649,195 @@ __global__ void __launch_bounds__(128, 3) k_det_value_small(Shape sh, DetArgs a)
   }
 }
 
+// ---- local-energy pass for small blocks --------------------------------------------------
+// Blocks of at most 4 x 4 and at most 8 electrons (hydrogen, lithium hydride and its ions,
+// atoms up to oxygen): one thread per (walker, determinant, spin) block does the
+// Gauss-Jordan inversion with partial pivoting (first maximal |pivot|), the determinant as
+// mantissa x 2^exponent, every tangent trace g_t = tr(C d_t A), the sum over t of
+// q_t = tr((C d_t A)^2) and tr(C lap A), all in registers; one thread per walker then combines
+// the K terms and assembles E_L.  128 / (2K) walkers share a CTA, so a small walker does not
+// occupy a CTA of idle threads.
+template <int NMAX, typename Det, typename Wlk, typename PhiT>
+__global__ void __launch_bounds__(128) k_det_energy_small(const Wlk* __restrict__ r, const double* __restrict__ nuc,
+                                                          Shape sh, DetArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = a.K, NM = 2 * K, NC = 3 * sh.N, T = sh.T;
+  const int per_cta = 128 / NM;
+  const int wl = threadIdx.x / NM, p = threadIdx.x % NM;
+  const int w = blockIdx.x * per_cta + wl;
+  const int ns[2] = {sh.n_up, sh.n_dn};
+  // per walker of the CTA: gt [NM][NC], lt [NM], qs [NM], mant [NM]; then expo [NM] ints
+  const int stride = NM * (NC + 3);
+  Det* sd = (Det*)smem_raw;
+  int* sexp = (int*)(sd + (int64_t)per_cta * stride);
+  if (wl < per_cta && w < sh.B) {
+    Det* gt = sd + (int64_t)wl * stride + p * NC;
+    Det* lt = sd + (int64_t)wl * stride + NM * NC + p;
+    Det* qs = lt + NM;
+    Det* mt = qs + NM;
+    const int k = p >> 1, sp = p & 1, n = ns[sp];
+    if (n == 0) {
+      for (int t = 0; t < NC; ++t) gt[t] = 0;
+      *lt = 0; *qs = 0; *mt = 1;
+      sexp[wl * NM + p] = 0;
+    } else {
+      const PhiT* blk = (const PhiT*)a.Phi + (int64_t)w * a.PW + (sp ? (int64_t)K * T * ns[0] * ns[0] : 0) +
+                        (int64_t)k * T * n * n;
+      // [A | I] -> [I | A^-1]
+      Det M[NMAX][2 * NMAX];
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i)
+#pragma unroll
+        for (int j = 0; j < 2 * NMAX; ++j) M[i][j] = 0;
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i)
+#pragma unroll
+        for (int j = 0; j < NMAX; ++j)
+          if (i < n && j < n) M[i][j] = widen<Det, PhiT>(blk[i * n + j]);
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i) M[i][NMAX + i] = (i < n) ? (Det)1 : (Det)0;
+      Det sgn = 1, mant = 1;
+      int expo = 0;
+      bool singular = false;
+#pragma unroll
+      for (int c = 0; c < NMAX; ++c) {
+        if (c < n) {
+          int piv = c;
+          auto best = abs_key(M[c][c]);
+#pragma unroll
+          for (int i = c + 1; i < NMAX; ++i)
+            if (i < n && abs_key(M[i][c]) > best) { best = abs_key(M[i][c]); piv = i; }
+          if (best == 0) singular = true;
+#pragma unroll
+          for (int i = c + 1; i < NMAX; ++i)
+            if (i == piv) {
+#pragma unroll
+              for (int j = 0; j < 2 * NMAX; ++j) { const Det tmp = M[c][j]; M[c][j] = M[i][j]; M[i][j] = tmp; }
+            }
+          if (piv != c) sgn = -sgn;
+          const Det pv = M[c][c];
+          int e;
+          mant *= frexp(pv, &e);
+          expo += e;
+          int e2;
+          mant = frexp(mant, &e2);
+          expo += e2;
+          const Det rp = (Det)1 / pv;
+#pragma unroll
+          for (int j = 0; j < 2 * NMAX; ++j) M[c][j] *= rp;
+#pragma unroll
+          for (int i = 0; i < NMAX; ++i)
+            if (i != c && i < n) {
+              const Det f = M[i][c];
+#pragma unroll
+              for (int j = 0; j < 2 * NMAX; ++j) M[i][j] -= f * M[c][j];
+            }
+        }
+      }
+      *mt = singular ? (Det)0 : sgn * mant;
+      sexp[wl * NM + p] = singular ? 0 : expo;
+      // C = A^-1 in M[.][NMAX ..]; tangent items
+      Det qsum = 0;
+      for (int t = 0; t < NC; ++t) {
+        const PhiT* D = blk + (int64_t)(1 + t) * n * n;
+        Det Bm[NMAX][NMAX];
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+#pragma unroll
+          for (int j = 0; j < NMAX; ++j) {
+            Det s = 0;
+#pragma unroll
+            for (int m = 0; m < NMAX; ++m)
+              if (m < n && j < n) s += M[i][NMAX + m] * widen<Det, PhiT>(D[m * n + j]);
+            Bm[i][j] = s;
+          }
+        Det g = 0, q = 0;
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i) {
+          if (i < n) {
+            g += Bm[i][i];
+            q += Bm[i][i] * Bm[i][i];
+#pragma unroll
+            for (int j = i + 1; j < NMAX; ++j)
+              if (j < n) q += (Det)2 * Bm[i][j] * Bm[j][i];
+          }
+        }
+        gt[t] = singular ? (Det)0 : g;
+        qsum += q;
+      }
+      const PhiT* DL = blk + (int64_t)(T - 1) * n * n;
+      Det l = 0;
+#pragma unroll
+      for (int i = 0; i < NMAX; ++i)
+#pragma unroll
+        for (int j = 0; j < NMAX; ++j)
+          if (i < n && j < n) l += M[j][NMAX + i] * widen<Det, PhiT>(DL[i * n + j]);
+      *lt = singular ? (Det)0 : l;
+      *qs = singular ? (Det)0 : qsum;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < per_cta) {
+    const int wc = threadIdx.x;
+    const int w2 = blockIdx.x * per_cta + wc;
+    if (w2 < sh.B) {
+      const Det* gtw = sd + (int64_t)wc * stride;
+      const Det* ltw = gtw + NM * NC;
+      const Det* qsw = ltw + NM;
+      const Det* mtw = qsw + NM;
+      const int* ew = sexp + wc * NM;
+      int emax = INT_MIN;
+      for (int kk = 0; kk < K; ++kk)
+        if (mtw[2 * kk] * mtw[2 * kk + 1] != 0 && ew[2 * kk] + ew[2 * kk + 1] > emax) emax = ew[2 * kk] + ew[2 * kk + 1];
+      Det S = 0;
+      for (int kk = 0; kk < K; ++kk) {
+        const Det mk = mtw[2 * kk] * mtw[2 * kk + 1];
+        if (mk != 0) S += ldexp(mk, ew[2 * kk] + ew[2 * kk + 1] - emax);
+      }
+      // E_kin = -1/2 sum_k rho_k (lap_k + |g_k|^2), rho_k = D_k / psi
+      Det kin = 0;
+      for (int kk = 0; kk < K; ++kk) {
+        const Det mk = mtw[2 * kk] * mtw[2 * kk + 1];
+        if (mk == 0 || S == 0) continue;
+        const Det rho = ldexp(mk, ew[2 * kk] + ew[2 * kk + 1] - emax) / S;
+        Det g2 = 0;
+        for (int t = 0; t < NC; ++t) {
+          const Det g = gtw[(2 * kk) * NC + t] + gtw[(2 * kk + 1) * NC + t];
+          g2 += g * g;
+        }
+        kin += rho * (ltw[2 * kk] + ltw[2 * kk + 1] - qsw[2 * kk] - qsw[2 * kk + 1] + g2);
+      }
+      double pot = 0.0;
+      const Wlk* rw = r + (int64_t)w2 * sh.N * 3;
+      for (int i = 0; i < sh.N; ++i)
+        for (int j = i + 1; j < sh.N; ++j) {
+          const double dx = (double)rw[3 * i] - (double)rw[3 * j], dy = (double)rw[3 * i + 1] - (double)rw[3 * j + 1],
+                       dz = (double)rw[3 * i + 2] - (double)rw[3 * j + 2];
+          pot += 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+        }
+      for (int i = 0; i < sh.N; ++i)
+        for (int m = 0; m < sh.M; ++m) {
+          const double dx = (double)rw[3 * i] - nuc[3 * m], dy = (double)rw[3 * i + 1] - nuc[3 * m + 1],
+                       dz = (double)rw[3 * i + 2] - nuc[3 * m + 2];
+          pot -= a.charges[m] / sqrt(dx * dx + dy * dy + dz * dz);
+        }
+      const int sgn = S > 0 ? 1 : (S < 0 ? -1 : 0);
+      const double lpsi = sgn == 0 ? (double)f_log(f_abs(S)) : (double)(f_log(f_abs(S)) + (Det)emax * (Det)0.6931471805599453);
+      const double e = (double)((Det)(-0.5) * kin) + pot + a.v_nn;
+      a.e_local[w2] = e;
+      if (a.log_psi) a.log_psi[w2] = lpsi;
+      if (a.sign) a.sign[w2] = (int8_t)sgn;
+      if (sgn == 0) atomicOr(a.status, kStatusSingular);
+      else if (!isfinite(e) || !isfinite(lpsi)) atomicOr(a.status, kStatusNonFinite);
+    }
+  }
+}
+
+inline size_t smem_det_energy_small(int det_bytes, int N, int K) {
+  const int NM = 2 * K, per_cta = 128 / NM;
+  return (size_t)per_cta * ((size_t)det_bytes * NM * (3 * N + 3) + sizeof(int) * NM);
+}
+
 template <class Mode>
 void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh, double* e_local, double* log_psi,
                        int8_t* sign, bool keep_inverse, cudaStream_t st) {
@@ -667,7 +856,13 @@ void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh,
   const bool full = sh.T > 1 && e_local != nullptr;
   const int nmax = std::max(s->n_up, s->n_dn), K = s->cfg.n_dets;
   ProfScope ps(s->prof, full ? kProfDetFull : kProfDetValue, st);
-  if (full) {
+  if (full && nmax <= 4 && s->N <= 8) {
+    const int per_cta = 128 / (2 * K);
+    const size_t smem = smem_det_energy_small(sizeof(Det), s->N, K);
+    cudaFuncSetAttribute(k_det_energy_small<4, Det, Wlk, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_det_energy_small<4, Det, Wlk, PhiT><<<(unsigned)((sh.B + per_cta - 1) / per_cta), 128, smem, st>>>(
+        (const Wlk*)walkers, s->d_nuclei, sh, a);
+  } else if (full) {
     const size_t smem = smem_det_energy(sizeof(Det), nmax, s->N, K,
                                         std::is_same<Det, double>::value && std::is_same<PhiT, float>::value);
     cudaFuncSetAttribute(k_det_energy<Det, Wlk, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(128) k_pair_value_mma(const Wlk* __restrict__ 
   __nv_bfloat16* wl = wh + L1 * 32 * kPairWLd;                    // bf16(W - bf16(W))
   float* sc = (float*)(wl + L1 * 32 * kPairWLd);                  // [L-1][32] biases
   float* gs = sc + L1 * 32;                                       // [16-padded N^2][33] activations
-  const int w = blockIdx.x, N = sh.N, NP = N * N, NPp = (NP + 15) & ~15;
+  const int N = sh.N, NP = N * N, NPp = (NP + 15) & ~15;
   for (int l = 0; l < L1; ++l) {
     const float* W = (const float*)a.W[l];                        // [h2][d_g]
     const int dg = a.d_g[l];
@@ -567,6 +567,9 @@ __global__ void __launch_bounds__(128) k_pair_value_mma(const Wlk* __restrict__ 
     }
     for (int c = threadIdx.x; c < 32; c += blockDim.x) sc[l * 32 + c] = c < a.h2 ? ((const float*)a.c[l])[c] : 0.f;
   }
+  // CTAs loop over walkers, so the weights are staged once per CTA
+  for (int w = blockIdx.x; w < sh.B; w += gridDim.x) {
+  __syncthreads();
   for (int e = threadIdx.x; e < NPp * 33; e += blockDim.x) gs[e] = 0.f;
   __syncthreads();
   const Wlk* rw = r + (int64_t)w * N * 3;
@@ -643,6 +646,7 @@ __global__ void __launch_bounds__(128) k_pair_value_mma(const Wlk* __restrict__ 
       for (int e = threadIdx.x; e < NP * a.h2; e += blockDim.x) gsto[e] = gs[(e / a.h2) * 33 + e % a.h2];
     }
   }
+  }
 }
 
 // Full (E_L) pass of the two-electron stream in BF16 mode.  The 5-row pair jets of one CTA
@@ -662,9 +666,6 @@ __global__ void __launch_bounds__(256) k_pair_full_mma(const Wlk* __restrict__ r
   float* gs = sc + L1 * 32;                                       // [rows_p][33]: pair p, row srow at p * 5 + srow
   float* zs = gs + rows_p * 33;                                   // [rows_p][33]: products of the current layer
   const int blocks_per_walker = (sh.N + ib - 1) / ib;
-  const int w = blockIdx.x / blocks_per_walker, i0 = (blockIdx.x % blocks_per_walker) * ib;
-  const int n_i = min(ib, sh.N - i0);
-  const int npair = n_i * sh.N;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
   const int grp = lane >> 2, tig = lane & 3;
   for (int l = 0; l < L1; ++l) {
@@ -679,6 +680,12 @@ __global__ void __launch_bounds__(256) k_pair_full_mma(const Wlk* __restrict__ r
     }
     for (int c = threadIdx.x; c < 32; c += blockDim.x) sc[l * 32 + c] = c < a.h2 ? ((const float*)a.c[l])[c] : 0.f;
   }
+  // CTAs loop over (walker, run of electrons) items, so the weights are staged once per CTA
+  for (int item = blockIdx.x; item < sh.B * blocks_per_walker; item += gridDim.x) {
+  const int w = item / blocks_per_walker, i0 = (item % blocks_per_walker) * ib;
+  const int n_i = min(ib, sh.N - i0);
+  const int npair = n_i * sh.N;
+  __syncthreads();
   for (int e = threadIdx.x; e < rows_p * 33; e += blockDim.x) gs[e] = 0.f;
   __syncthreads();
   // layer-0 jets of the pair features [r_i - r_j, |r_i - r_j|]: value, Laplacian over both
@@ -793,6 +800,7 @@ __global__ void __launch_bounds__(256) k_pair_full_mma(const Wlk* __restrict__ r
       gr[99] = (res ? gr[99] : 0.f) + oy;
       gr[132] = (res ? gr[132] : 0.f) + oz;
     }
+  }
   }
 }
 
@@ -1126,7 +1134,8 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
       if (Mode::kMode == FN_BF16_MIXED) {
         const int ibm = pair_full_mma_ib(sh.N);
         const size_t smem_m = smem_pair_full_mma(sh.N, L, ibm);
-        const int64_t blocks_m = (int64_t)sh.B * ((sh.N + ibm - 1) / ibm);
+        const int64_t blocks_m =
+            std::min<int64_t>((int64_t)sh.B * ((sh.N + ibm - 1) / ibm), (int64_t)s->sm_count * 8);
         cudaFuncSetAttribute(k_pair_full_mma<Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_m);
         k_pair_full_mma<Wlk><<<(unsigned)blocks_m, 256, smem_m, st>>>(r, sh, pa, ibm);
       } else {
@@ -1139,7 +1148,8 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
       if (Mode::kMode == FN_BF16_MIXED) {
         const size_t smem = smem_pair_value_mma(sh.N, L);
         cudaFuncSetAttribute(k_pair_value_mma<Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_pair_value_mma<Wlk><<<(unsigned)sh.B, 128, smem, st>>>(r, sh, pa);
+        const int64_t blocks_v = std::min<int64_t>(sh.B, (int64_t)s->sm_count * 16);
+        k_pair_value_mma<Wlk><<<(unsigned)blocks_v, 128, smem, st>>>(r, sh, pa);
       } else {
         const size_t smem = smem_pair_value(sizeof(Cmp), sh.N, L);
         const int threads = (int)std::min<int64_t>(512, round_up((int64_t)sh.N * sh.N, 32));
