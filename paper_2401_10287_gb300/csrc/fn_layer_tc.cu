@@ -31,7 +31,6 @@ namespace fn {
 namespace tc {
 
 constexpr int kStages = 4;                      // TMA ring depth (the layer kernel uses 3, see stages_for)
-constexpr int kMaxNucleiTc = 16;
 constexpr int kBlockK = 64;                     // bf16 elements per 128-byte swizzled row
 constexpr int kEpiWarps = 8;                   // two warps per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
@@ -1004,7 +1003,6 @@ __global__ void __launch_bounds__(kResThreads, 1)
     const int n0 = ctile * nt;
     const int wl = r / sh.N;
     const int ethread = threadIdx.x - 128;
-    const int64_t yslab = sh.R * a.ldy;
     uint4* ystg = ystage + (warp - 4) * 64;
     // the 16-column pieces of this thread: chunk cc = 2 (pc / 2) + ehalf (where it exists), half pc % 2
     const int npieces = (ehalf < nchunks ? 2 : 0) + (2 + ehalf < nchunks ? 2 : 0);
@@ -1076,34 +1074,43 @@ __global__ void __launch_bounds__(kResThreads, 1)
             outf[j] = h + ((j & 1) ? r2.y : r2.x);
             al[j] = __float_as_uint(h);           // h of this piece, for act_out
           }
-          if (valid) {
-            if (a.residual && a.alo_row > 0) {
-              // the value slab's residual is a pair: add its low part (slab T of X)
-              const uint4* xl = (const uint4*)(a.X + (int64_t)T * sh.R * a.ldx + row * a.ldx + col0);
+          if (valid && a.residual && a.alo_row > 0) {
+            // the value slab's residual is a pair: add its low part (slab T of X)
+            const uint4* xl = (const uint4*)(a.X + (int64_t)T * sh.R * a.ldx + row * a.ldx + col0);
 #pragma unroll
-              for (int v = 0; v < 2; ++v) {
-                const uint4 u = xl[v];
-                const uint32_t* uu = (const uint32_t*)&u;
+            for (int v = 0; v < 2; ++v) {
+              const uint4 u = xl[v];
+              const uint32_t* uu = (const uint32_t*)&u;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  const float2 f = bf2_to_f2(uu[e]);
-                  outf[8 * v + 2 * e] += f.x;
-                  outf[8 * v + 2 * e + 1] += f.y;
-                }
+              for (int e = 0; e < 4; ++e) {
+                const float2 f = bf2_to_f2(uu[e]);
+                outf[8 * v + 2 * e] += f.x;
+                outf[8 * v + 2 * e + 1] += f.y;
               }
             }
+          }
+          // the value slab and its low part (slab T) as TMA tile stores, like the tangent slabs
+          const int yrow = (int)((int64_t)tile * 128 + q * 32);
 #pragma unroll
-            for (int p = 0; p < 8; ++p) o[p] = f2_to_bf2(outf[2 * p], outf[2 * p + 1]);
-            uint4* yo = (uint4*)(a.Y + t * yslab + row * a.ldy + col0);
-            yo[0] = make_uint4(o[0], o[1], o[2], o[3]);
-            yo[1] = make_uint4(o[4], o[5], o[6], o[7]);
-            if (a.alo_row > 0) {
+          for (int part = 0; part < 2; ++part) {
+            if (part == 1 && a.alo_row <= 0) break;
 #pragma unroll
-              for (int p = 0; p < 8; ++p) o[p] = f2_to_bf2(bf16_rem(outf[2 * p]), bf16_rem(outf[2 * p + 1]));
-              uint4* yl = (uint4*)(a.Y + (int64_t)T * yslab + row * a.ldy + col0);
-              yl[0] = make_uint4(o[0], o[1], o[2], o[3]);
-              yl[1] = make_uint4(o[4], o[5], o[6], o[7]);
+            for (int p = 0; p < 8; ++p)
+              o[p] = !valid ? 0u
+                            : (part == 0 ? f2_to_bf2(outf[2 * p], outf[2 * p + 1])
+                                         : f2_to_bf2(bf16_rem(outf[2 * p]), bf16_rem(outf[2 * p + 1])));
+            if (lane == 0) bulk_wait_read0();
+            __syncwarp();
+            ystg[2 * lane] = make_uint4(o[0], o[1], o[2], o[3]);
+            ystg[2 * lane + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+              tma_store_2d(&tmY, ystg, col0, (int)(part ? (int64_t)T * sh.R + yrow : yrow));
+              bulk_commit();
             }
+          }
+          if (valid) {
             if (a.act_out) {
               float4* ao = (float4*)(a.act_out + row * a.h1 + col0);
 #pragma unroll
@@ -1308,7 +1315,7 @@ bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, int lo
     a.tmem_cols = pow2_cols(4 * nt);
     // output tiles of 16 columns x 32 rows (tangent slabs), no swizzle
     CUtensorMap ty;
-    const int64_t y_rows = (int64_t)(sh.T > 1 ? sh.T : 2) * sh.R;
+    const int64_t y_rows = (int64_t)(sh.T + 1) * sh.R;        // slabs 0..T-1 and the value's low part
     if (!make_store_map(&ty, Y, ldy, y_rows, ldy)) return false;
     const size_t smem = tc::res_layout(a.nkb, nt, stages, sh.wpt).total;
     const dim3 grid = persistent_grid(h1 / nt, sh.tiles);
