@@ -23,6 +23,8 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "fn_device.cuh"
 #include "fn_internal.cuh"
@@ -835,6 +837,17 @@ __device__ __forceinline__ void tmem_wait_ld48(uint32_t (&a)[16], uint32_t (&b)[
                : "memory");
 }
 
+__device__ __forceinline__ void tmem_wait_ld32(uint32_t (&a)[16], uint32_t (&b)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+                 "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]),
+                 "+r"(a[15]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]),
+                 "+r"(b[7]), "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]),
+                 "+r"(b[14]), "+r"(b[15])
+               :
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
@@ -1174,6 +1187,481 @@ __global__ void __launch_bounds__(kResThreads, 1)
   }
 }
 
+
+// ---- stream layer on CTA pairs (cta_group::2) ---------------------------------------
+// The two CTAs of a cluster (the two SMs of one TPC) share every MMA: M = 256 rows, CTA
+// rank 0 supplying its row tile as rows 0..127 and rank 1 the next row tile as rows
+// 128..255.  Each CTA holds half of the weight tile, the high and low BF16 parts of 64 of
+// the pair's 128 output columns stacked as one 128-row operand (80 KB at k_self = 320),
+// and every MMA is N = 256: accumulator columns [0, 64) hold A W_hi and [64, 128) A W_lo
+// for rank 0's 64 columns, [128, 256) the same for rank 1's.  Per CTA:
+//   warp 0       TMA producer: the CTA's weight half once, then its A tiles (16 KB per
+//                k-block) into a ring; every copy of both CTAs completes on the rank-0
+//                CTA's barrier
+//   warp 1       allocates the pair's tensor memory; on rank 0 one lane issues the MMAs
+//                and commits to the barriers of both CTAs (multicast)
+//   warps 4..19  epilogue on the CTA's own 128 rows: a TMEM lane quarter and 32 output
+//                columns per warp.  Each warp first moves its accumulator columns (high +
+//                low) to registers and hands the accumulator back, then computes, with h
+//                and sum z^2 kept in tensor memory, and writes its 32 x 32 output tile by
+//                one TMA store.  Warps proceed independently: the mean-field rows M[t] of
+//                a warp's walkers are staged per warp (cp.async, one item ahead).
+// Tensor memory (512 columns): the accumulator [0, 256) and, in the tangent pass, h
+// [256, 384) and sum z^2 [384, 512); the value-only pass double-buffers the accumulator.
+struct PairLayout {
+  uint32_t b_bytes;      // resident weight half
+  int stages;            // A ring depth
+  uint32_t mt_bytes;     // M[t] staging: [16 warps][2][wpw][32] floats (rounded up to 1 KB)
+  uint32_t y_bytes;      // output staging: 2 KB per epilogue warp
+  size_t total;
+};
+
+constexpr int kPairEpiWarps = 16;
+constexpr int kPairThreads = 128 + 32 * kPairEpiWarps;     // 640
+constexpr int kPairRegsLow = 40;                           // warpgroup 0 after setmaxnreg.dec
+constexpr int kPairRegsHigh = 104;                         // epilogue warpgroups after setmaxnreg.inc
+// 640 threads launch with 96 registers each (65536 / 640 rounded down to 8); the split must
+// fit in them: 128 x 40 + 512 x 104 = 58368 <= 640 x 96 = 61440.  The host checks the launch count.
+constexpr int kPairLaunchRegs = 96;
+static_assert(128 * kPairRegsLow + 32 * kPairEpiWarps * kPairRegsHigh <= kPairThreads * kPairLaunchRegs,
+              "register split above the launch");
+
+// Walkers whose rows meet 32 consecutive rows of a tile: at most 32 / N + 2.
+__host__ __device__ inline int pair_wpw(int N) { return 32 / N + 2; }
+
+__host__ __device__ inline PairLayout pair_layout(int nkb, int stages, int N) {
+  PairLayout l;
+  l.b_bytes = (uint32_t)nkb * 2u * 64u * 128u;
+  l.stages = stages;
+  l.mt_bytes = ((uint32_t)kPairEpiWarps * 2u * (uint32_t)pair_wpw(N) * 128u + 1023u) & ~1023u;
+  l.y_bytes = (uint32_t)kPairEpiWarps * 2048u;
+  l.total = 1024 + (size_t)l.b_bytes + (size_t)stages * 128 * 128 + l.mt_bytes + l.y_bytes +
+            8 * (2 * (size_t)stages + 6) + 16;
+  return l;
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Address of the same shared variable in CTA `rank` of the cluster (shared::cluster window).
+__device__ __forceinline__ uint32_t mapa_rank(const void* p, uint32_t rank) {
+  uint32_t d;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(smem_u32(p)), "r"(rank));
+  return d;
+}
+// Arrival on a barrier of the peer CTA.  The ordering it carries is that of the tensor-memory
+// loads before it (tcgen05.wait::ld and fence::before_thread_sync), not of generic memory.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// TMA load into this CTA's shared memory whose completion is counted on a barrier of either
+// CTA of the pair (here always rank 0's).
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint32_t bar_cluster, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(bar_cluster), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// Arrive (once the pair's MMAs issued so far complete) on the barrier at this offset in both CTAs.
+__device__ __forceinline__ void mma_commit_pair_mc(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// The M[t] rows of the walkers that meet this warp's rows (walkers wa .. wa + nwm - 1 of the
+// tile), this CTA's columns n0 + cg0 .. + 31, into the warp's staging rows of 32 floats;
+// one commit group per call and lane.
+__device__ __forceinline__ void stage_mterm_warp(const TcArgs& a, int t, int tile, int wa, int nwm, int col,
+                                                 float* dst, int lane) {
+  const Shape& sh = a.sh;
+  const int w0 = tile * sh.wpt + wa;
+  for (int e = lane; e < nwm * 8; e += 32) {
+    const int j = e >> 3, c = e & 7;
+    if (w0 + j < sh.B) cp_async16(dst + j * 32 + 4 * c, a.Mterm + ((int64_t)t * sh.B + w0 + j) * a.h1 + col + 4 * c);
+  }
+  cp_async_commit();
+}
+
+template <bool FULL>
+__global__ void __launch_bounds__(kPairThreads, 1)
+    k_layer_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const __grid_constant__ CUtensorMap tmY, TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int nt = 128;
+  constexpr int NACC = FULL ? 1 : 2;                          // accumulators of 256 columns
+  constexpr uint32_t bytesA = 128 * 128, bytesB = 128 * 128;  // B: 64 W_hi rows then 64 W_lo rows
+  const int nkb = a.nkb;
+  const Shape& sh = a.sh;
+  const PairLayout lay = pair_layout(nkb, a.stages, sh.N);
+  const int NS = lay.stages;
+  const int wpw = pair_wpw(sh.N);
+  unsigned char* sB = base;                                   // [nkb][128 rows] weight tiles
+  unsigned char* sA = sB + lay.b_bytes;                       // NS A tiles
+  float* mts = (float*)(sA + (size_t)NS * bytesA);            // [16 warps][2][wpw][32] M[t] rows
+  unsigned char* ystage = (unsigned char*)mts + lay.mt_bytes; // [16 warps][32 rows][64 B]
+  uint64_t* bars = (uint64_t*)(ystage + lay.y_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + NS;
+  uint64_t* accf = bars + 2 * NS;
+  uint64_t* acce = accf + 2;
+  uint64_t* bfull = acce + 2;
+  uint64_t* mma_done = bfull + 1;
+  uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int ctile = (int)(blockIdx.x >> 1);
+  const int pairs = (a.tiles + 1) >> 1;
+  const int my_pairs = pairs > (int)blockIdx.y ? (pairs - 1 - (int)blockIdx.y) / (int)gridDim.y + 1 : 0;
+  const int T = sh.T;
+  const int n_items = my_pairs * T;                           // the same in both CTAs of the pair
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(accf + b, 1); mbar_init(acce + b, 2 * kPairEpiWarps); }
+    mbar_init(bfull, 1);
+    mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    // one warp of each CTA of the pair allocates, together, the same columns in both
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  // both CTAs' barriers are initialised before any copy or arrival of the peer reaches them
+  fence_before();
+  cluster_sync_all();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint64_t deadline = globaltimer() + kWaitNs * 8 * (uint64_t)(my_pairs > 0 ? my_pairs : 1);
+
+  if (warp < 4) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kPairRegsLow));
+    if (warp == 0 && lane == 0 && n_items > 0) {
+      // this CTA's weight half, once: k-block kb holds 64 W_hi rows then 64 W_lo rows
+      if (rank == 0) mbar_expect_tx(bfull, 2 * lay.b_bytes);
+      const uint32_t bfull0 = mapa_rank(bfull, 0);
+      for (int kb = 0; kb < nkb; ++kb)
+        for (int part = 0; part < 2; ++part)
+          tma_load_2d_pair(sB + (size_t)kb * bytesB + part * (bytesB / 2), &tmB, bfull0,
+                           part * a.bsplit + kb * kBlockK, ctile * nt + (int)rank * 64);
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int pr = (int)blockIdx.y, t = 0;
+      for (int item = 0; item < n_items && ok; ++item) {
+        const int tile = 2 * pr + (int)rank;
+        // (rank 1's tile of the last pair may lie past the rows: its copies read rows of
+        // the next slab or the zero fill, and its epilogue stores nothing)
+        const int arow = (int)(t * sh.R + (int64_t)tile * 128);
+        const int lo_row = (int)(a.alo_row + (int64_t)t * sh.R + (int64_t)tile * 128);
+        const int lf = lo_first<kEpiLayer>(a, t, 0, nkb);
+        const int n_k = nkb + (nkb - lf);
+        for (int kk = 0; kk < n_k; ++kk) {
+          const bool lo = kk >= nkb;
+          const int kb = lo ? lf + (kk - nkb) : kk;
+          if (*abort_flag || !mbar_wait(empty + stage, phase ^ 1u, deadline)) { ok = false; break; }
+          if (rank == 0) mbar_expect_tx(full + stage, 2 * bytesA);
+          tma_load_2d_pair(sA + (size_t)stage * bytesA, &tmA, mapa_rank(full + stage, 0), kb * kBlockK,
+                           lo ? lo_row : arow);
+          if (++stage == NS) { stage = 0; phase ^= 1u; }
+        }
+        if (++t == T) { t = 0; pr += (int)gridDim.y; }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(a.status, kStatusTimeout);
+        // the copies in flight complete on rank 0's barriers, which this thread cannot
+        // wait on: give them a bounded 200 us before the CTA leaves
+        const uint64_t until = globaltimer() + 200000ull;
+        while (globaltimer() < until) {}
+      }
+    } else if (warp == 1 && lane == 0 && rank == 0) {
+      // per k-block of the A tile, 4 MMAs (K = 16, N = 256) against the stacked weight rows
+      const uint32_t idesc = idesc_bf16(256, 256);
+      int stage = 0;
+      uint32_t phase = 0;
+      int t = 0;
+      bool ok = n_items == 0 || (!*abort_flag && mbar_wait(bfull, 0u, deadline));
+      fence_after();
+      const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
+      for (int item = 0; item < n_items && ok; ++item) {
+        const int buf = NACC == 1 ? 0 : (item & 1);
+        const uint32_t use = (uint32_t)(NACC == 1 ? item : item >> 1);
+        if (*abort_flag || !mbar_wait(acce + buf, (use & 1u) ^ 1u, deadline)) { ok = false; break; }
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * 256);
+        const int lf = lo_first<kEpiLayer>(a, t, 0, nkb);
+        const int n_k = nkb + (nkb - lf);
+        for (int kk = 0; kk < n_k; ++kk) {
+          const int kb = kk >= nkb ? lf + (kk - nkb) : kk;
+          if (*abort_flag || !mbar_wait(full + stage, phase, deadline)) { ok = false; break; }
+          fence_after();
+          const uint64_t da = sdesc(sA_u + (uint32_t)stage * bytesA);
+          const uint64_t db = sdesc(sB_u + (uint32_t)kb * bytesB);
+#pragma unroll
+          for (int k4 = 0; k4 < kBlockK / 16; ++k4)
+            mma_bf16_pair(d, da + (uint64_t)(2 * k4), db + (uint64_t)(2 * k4), idesc, (kk != 0 || k4 != 0) ? 1u : 0u);
+          mma_commit_pair_mc(empty + stage);
+          if (++stage == NS) { stage = 0; phase ^= 1u; }
+        }
+        if (ok) mma_commit_pair_mc(accf + buf);
+        if (++t == T) t = 0;
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(a.status, kStatusTimeout);
+      }
+      mma_commit_pair(mma_done);
+      mbar_wait(mma_done, 0u, globaltimer() + kWaitNs);
+    }
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kPairRegsHigh));
+    const int q = warp & 3;                       // TMEM lane quarter this warp may access
+    const int r = q * 32 + lane;                  // row in the CTA's tile
+    const int cg0 = ((warp - 4) >> 2) * 32;       // the warp's 32 output columns within the 128
+    // accumulator columns of those outputs' W_hi products (the W_lo ones follow 64 later)
+    const uint32_t dhi = (uint32_t)(cg0 < 64 ? cg0 : cg0 + 64);
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const int n0 = ctile * nt;
+    const int wl = r / sh.N;
+    const int wa = (q * 32) / sh.N;               // first walker meeting the warp's rows
+    const int nwm = min(sh.wpt, (q * 32 + 31) / sh.N + 1) - wa;   // walkers of the warp's rows
+    const int wrow = min(wl, sh.wpt - 1) - wa;    // this row's walker in the warp's staging
+    float* mw = mts + (size_t)(warp - 4) * 2 * wpw * 32;
+    unsigned char* ystg = ystage + (warp - 4) * 2048;
+    uint4* yrow = (uint4*)(ystg + lane * 64);     // this thread's row of the 32 x 32 output tile
+    const uint32_t hcol = 256, scol = 384;        // tensor-memory columns of h and sum z^2
+    const uint32_t acce0 = mapa_rank(acce, 0);
+    int pr = (int)blockIdx.y, t = 0;
+    if (n_items > 0 && nwm > 0) stage_mterm_warp(a, 0, 2 * pr + (int)rank, wa, nwm, n0 + cg0, mw, lane);
+    else cp_async_commit();
+    for (int item = 0; item < n_items; ++item) {
+      const int buf = NACC == 1 ? 0 : (item & 1);
+      const uint32_t use = (uint32_t)(NACC == 1 ? item : item >> 1);
+      const int tile = 2 * pr + (int)rank;
+      const bool tile_ok = tile < a.tiles;
+      const int64_t row = (int64_t)tile * 128 + r;
+      const int w = tile * sh.wpt + wl;
+      const bool valid = tile_ok && wl < sh.wpt && w < sh.B;
+      const uint32_t tl = tmem + lane_base;
+      const int yr = (int)((int64_t)tile * 128 + q * 32);
+      const uint4* xr = (const uint4*)(a.X + t * sh.R * (int64_t)a.ldx + row * a.ldx + n0 + cg0);
+      // Waits for the item's M[t] rows and accumulator (false: timed out), moves z without the
+      // mean-field term (the W_hi and W_lo products of the warp's 32 columns) to registers,
+      // hands the accumulator back to the MMA, stages the next item's M[t] rows and waits
+      // until the previous item's stores have read the staging tile.
+      auto begin_item = [&](float (&zr)[2][16]) -> bool {
+        cp_async_wait_all();
+        __syncwarp();
+        if (*abort_flag || !mbar_wait(accf + buf, use & 1u, deadline)) {
+          *abort_flag = 1;
+          if (lane == 0) atomicOr(a.status, kStatusTimeout);
+          return false;
+        }
+        fence_after();
+#pragma unroll
+        for (int pc = 0; pc < 2; ++pc) {
+          uint32_t ah[16], al[16];
+          tmem_ld16_nowait(tl + (uint32_t)(buf * 256) + dhi + (uint32_t)(pc * 16), ah);
+          tmem_ld16_nowait(tl + (uint32_t)(buf * 256) + dhi + 64u + (uint32_t)(pc * 16), al);
+          tmem_wait_ld32(ah, al);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) zr[pc][j] = __uint_as_float(ah[j]) + __uint_as_float(al[j]);
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) {
+          if (rank == 0) mbar_arrive(acce + buf);
+          else mbar_arrive_remote(acce0 + 8u * (uint32_t)buf);
+        }
+        // the next item's M[t] rows into the warp's other buffer (its last reader was this
+        // warp at the previous item)
+        int pr1 = pr, t1 = t + 1;
+        if (t1 == T) { t1 = 0; pr1 += (int)gridDim.y; }
+        if (item + 1 < n_items && nwm > 0)
+          stage_mterm_warp(a, t1, 2 * pr1 + (int)rank, wa, nwm, n0 + cg0, mw + ((item + 1) & 1) * wpw * 32, lane);
+        else cp_async_commit();
+        if (lane == 0) bulk_wait_read0();
+        __syncwarp();
+        return true;
+      };
+      const float* mrow = mw + ((item & 1) * wpw + max(wrow, 0)) * 32;
+      // The warp's 32 rows x 32 columns leave as one TMA tile store (none for a tile past the rows).
+      auto store_tile = [&](int64_t slab_row) {
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0 && tile_ok) {
+          tma_store_2d(&tmY, ystg, n0 + cg0, (int)(slab_row + yr));
+          bulk_commit();
+        }
+      };
+      if (t == 0) {
+        // value slab: h = tanh(z), out = h + residual (a hi/lo pair in and out); the residual
+        // and its low part (slab T) are loaded before the accumulator wait
+        uint4 res[2][2], rlo[2][2];
+#pragma unroll
+        for (int pc = 0; pc < 2; ++pc)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) { res[pc][v] = make_uint4(0u, 0u, 0u, 0u); rlo[pc][v] = res[pc][v]; }
+        const uint4* xl = (const uint4*)(a.X + (int64_t)T * sh.R * a.ldx + row * a.ldx + n0 + cg0);
+        const bool has_lo = valid && a.residual && a.alo_row > 0;
+        if (valid && a.residual) {
+#pragma unroll
+          for (int pc = 0; pc < 2; ++pc) { res[pc][0] = __ldg(xr + 2 * pc); res[pc][1] = __ldg(xr + 2 * pc + 1); }
+          if (!FULL && has_lo) {
+#pragma unroll
+            for (int pc = 0; pc < 2; ++pc) { rlo[pc][0] = __ldg(xl + 2 * pc); rlo[pc][1] = __ldg(xl + 2 * pc + 1); }
+          }
+        }
+        float zr[2][16];
+        if (!begin_item(zr)) break;
+        if (FULL && has_lo) {
+          // (in the tangent pass the value slab is one item in 3N + 2: its low-part loads wait
+          // here rather than hold registers through the accumulator hand-back)
+#pragma unroll
+          for (int pc = 0; pc < 2; ++pc) { rlo[pc][0] = __ldg(xl + 2 * pc); rlo[pc][1] = __ldg(xl + 2 * pc + 1); }
+        }
+        uint32_t olo[2][8];
+#pragma unroll
+        for (int pc = 0; pc < 2; ++pc) {
+          const float4* mt = (const float4*)(mrow + pc * 16);
+          const uint32_t* rr = (const uint32_t*)res[pc];
+          const uint32_t* rl = (const uint32_t*)rlo[pc];
+          uint32_t hv[16], o[8];
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            const float4 m4 = mt[p >> 1];
+            const float h0 = tanh_fast(zr[pc][2 * p] + ((p & 1) ? m4.z : m4.x));
+            const float h1 = tanh_fast(zr[pc][2 * p + 1] + ((p & 1) ? m4.w : m4.y));
+            hv[2 * p] = __float_as_uint(h0);
+            hv[2 * p + 1] = __float_as_uint(h1);
+            const float2 r2 = bf2_to_f2(rr[p]);
+            const float2 l2 = bf2_to_f2(rl[p]);
+            const float y0 = h0 + r2.x + l2.x, y1 = h1 + r2.y + l2.y;
+            o[p] = valid ? f2_to_bf2(y0, y1) : 0u;
+            olo[pc][p] = valid ? f2_to_bf2(bf16_rem(y0), bf16_rem(y1)) : 0u;
+          }
+          if (FULL) tmem_st16(tl + hcol + (uint32_t)(cg0 + pc * 16), hv);   // h, for the tangent slabs
+          if (valid && a.act_out) {
+            float4* ao = (float4*)(a.act_out + row * a.h1 + n0 + cg0 + pc * 16);
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              ao[v] = make_float4(__uint_as_float(hv[4 * v]), __uint_as_float(hv[4 * v + 1]),
+                                  __uint_as_float(hv[4 * v + 2]), __uint_as_float(hv[4 * v + 3]));
+          }
+          yrow[2 * pc] = make_uint4(o[0], o[1], o[2], o[3]);
+          yrow[2 * pc + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+        }
+        store_tile(0);
+        if (a.alo_row > 0) {
+          // the value slab's low part (slab T of Y) from the same staging tile
+          if (lane == 0) bulk_wait_read0();
+          __syncwarp();
+#pragma unroll
+          for (int pc = 0; pc < 2; ++pc) {
+            yrow[2 * pc] = make_uint4(olo[pc][0], olo[pc][1], olo[pc][2], olo[pc][3]);
+            yrow[2 * pc + 1] = make_uint4(olo[pc][4], olo[pc][5], olo[pc][6], olo[pc][7]);
+          }
+          store_tile((int64_t)T * sh.R);
+        }
+        if (FULL) tmem_wait_st();
+      } else if (FULL) {
+        // tangent slab: out = res + (1 - h^2) z, sum z^2 += z^2; Laplacian slab:
+        // out = res + (1 - h^2) (z - 2 h sum z^2); packed two-lane FP32 arithmetic
+        const bool lap = t == T - 1;
+        uint4 res[2][2];
+#pragma unroll
+        for (int pc = 0; pc < 2; ++pc) {
+          res[pc][0] = make_uint4(0u, 0u, 0u, 0u);
+          res[pc][1] = res[pc][0];
+          if (valid && a.residual) { res[pc][0] = __ldg(xr + 2 * pc); res[pc][1] = __ldg(xr + 2 * pc + 1); }
+        }
+        float zr[2][16];
+        if (!begin_item(zr)) break;
+        const uint64_t m1 = pack_f2(-1.f, -1.f), m2 = pack_f2(-2.f, -2.f);
+#pragma unroll
+        for (int pc = 0; pc < 2; ++pc) {
+          const int c = cg0 + pc * 16;
+          uint32_t hv[16], sq[16];
+          tmem_ld16_nowait(tl + hcol + (uint32_t)c, hv);
+          if (t > 1) tmem_ld16_nowait(tl + scol + (uint32_t)c, sq);   // the first tangent slab starts the sum
+          tmem_wait_ld32(hv, sq);
+          const float4* mt = (const float4*)(mrow + pc * 16);
+          const uint32_t* rr = (const uint32_t*)res[pc];
+          uint32_t o[8];
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            const float4 m4 = mt[p >> 1];
+            const uint64_t z2 = add_f2(pack_f2(zr[pc][2 * p], zr[pc][2 * p + 1]),
+                                       (p & 1) ? pack_f2(m4.z, m4.w) : pack_f2(m4.x, m4.y));
+            const uint64_t h2 = pack_f2(__uint_as_float(hv[2 * p]), __uint_as_float(hv[2 * p + 1]));
+            const uint64_t s2 = pack_f2(__uint_as_float(sq[2 * p]), __uint_as_float(sq[2 * p + 1]));
+            const uint64_t nd2 = fma_f2(h2, h2, m1);              // -(1 - h^2)
+            uint64_t w2;
+            if (!lap) {
+              w2 = z2;
+              float s0, s1;
+              unpack_f2(t == 1 ? mul_f2(z2, z2) : fma_f2(z2, z2, s2), s0, s1);
+              sq[2 * p] = __float_as_uint(s0);
+              sq[2 * p + 1] = __float_as_uint(s1);
+            } else {
+              w2 = fma_f2(mul_f2(h2, s2), m2, z2);                // z - 2 h sum z^2
+            }
+            const float2 r2 = bf2_to_f2(rr[p]);
+            float a0, a1;
+            unpack_f2(sub_f2(pack_f2(r2.x, r2.y), mul_f2(nd2, w2)), a0, a1);
+            o[p] = valid ? f2_to_bf2(a0, a1) : 0u;  // rows without an electron are written as zero
+          }
+          if (!lap) tmem_st16(tl + scol + (uint32_t)c, sq);
+          yrow[2 * pc] = make_uint4(o[0], o[1], o[2], o[3]);
+          yrow[2 * pc + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+        }
+        store_tile(t * sh.R);
+        tmem_wait_st();
+      }
+      if (++t == T) { t = 0; pr += (int)gridDim.y; }
+    }
+    cp_async_wait_all();
+    if (lane == 0) bulk_wait0();          // the output stores have completed
+  }
+  // neither CTA leaves (or frees tensor memory) while the pair's MMAs or the peer's
+  // arrivals may still reach it
+  fence_before();
+  cluster_sync_all();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------------------------------
@@ -1207,12 +1695,13 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t cols, int64_t row
 }
 
 // 2-D bf16 tensor map for tile stores: box 16 columns x 32 rows, no swizzle.
-static bool make_store_map(CUtensorMap* m, const void* base, int64_t cols, int64_t rows, int64_t ld) {
+static bool make_store_map(CUtensorMap* m, const void* base, int64_t cols, int64_t rows, int64_t ld,
+                           int box_cols = 16) {
   auto enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  cuuint32_t box[2] = {16, 32};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, 32};
   cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
@@ -1275,6 +1764,86 @@ static void launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const tc::Tc
   }
 }
 
+// The stream layer runs on the one-CTA resident-weight kernel; FN_LAYER_KERNEL=pair selects
+// the CTA-pair kernel where it applies (output columns in tiles of 128).  Both produce the
+// same bits: the same products, accumulated in the same order.  On the N2 network at 4096
+// walkers the pair kernel issues its MMAs at the full N = 256 rate but is not faster: the
+// stream of A tiles through the TMA ring bounds both (a copy of the pair kernel that only
+// streams them, with no MMA and no epilogue arithmetic, takes 0.98 ms per launch; the
+// one-CTA kernel takes 1.11 ms).
+static bool layer_pair_enabled() {
+  const char* v = getenv("FN_LAYER_KERNEL");
+  return v && strcmp(v, "pair") == 0;
+}
+
+// Largest number of 2-CTA clusters of the pair kernel resident at once (0: none).
+template <bool FULL>
+static int pair_max_clusters(size_t smem) {
+  static int cached = -1;
+  static size_t cached_smem = 0;
+  if (cached >= 0 && cached_smem == smem) return cached;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2, 1, 1);
+  cfg.blockDim = dim3(tc::kPairThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, tc::k_layer_pair<FULL>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  cached = n;
+  cached_smem = smem;
+  return n;
+}
+
+// The stream layer on CTA pairs (output columns in tiles of 128); false when this device
+// or shape cannot run it (nothing launched).
+template <bool FULL>
+static bool launch_layer_pair(const CUtensorMap& ta, const CUtensorMap& tbp, const CUtensorMap& ty,
+                              const tc::TcArgs& a, size_t smem, cudaStream_t st) {
+  static int regs_ok = -1;
+  if (regs_ok < 0) {
+    cudaFuncAttributes fa;
+    regs_ok = cudaFuncGetAttributes(&fa, tc::k_layer_pair<FULL>) == cudaSuccess &&
+              fa.numRegs >= tc::kPairLaunchRegs;
+    cudaGetLastError();
+  }
+  if (!regs_ok) return false;
+  if (cudaFuncSetAttribute(tc::k_layer_pair<FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int ctiles = a.h1 / 128;
+  const int clusters = pair_max_clusters<FULL>(smem);
+  if (clusters < ctiles) return false;
+  const int pairs = (a.tiles + 1) / 2;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * ctiles, std::min(pairs, clusters / ctiles), 1);
+  cfg.blockDim = dim3(tc::kPairThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, tc::k_layer_pair<FULL>, ta, tbp, ty, a) != cudaSuccess) {
+    cudaGetLastError();          // a refused launch is not an error of the call: the caller falls back
+    return false;
+  }
+  return true;
+}
+
 // Stream layer on the tensor cores; returns false (nothing launched) if a tensor map could not be built.
 bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, int lo_col0, const void* Vs16,
                      const float* Mterm, void* Y, int ldy, int residual, float* act_out, int h1, int* status,
@@ -1306,6 +1875,21 @@ bool launch_layer_tc(const Shape& sh, const void* X, int ldx, int k_self, int lo
   a.tmem_cols = pow2_cols(full ? 4 * nt : 2 * nt);
   a.tiles = sh.tiles;
   // weights resident in shared memory when they fit beside an A ring of two or more stages
+  if (nt == 128 && layer_pair_enabled()) {
+    // CTA pairs: each CTA holds half of the weight tile; A ring as deep as shared memory allows
+    int pstages = 0;
+    while (pstages < 8 && tc::pair_layout(a.nkb, pstages + 1, sh.N).total <= kMaxDynamicSmem) ++pstages;
+    CUtensorMap tbp, ty;
+    if (pstages >= 3 && make_map(&tbp, Vs16, ldx + k_self, h1, 2 * ldx, 64) &&
+        make_store_map(&ty, Y, ldy, (int64_t)(sh.T + 1) * sh.R, ldy, 32)) {
+      tc::TcArgs ap = a;
+      ap.stages = pstages;
+      ap.tmem_cols = 512;
+      const size_t smem = tc::pair_layout(a.nkb, pstages, sh.N).total;
+      if (full ? launch_layer_pair<true>(ta, tbp, ty, ap, smem, st) : launch_layer_pair<false>(ta, tbp, ty, ap, smem, st))
+        return true;
+    }
+  }
   const uint32_t b_bytes = tc::res_layout(a.nkb, nt, 0, sh.wpt).b_bytes;
   int stages = 0;
   while (stages < 8 && tc::res_layout(a.nkb, nt, stages + 1, sh.wpt).total <= kMaxDynamicSmem) ++stages;

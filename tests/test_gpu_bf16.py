@@ -149,3 +149,28 @@ def test_bf16_atoms_unequal_spins_against_oracle(name, make):
     assert np.all(np.isfinite(e))
     assert np.median(rel) < 1e-2
     assert np.median(np.abs(lp - lp_ref)) < 1e-2
+
+
+def test_bf16_layer_pair_kernel_matches_single(monkeypatch):
+    """The CTA-pair stream-layer kernel (FN_LAYER_KERNEL=pair: cta_group::2 MMAs of M = 256,
+    each CTA holding half of the weight tile) forms the same products, accumulated in the
+    same order, as the default one-CTA kernel, so every output is bit-identical.  N2 network
+    (4 layers 256/32, 16 determinants), 256 walkers: 29 row tiles, so the last CTA pair has
+    a rank-1 tile past the rows."""
+    sysm = W.n2()
+    cfg = W.N2_LARGE
+    _, gpu = make_pair(sysm, cfg["ansatz"], 2)
+    params = gpu.init_params(cfg["seed"])
+    walkers, _ = gpu.init_walkers(256, cfg["seed"], cfg["init_std"])
+    lp0, _ = gpu.log_psi(params, walkers)
+    gpu.mcmc_steps(params, walkers, lp0, 3, 0.05, 7)
+    out = {}
+    for mode in ["single", "pair"]:
+        monkeypatch.setenv("FN_LAYER_KERNEL", mode)
+        lp, sg = gpu.log_psi(params, walkers)
+        e, lp2, _ = gpu.local_energy(params, walkers)
+        g, _ = gpu.energy_grad(params, walkers, e)
+        gpu.sync()
+        out[mode] = [x.clone() for x in (lp, sg, e, lp2, g)]
+    for a, b in zip(out["single"], out["pair"]):
+        assert torch.equal(a, b)
