@@ -493,8 +493,8 @@ __global__ void __launch_bounds__(512) k_pair_value(const Wlk* __restrict__ r, S
 // Spin means of a BF16 stream-layer output, the next layer's mean-field input:
 // Hbar[t][w][s h1 + c] = mean over the electrons i of spin s of Y[t][row(w, i)][c].
 // The value slab adds its low part (slab T of Y); every mean is stored as a hi/lo pair
-// (the low part of slab t in slab T + t of Hbar).  One thread per (slab, walker, spin, 8 columns); a warp reads 512
-// contiguous bytes of a row.
+// (the low part of slab t in slab T + t of Hbar).  One thread per (slab, walker, spin, 8
+// columns); a warp reads 512 contiguous bytes of a row.
 __global__ void k_spin_means_bf16(Shape sh, const __nv_bfloat16* __restrict__ Y, int ldy, int h1,
                                   __nv_bfloat16* __restrict__ Hbar) {
   const int g8 = h1 >> 3;
@@ -510,16 +510,26 @@ __global__ void k_spin_means_bf16(Shape sh, const __nv_bfloat16* __restrict__ Y,
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = 0.f;
     const int parts = t == 0 ? 2 : 1;
+    const int64_t row0 = tile_row(w, 0, sh.N, sh.wpt);            // a walker's rows are consecutive
     for (int part = 0; part < parts; ++part) {
-      const __nv_bfloat16* base = Y + (int64_t)(part ? sh.T : t) * sh.R * ldy + 8 * c8;
-      for (int i = lo; i < hi; ++i) {
-        const uint4 u = *(const uint4*)(base + tile_row(w, i, sh.N, sh.wpt) * ldy);
-        const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u;
+      const __nv_bfloat16* base = Y + ((int64_t)(part ? sh.T : t) * sh.R + row0) * ldy + 8 * c8;
+      // the rows of up to 8 electrons are loaded together (one memory round trip), then
+      // summed in electron order
+      for (int i0 = lo; i0 < hi; i0 += 8) {
+        uint4 u[8];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float2 f = __bfloat1622float2(p2[k]);
-          acc[2 * k] += f.x;
-          acc[2 * k + 1] += f.y;
+        for (int k = 0; k < 8; ++k)
+          u[k] = i0 + k < hi ? __ldg((const uint4*)(base + (int64_t)(i0 + k) * ldy)) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if (i0 + k >= hi) break;
+          const __nv_bfloat162* p2 = (const __nv_bfloat162*)&u[k];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const float2 f = __bfloat1622float2(p2[m]);
+            acc[2 * m] += f.x;
+            acc[2 * m + 1] += f.y;
+          }
         }
       }
     }

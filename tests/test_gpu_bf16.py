@@ -154,7 +154,7 @@ def test_bf16_atoms_unequal_spins_against_oracle(name, make):
 def test_bf16_layer_pair_kernel_matches_single(monkeypatch):
     """The CTA-pair stream-layer kernel (FN_LAYER_KERNEL=pair: cta_group::2 MMAs of M = 256,
     each CTA holding half of the weight tile) forms the same products, accumulated in the
-    same order, as the default one-CTA kernel, so every output is bit-identical.  N2 network
+    same order, as the default one-CTA kernel, so log psi and E_L are bit-identical.  N2 network
     (4 layers 256/32, 16 determinants), 256 walkers: 29 row tiles, so the last CTA pair has
     a rank-1 tile past the rows."""
     sysm = W.n2()
@@ -172,5 +172,9 @@ def test_bf16_layer_pair_kernel_matches_single(monkeypatch):
         g, _ = gpu.energy_grad(params, walkers, e)
         gpu.sync()
         out[mode] = [x.clone() for x in (lp, sg, e, lp2, g)]
-    for a, b in zip(out["single"], out["pair"]):
+    for a, b in zip(out["single"][:4], out["pair"][:4]):
         assert torch.equal(a, b)
+    # the gradient's sums over walkers end in FP32 atomic additions, whose order varies from
+    # run to run: equal to that rounding
+    g1, g2 = out["single"][4], out["pair"][4]
+    assert torch.all((g1 - g2).abs() <= 1e-5 * g1.abs().max())
