@@ -443,6 +443,327 @@ __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, c
   }
 }
 
+// ---- local-energy pass on 8-lane groups (BF16-mixed mode, blocks of up to 8 electrons) ----
+// One CTA of 128 threads per walker, in 16 groups of 8 lanes; lane r of a group holds row r
+// of one (determinant, spin) block.  Every lane works in every phase, so no thread waits on
+// a barrier while a few others factorise, and no thread holds a whole matrix in registers:
+//   1. Gauss-Jordan elimination with partial pivoting on [A | I] in FP64 registers, the pivot
+//      row found by a group reduction and broadcast by shuffles.  The rows are not swapped:
+//      the lane that supplies column c's pivot ends with row c of C = A^-1.  The unused rows
+//      receive exactly the updates of an LU factorisation (same pivots, same products), so
+//      log|det| and its sign are those of the one-thread LU.  The same lanes form the
+//      Laplacian trace tr(C lap A) in FP64 and store C as double-FP32 rows.
+//   2. Tangent items (block, coordinate): lane r forms row r of B = C d_t A in double-FP32
+//      arithmetic (the same operations as the one-thread items, so every B entry is the
+//      same), then g = tr B and q = tr(B^2) from the rows staged in shared memory and a
+//      double-FP32 reduction over the group.
+//   3. The determinant terms are combined and E_L assembled as in k_det_energy.
+constexpr int kGrpN = 8;                 // rows per group (largest block of this kernel)
+constexpr int kGrpCP = kGrpN + 1;        // padded row of a staged C copy (floats)
+constexpr int kGrpBS = 2 * kGrpN + 1;    // padded row of a staged B row (high, low words)
+
+__host__ __device__ inline size_t smem_det_energy_grp(int N, int K) {
+  const int NM = 2 * K, NC = 3 * N;
+  return sizeof(double) * ((size_t)2 * NM * NC + 3 * NM + (size_t)K * NC + 2 * K + 128) +
+         sizeof(float) * ((size_t)NM * 2 * kGrpN * kGrpCP + 16 * 8 * kGrpBS);
+}
+
+// (h, l) += the (h, l) of the lane `off` away (double-FP32 sum, error-free on the high words)
+__device__ __forceinline__ void ff_add_xor(float& h, float& l, int off) {
+  const float oh = __shfl_xor_sync(0xffffffffu, h, off), ol = __shfl_xor_sync(0xffffffffu, l, off);
+  float s, e;
+  ff_two_sum(h, oh, s, e);
+  h = s;
+  l = __fadd_rn(__fadd_rn(l, ol), e);
+}
+
+// Row r of B = C D for an M x M block: M double-FP32 accumulators (the operations of
+// tangent_item_ff's inner loop, so every entry is the same).
+template <int M>
+__device__ __forceinline__ void ff_row(const float* __restrict__ chr, const float* __restrict__ clr,
+                                       const float* __restrict__ D, float (&bh)[kGrpN], float (&bl)[kGrpN]) {
+#pragma unroll
+  for (int j = 0; j < M; ++j) { bh[j] = 0.f; bl[j] = 0.f; }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const float ch = chr[m], cl = clr[m];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      const float d = __ldg(D + m * M + j);
+      const float p = __fmul_rn(ch, d);
+      const float pe = __fmaf_rn(ch, d, -p);
+      float s, e;
+      ff_two_sum(bh[j], p, s, e);
+      bh[j] = s;
+      bl[j] = __fmaf_rn(cl, d, __fadd_rn(bl[j], __fadd_rn(e, pe)));
+    }
+  }
+}
+
+template <typename Wlk>
+__global__ void __launch_bounds__(128, 4) k_det_energy_grp(const Wlk* __restrict__ r, const double* __restrict__ nuc,
+                                                           Shape sh, DetArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int w = blockIdx.x, tid = threadIdx.x;
+  const int N = sh.N, T = sh.T, K = a.K, NC = 3 * N, NM = 2 * K;
+  const int ns[2] = {sh.n_up, sh.n_dn};
+  double* gt = (double*)smem_raw;                         // [NM][NC]
+  double* qt = gt + NM * NC;                              // [NM][NC]
+  double* lt = qt + NM * NC;                              // [NM]
+  double* ld2 = lt + NM;                                  // [NM]
+  double* sg2 = ld2 + NM;                                 // [NM]
+  double* gradk = sg2 + NM;                               // [K][NC]
+  double* lapk = gradk + K * NC;                          // [K]
+  double* rho = lapk + K;                                 // [K]
+  double* red = rho + K;                                  // [128]
+  float* Cs = (float*)(red + 128);                        // [NM][2][8][9]: rows of C, high then low words
+  float* Bs = Cs + NM * 2 * kGrpN * kGrpCP;               // [16 groups][8 rows][17]: B rows of an item
+  const float* Phi = (const float*)a.Phi + (int64_t)w * a.PW;
+  const int64_t blk_off[2] = {0, (int64_t)K * T * ns[0] * ns[0]};
+  const int lane = tid & 31, gid = tid >> 3, rr = tid & 7;
+  const int gbase = lane & ~7;                            // the group's first lane in the warp
+
+  // 1. factorisation, 16 blocks at a time (every lane runs every shuffle)
+  for (int p0 = 0; p0 < NM; p0 += 16) {
+    const int p = p0 + gid;
+    const bool live = p < NM;
+    const int n = live ? ns[p & 1] : 0;
+    const float* Ab = Phi + blk_off[p & 1] + (int64_t)(p >> 1) * T * n * n;     // value slab of the block
+    double av[kGrpN], vv[kGrpN];
+#pragma unroll
+    for (int j = 0; j < kGrpN; ++j) {
+      av[j] = (rr < n && j < n) ? widen<double, float>(Ab[rr * n + j]) : 0.0;
+      vv[j] = j == rr ? 1.0 : 0.0;
+    }
+    bool used = rr >= n, singular = false;
+    int mycol = -1, pc[kGrpN];
+    double mant = 1.0;
+    int expo = 0;
+#pragma unroll
+    for (int c = 0; c < kGrpN; ++c) {
+      const bool col = c < n;
+      // pivot: the unused row of largest |a_c| (the first such row on ties)
+      unsigned long long key = (!used && col) ? abs_key(av[c]) : 0ull;
+      int li = rr;
+#pragma unroll
+      for (int off = 4; off > 0; off >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, off);
+        const int ol = __shfl_xor_sync(0xffffffffu, li, off);
+        if (ok > key || (ok == key && ol < li)) { key = ok; li = ol; }
+      }
+      pc[c] = li;
+      if (col && key == 0ull) singular = true;
+      double pa[kGrpN], pv[kGrpN];
+#pragma unroll
+      for (int j = 0; j < kGrpN; ++j) {
+        pa[j] = j >= c ? __shfl_sync(0xffffffffu, av[j], gbase + li) : 0.0;
+        pv[j] = __shfl_sync(0xffffffffu, vv[j], gbase + li);
+      }
+      if (col && !singular) {
+        const double piv = pa[c];
+        const double rp = 1.0 / piv;
+        int e;
+        mant *= frexp(piv, &e);
+        expo += e;
+        int e2;
+        mant = frexp(mant, &e2);
+        expo += e2;
+        // (only the columns right of c of the A part are read again)
+        if (rr == li) {
+#pragma unroll
+          for (int j = c + 1; j < kGrpN; ++j) av[j] = pa[j] * rp;
+#pragma unroll
+          for (int j = 0; j < kGrpN; ++j) vv[j] = pv[j] * rp;
+          used = true;
+          mycol = c;
+        } else {
+          const double f = av[c] * rp;
+#pragma unroll
+          for (int j = c + 1; j < kGrpN; ++j) av[j] -= f * pa[j];
+#pragma unroll
+          for (int j = 0; j < kGrpN; ++j) vv[j] -= f * pv[j];
+        }
+      }
+    }
+    // log|det| and its sign: the pivots' product (mantissa x 2^exponent) and the parity of
+    // the permutation column c -> pivot row pc[c]
+    int par = 0;
+#pragma unroll
+    for (int i = 0; i < kGrpN; ++i)
+#pragma unroll
+      for (int j = i + 1; j < kGrpN; ++j)
+        if (j < n && pc[i] > pc[j]) par ^= 1;
+    if (live && rr == 0) {
+      if (n == 0) {
+        ld2[p] = 0;
+        sg2[p] = 1;
+      } else if (singular) {
+        ld2[p] = 0;
+        sg2[p] = 0;
+      } else {
+        const double sgn = par ? -1.0 : 1.0;
+        sg2[p] = mant < 0 ? -sgn : sgn;
+        ld2[p] = log(fabs(mant)) + (double)expo * 0.6931471805599453;
+      }
+    }
+    // row `row` of C (zero for a singular block) as double-FP32 words, and this row's part of
+    // tr(C lap A) = sum_i C[row][i] lap A[i][row]
+    const int row = singular ? rr : mycol;
+    double lpart = 0.0;
+    if (live && rr < n && row >= 0 && row < n) {
+      float* ch = Cs + ((int64_t)(p * 2) * kGrpN + row) * kGrpCP;
+      float* cl = ch + kGrpN * kGrpCP;
+      const float* Dl = Phi + blk_off[p & 1] + (int64_t)(p >> 1) * T * n * n + (int64_t)(T - 1) * n * n;
+#pragma unroll
+      for (int m = 0; m < kGrpN; ++m) {
+        if (m < n) {
+          const double c = singular ? 0.0 : vv[m];
+          const float h = __double2float_rn(c);
+          ch[m] = h;
+          cl[m] = __double2float_rn(c - (double)h);
+          lpart += c * widen<double, float>(Dl[m * n + row]);
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) lpart += __shfl_xor_sync(0xffffffffu, lpart, off);
+    if (live && rr == 0) lt[p] = lpart;
+  }
+  __syncthreads();
+
+  // 2. tangent items (block p, coordinate tr), four per warp at a time
+  for (int base = (tid >> 5) * 4; base < NM * NC; base += 16) {
+    const int it = base + ((tid >> 3) & 3);
+    const bool live = it < NM * NC;
+    const int p = live ? it / NC : 0, tr = live ? it - (it / NC) * NC : 0;
+    const int n = live ? ns[p & 1] : 0;
+    float bh[kGrpN], bl[kGrpN];
+#pragma unroll
+    for (int j = 0; j < kGrpN; ++j) { bh[j] = 0.f; bl[j] = 0.f; }
+    float* brow = Bs + (gid * 8 + rr) * kGrpBS;
+    {
+      // the orbital tangents are read once, from DRAM: start the block this group takes two
+      // items later on its way into L2 (up to three 128-byte lines)
+      const int it2 = it + 32;
+      if (rr < 3 && it2 < NM * NC) {
+        const int p2 = it2 / NC, n2 = ns[p2 & 1];
+        const float* D2 = Phi + blk_off[p2 & 1] + (int64_t)(p2 >> 1) * T * n2 * n2 + (int64_t)(1 + it2 - p2 * NC) * n2 * n2;
+        if (rr * 32 < n2 * n2) asm volatile("prefetch.L2 [%0];" ::"l"(D2 + rr * 32));
+      }
+    }
+    if (rr < n) {
+      const float* D = Phi + blk_off[p & 1] + (int64_t)(p >> 1) * T * n * n + (int64_t)(1 + tr) * n * n;
+      const float* chr = Cs + ((int64_t)(p * 2) * kGrpN + rr) * kGrpCP;
+      const float* clr = chr + kGrpN * kGrpCP;
+      switch (n) {
+        case 1: ff_row<1>(chr, clr, D, bh, bl); break;
+        case 2: ff_row<2>(chr, clr, D, bh, bl); break;
+        case 3: ff_row<3>(chr, clr, D, bh, bl); break;
+        case 4: ff_row<4>(chr, clr, D, bh, bl); break;
+        case 5: ff_row<5>(chr, clr, D, bh, bl); break;
+        case 6: ff_row<6>(chr, clr, D, bh, bl); break;
+        case 7: ff_row<7>(chr, clr, D, bh, bl); break;
+        default: ff_row<8>(chr, clr, D, bh, bl); break;
+      }
+#pragma unroll
+      for (int j = 0; j < kGrpN; ++j) {
+        brow[2 * j] = bh[j];
+        brow[2 * j + 1] = bl[j];
+      }
+    }
+    __syncwarp();
+    // g: this row's diagonal entry; q: sum_j B[rr][j] B[j][rr]
+    float gh = 0.f, gl = 0.f, qh = 0.f, ql = 0.f;
+    if (rr < n) {
+      const float* bcol = Bs + (gid * 8) * kGrpBS + 2 * rr;
+      gh = bcol[rr * kGrpBS];
+      gl = bcol[rr * kGrpBS + 1];
+#pragma unroll
+      for (int j = 0; j < kGrpN; ++j)
+        if (j < n) ff_fma_acc(bh[j], bl[j], bcol[j * kGrpBS], bcol[j * kGrpBS + 1], 1.f, qh, ql);
+    }
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) {
+      ff_add_xor(gh, gl, off);
+      ff_add_xor(qh, ql, off);
+    }
+    if (live && rr == 0) {
+      gt[p * NC + tr] = (double)gh + (double)gl;
+      qt[p * NC + tr] = (double)qh + (double)ql;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // 3. the determinant terms and E_L (as in k_det_energy)
+  for (int e = tid; e < K * NC; e += blockDim.x) {
+    const int k = e / NC, t = e % NC;
+    gradk[e] = gt[(2 * k) * NC + t] + gt[(2 * k + 1) * NC + t];
+  }
+  for (int k = tid; k < K; k += blockDim.x) {
+    double qs = 0;
+    for (int t = 0; t < NC; ++t) qs += qt[(2 * k) * NC + t] + qt[(2 * k + 1) * NC + t];
+    lapk[k] = lt[2 * k] + lt[2 * k + 1] - qs;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double m = -INFINITY;
+    for (int k = 0; k < K; ++k) {
+      const double sk = sg2[2 * k] * sg2[2 * k + 1];
+      if (sk != 0 && ld2[2 * k] + ld2[2 * k + 1] > m) m = ld2[2 * k] + ld2[2 * k + 1];
+    }
+    double S = 0;
+    for (int k = 0; k < K; ++k) {
+      const double sk = sg2[2 * k] * sg2[2 * k + 1];
+      rho[k] = sk != 0 ? sk * f_exp(ld2[2 * k] + ld2[2 * k + 1] - m) : (double)0;
+      S += rho[k];
+    }
+    for (int k = 0; k < K; ++k) rho[k] = S != 0 ? rho[k] / S : (double)0;
+    red[0] = m + f_log(f_abs(S));
+    red[1] = S > 0 ? 1 : (S < 0 ? -1 : 0);
+  }
+  __syncthreads();
+  const double lpsi = (double)red[0];
+  const int sgn = (int)red[1];
+  __syncthreads();
+  // E_kin = -1/2 (|grad log psi|^2 + lap log psi) = -1/2 sum_k rho_k (lap_k + |g_k|^2)
+  double kin = 0;
+  for (int k = tid; k < K; k += blockDim.x) {
+    double g2 = 0;
+    for (int t = 0; t < NC; ++t) g2 += gradk[k * NC + t] * gradk[k * NC + t];
+    kin += rho[k] * (lapk[k] + g2);
+  }
+  double pot = 0.0;
+  const Wlk* rw = r + (int64_t)w * N * 3;
+  for (int p = tid; p < N * N; p += blockDim.x) {
+    const int i = p / N, j = p % N;
+    if (j <= i) continue;
+    const double dx = (double)rw[3 * i] - (double)rw[3 * j], dy = (double)rw[3 * i + 1] - (double)rw[3 * j + 1],
+                 dz = (double)rw[3 * i + 2] - (double)rw[3 * j + 2];
+    pot += 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  for (int p = tid; p < N * sh.M; p += blockDim.x) {
+    const int i = p / sh.M, m = p % sh.M;
+    const double dx = (double)rw[3 * i] - nuc[3 * m], dy = (double)rw[3 * i + 1] - nuc[3 * m + 1],
+                 dz = (double)rw[3 * i + 2] - nuc[3 * m + 2];
+    pot -= a.charges[m] / sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  red[tid] = (double)(-0.5) * kin + (double)pot;
+  __syncthreads();
+  for (int off = 64; off > 0; off >>= 1) {
+    if (tid < off) red[tid] += red[tid + off];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double e = (double)red[0] + a.v_nn;
+    a.e_local[w] = e;
+    if (a.log_psi) a.log_psi[w] = lpsi;
+    if (a.sign) a.sign[w] = (int8_t)sgn;
+    if (sgn == 0) atomicOr(a.status, kStatusSingular);
+    else if (!isfinite(e) || !isfinite(lpsi)) atomicOr(a.status, kStatusNonFinite);
+  }
+}
+
+
 // Value pass (log|psi|, plus the backward seed rho_k A^{-T} when requested): one CTA per
 // walker, one thread per (determinant, spin) block.
 template <typename Det, typename PhiT>
@@ -862,6 +1183,10 @@ void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh,
     cudaFuncSetAttribute(k_det_energy_small<4, Det, Wlk, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_det_energy_small<4, Det, Wlk, PhiT><<<(unsigned)((sh.B + per_cta - 1) / per_cta), 128, smem, st>>>(
         (const Wlk*)walkers, s->d_nuclei, sh, a);
+  } else if (full && std::is_same<Det, double>::value && std::is_same<PhiT, float>::value && nmax <= kGrpN) {
+    const size_t smem = smem_det_energy_grp(s->N, K);
+    cudaFuncSetAttribute(k_det_energy_grp<Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_det_energy_grp<Wlk><<<sh.B, 128, smem, st>>>((const Wlk*)walkers, s->d_nuclei, sh, a);
   } else if (full) {
     const size_t smem = smem_det_energy(sizeof(Det), nmax, s->N, K,
                                         std::is_same<Det, double>::value && std::is_same<PhiT, float>::value);
