@@ -500,6 +500,35 @@ __device__ __forceinline__ void ff_row(const float* __restrict__ chr, const floa
   }
 }
 
+// The same row for two consecutive tangent slabs of a block (D1 = D0 + M^2): the C row is
+// read once and the two sets of accumulators are independent (twice the instruction-level
+// parallelism of ff_row).
+template <int M>
+__device__ __forceinline__ void ff_row2(const float* __restrict__ chr, const float* __restrict__ clr,
+                                        const float* __restrict__ D0, float (&bh0)[kGrpN], float (&bl0)[kGrpN],
+                                        float (&bh1)[kGrpN], float (&bl1)[kGrpN]) {
+  const float* D1 = D0 + M * M;
+#pragma unroll
+  for (int j = 0; j < M; ++j) { bh0[j] = 0.f; bl0[j] = 0.f; bh1[j] = 0.f; bl1[j] = 0.f; }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const float ch = chr[m], cl = clr[m];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      const float d0 = __ldg(D0 + m * M + j), d1 = __ldg(D1 + m * M + j);
+      const float p0 = __fmul_rn(ch, d0), p1 = __fmul_rn(ch, d1);
+      const float pe0 = __fmaf_rn(ch, d0, -p0), pe1 = __fmaf_rn(ch, d1, -p1);
+      float s0, e0, s1, e1;
+      ff_two_sum(bh0[j], p0, s0, e0);
+      ff_two_sum(bh1[j], p1, s1, e1);
+      bh0[j] = s0;
+      bh1[j] = s1;
+      bl0[j] = __fmaf_rn(cl, d0, __fadd_rn(bl0[j], __fadd_rn(e0, pe0)));
+      bl1[j] = __fmaf_rn(cl, d1, __fadd_rn(bl1[j], __fadd_rn(e1, pe1)));
+    }
+  }
+}
+
 template <typename Wlk>
 __global__ void __launch_bounds__(128, 4) k_det_energy_grp(const Wlk* __restrict__ r, const double* __restrict__ nuc,
                                                            Shape sh, DetArgs a) {
@@ -507,9 +536,12 @@ __global__ void __launch_bounds__(128, 4) k_det_energy_grp(const Wlk* __restrict
   const int w = blockIdx.x, tid = threadIdx.x;
   const int N = sh.N, T = sh.T, K = a.K, NC = 3 * N, NM = 2 * K;
   const int ns[2] = {sh.n_up, sh.n_dn};
-  double* gt = (double*)smem_raw;                         // [NM][NC]
-  double* qt = gt + NM * NC;                              // [NM][NC]
-  double* lt = qt + NM * NC;                              // [NM]
+  // g and q of every item as double-FP32 pairs (converted to FP64 in the reductions, where
+  // every lane of a warp has work: an FP64 instruction costs the same warp slot with one
+  // active lane as with 32)
+  float2* gt = (float2*)smem_raw;                         // [NM][NC]
+  float2* qt = gt + NM * NC;                              // [NM][NC]
+  double* lt = (double*)(qt + NM * NC);                   // [NM]
   double* ld2 = lt + NM;                                  // [NM]
   double* sg2 = ld2 + NM;                                 // [NM]
   double* gradk = sg2 + NM;                               // [K][NC]
@@ -631,77 +663,107 @@ __global__ void __launch_bounds__(128, 4) k_det_energy_grp(const Wlk* __restrict
   }
   __syncthreads();
 
-  // 2. tangent items (block p, coordinate tr), four per warp at a time
-  for (int base = (tid >> 5) * 4; base < NM * NC; base += 16) {
+  // 2. tangent items: each group takes two coordinates (tr0, tr0 + 1) of a block per step,
+  // four groups per warp
+  const int NP2 = (NC + 1) / 2;                           // coordinate pairs per block
+  for (int base = (tid >> 5) * 4; base < NM * NP2; base += 16) {
     const int it = base + ((tid >> 3) & 3);
-    const bool live = it < NM * NC;
-    const int p = live ? it / NC : 0, tr = live ? it - (it / NC) * NC : 0;
+    const bool live = it < NM * NP2;
+    const int p = live ? it / NP2 : 0;
+    const int tr0 = live ? 2 * (it - p * NP2) : 0;
+    const bool two = tr0 + 1 < NC;
     const int n = live ? ns[p & 1] : 0;
-    float bh[kGrpN], bl[kGrpN];
+    float bh0[kGrpN], bl0[kGrpN], bh1[kGrpN], bl1[kGrpN];
 #pragma unroll
-    for (int j = 0; j < kGrpN; ++j) { bh[j] = 0.f; bl[j] = 0.f; }
+    for (int j = 0; j < kGrpN; ++j) { bh0[j] = 0.f; bl0[j] = 0.f; bh1[j] = 0.f; bl1[j] = 0.f; }
     float* brow = Bs + (gid * 8 + rr) * kGrpBS;
     {
-      // the orbital tangents are read once, from DRAM: start the block this group takes two
-      // items later on its way into L2 (up to three 128-byte lines)
+      // the orbital tangents are read once, from DRAM: start the pair of blocks this group
+      // takes two steps later on its way into L2 (up to four 128-byte lines)
       const int it2 = it + 32;
-      if (rr < 3 && it2 < NM * NC) {
-        const int p2 = it2 / NC, n2 = ns[p2 & 1];
-        const float* D2 = Phi + blk_off[p2 & 1] + (int64_t)(p2 >> 1) * T * n2 * n2 + (int64_t)(1 + it2 - p2 * NC) * n2 * n2;
-        if (rr * 32 < n2 * n2) asm volatile("prefetch.L2 [%0];" ::"l"(D2 + rr * 32));
+      if (rr < 4 && it2 < NM * NP2) {
+        const int p2 = it2 / NP2, n2 = ns[p2 & 1];
+        const float* D2 = Phi + blk_off[p2 & 1] + (int64_t)(p2 >> 1) * T * n2 * n2 +
+                          (int64_t)(1 + 2 * (it2 - p2 * NP2)) * n2 * n2;
+        if (rr * 32 < 2 * n2 * n2) asm volatile("prefetch.L2 [%0];" ::"l"(D2 + rr * 32));
       }
     }
     if (rr < n) {
-      const float* D = Phi + blk_off[p & 1] + (int64_t)(p >> 1) * T * n * n + (int64_t)(1 + tr) * n * n;
+      // (a block's last odd coordinate runs its pair on the same slab twice and keeps one)
+      const float* D = Phi + blk_off[p & 1] + (int64_t)(p >> 1) * T * n * n + (int64_t)(1 + tr0 - (two ? 0 : 1)) * n * n;
       const float* chr = Cs + ((int64_t)(p * 2) * kGrpN + rr) * kGrpCP;
       const float* clr = chr + kGrpN * kGrpCP;
       switch (n) {
-        case 1: ff_row<1>(chr, clr, D, bh, bl); break;
-        case 2: ff_row<2>(chr, clr, D, bh, bl); break;
-        case 3: ff_row<3>(chr, clr, D, bh, bl); break;
-        case 4: ff_row<4>(chr, clr, D, bh, bl); break;
-        case 5: ff_row<5>(chr, clr, D, bh, bl); break;
-        case 6: ff_row<6>(chr, clr, D, bh, bl); break;
-        case 7: ff_row<7>(chr, clr, D, bh, bl); break;
-        default: ff_row<8>(chr, clr, D, bh, bl); break;
+        case 1: ff_row2<1>(chr, clr, D, bh0, bl0, bh1, bl1); break;
+        case 2: ff_row2<2>(chr, clr, D, bh0, bl0, bh1, bl1); break;
+        case 3: ff_row2<3>(chr, clr, D, bh0, bl0, bh1, bl1); break;
+        case 4: ff_row2<4>(chr, clr, D, bh0, bl0, bh1, bl1); break;
+        case 5: ff_row2<5>(chr, clr, D, bh0, bl0, bh1, bl1); break;
+        case 6: ff_row2<6>(chr, clr, D, bh0, bl0, bh1, bl1); break;
+        case 7: ff_row2<7>(chr, clr, D, bh0, bl0, bh1, bl1); break;
+        default: ff_row2<8>(chr, clr, D, bh0, bl0, bh1, bl1); break;
       }
+      if (!two) {
 #pragma unroll
-      for (int j = 0; j < kGrpN; ++j) {
-        brow[2 * j] = bh[j];
-        brow[2 * j + 1] = bl[j];
+        for (int j = 0; j < kGrpN; ++j) { bh0[j] = bh1[j]; bl0[j] = bl1[j]; }
       }
     }
-    __syncwarp();
-    // g: this row's diagonal entry; q: sum_j B[rr][j] B[j][rr]
-    float gh = 0.f, gl = 0.f, qh = 0.f, ql = 0.f;
-    if (rr < n) {
-      const float* bcol = Bs + (gid * 8) * kGrpBS + 2 * rr;
-      gh = bcol[rr * kGrpBS];
-      gl = bcol[rr * kGrpBS + 1];
+    // g: this row's diagonal entry; q: sum_j B[rr][j] B[j][rr]; the rows of the first slab,
+    // then of the second, pass through the group's staging rows
+    float g0h = 0.f, g0l = 0.f, q0h = 0.f, q0l = 0.f, g1h = 0.f, g1l = 0.f, q1h = 0.f, q1l = 0.f;
+    const float* bcol = Bs + (gid * 8) * kGrpBS + 2 * rr;
 #pragma unroll
-      for (int j = 0; j < kGrpN; ++j)
-        if (j < n) ff_fma_acc(bh[j], bl[j], bcol[j * kGrpBS], bcol[j * kGrpBS + 1], 1.f, qh, ql);
+    for (int half = 0; half < 2; ++half) {
+      float(&bh)[kGrpN] = half ? bh1 : bh0;
+      float(&bl)[kGrpN] = half ? bl1 : bl0;
+      if (rr < n) {
+#pragma unroll
+        for (int j = 0; j < kGrpN; ++j) {
+          brow[2 * j] = bh[j];
+          brow[2 * j + 1] = bl[j];
+        }
+      }
+      __syncwarp();
+      float gh = 0.f, gl = 0.f, qh = 0.f, ql = 0.f;
+      if (rr < n) {
+        gh = bcol[rr * kGrpBS];
+        gl = bcol[rr * kGrpBS + 1];
+#pragma unroll
+        for (int j = 0; j < kGrpN; ++j)
+          if (j < n) ff_fma_acc(bh[j], bl[j], bcol[j * kGrpBS], bcol[j * kGrpBS + 1], 1.f, qh, ql);
+      }
+      __syncwarp();
+      if (half) { g1h = gh; g1l = gl; q1h = qh; q1l = ql; } else { g0h = gh; g0l = gl; q0h = qh; q0l = ql; }
     }
 #pragma unroll
     for (int off = 4; off > 0; off >>= 1) {
-      ff_add_xor(gh, gl, off);
-      ff_add_xor(qh, ql, off);
+      ff_add_xor(g0h, g0l, off);
+      ff_add_xor(q0h, q0l, off);
+      ff_add_xor(g1h, g1l, off);
+      ff_add_xor(q1h, q1l, off);
     }
     if (live && rr == 0) {
-      gt[p * NC + tr] = (double)gh + (double)gl;
-      qt[p * NC + tr] = (double)qh + (double)ql;
+      gt[p * NC + tr0] = make_float2(g0h, g0l);
+      qt[p * NC + tr0] = make_float2(q0h, q0l);
+      if (two) {
+        gt[p * NC + tr0 + 1] = make_float2(g1h, g1l);
+        qt[p * NC + tr0 + 1] = make_float2(q1h, q1l);
+      }
     }
-    __syncwarp();
   }
   __syncthreads();
   // 3. the determinant terms and E_L (as in k_det_energy)
   for (int e = tid; e < K * NC; e += blockDim.x) {
     const int k = e / NC, t = e % NC;
-    gradk[e] = gt[(2 * k) * NC + t] + gt[(2 * k + 1) * NC + t];
+    const float2 g0 = gt[(2 * k) * NC + t], g1 = gt[(2 * k + 1) * NC + t];
+    gradk[e] = ((double)g0.x + (double)g0.y) + ((double)g1.x + (double)g1.y);
   }
   for (int k = tid; k < K; k += blockDim.x) {
     double qs = 0;
-    for (int t = 0; t < NC; ++t) qs += qt[(2 * k) * NC + t] + qt[(2 * k + 1) * NC + t];
+    for (int t = 0; t < NC; ++t) {
+      const float2 q0 = qt[(2 * k) * NC + t], q1 = qt[(2 * k + 1) * NC + t];
+      qs += ((double)q0.x + (double)q0.y) + ((double)q1.x + (double)q1.y);
+    }
     lapk[k] = lt[2 * k] + lt[2 * k + 1] - qs;
   }
   __syncthreads();
