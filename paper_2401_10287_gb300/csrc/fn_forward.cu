@@ -580,7 +580,10 @@ __global__ void __launch_bounds__(128) k_pair_value_mma(const Wlk* __restrict__ 
   // CTAs loop over walkers, so the weights are staged once per CTA
   for (int w = blockIdx.x; w < sh.B; w += gridDim.x) {
   __syncthreads();
-  for (int e = threadIdx.x; e < NPp * 33; e += blockDim.x) gs[e] = 0.f;
+  // the layer-0 input occupies columns 0..15 of each row (features, zero padding, and the
+  // zero features of the i = j pairs); every later column is written by the layer-0 product
+  // before it is read
+  for (int e = threadIdx.x; e < NPp * 16; e += blockDim.x) gs[(e >> 4) * 33 + (e & 15)] = 0.f;
   __syncthreads();
   const Wlk* rw = r + (int64_t)w * N * 3;
   for (int p = threadIdx.x; p < NP; p += blockDim.x) {
@@ -597,13 +600,16 @@ __global__ void __launch_bounds__(128) k_pair_value_mma(const Wlk* __restrict__ 
     const int dg = a.d_g[l];
     __syncthreads();
     __nv_bfloat16* X = (__nv_bfloat16*)a.X[l];
-    for (int e = threadIdx.x; e < N * 2 * dg; e += blockDim.x) {
-      const int ii = e / (2 * dg), s2 = (e / dg) % 2, c = e % dg;
+    // spin means over the partners j of each electron i: warp per (i, spin) row, lane per channel
+    const int64_t xrow0 = tile_row(w, 0, N, sh.wpt);       // a walker's rows are consecutive
+    for (int e2 = warp; e2 < N * 2; e2 += (int)(blockDim.x >> 5)) {
+      const int ii = e2 >> 1, s2 = e2 & 1, c = lane;
+      if (c >= dg) continue;
       const int lo = s2 ? sh.n_up : 0, hi = s2 ? N : sh.n_up;
       float sum = 0.f;
       for (int jj = lo; jj < hi; ++jj) sum += gs[(ii * N + jj) * 33 + c];
       const float mean = hi > lo ? sum / (float)(hi - lo) : 0.f;
-      __nv_bfloat16* o = X + tile_row(w, ii, N, sh.wpt) * a.ldx[l] + a.col0[l] + s2 * dg + c;
+      __nv_bfloat16* o = X + (xrow0 + ii) * a.ldx[l] + a.col0[l] + s2 * dg + c;
       st(o, mean);
       st_lo(o + sh.T * sh.R * a.ldx[l], mean);
     }
