@@ -13,8 +13,9 @@
  *   - Lengths in bohr, energies in hartree.
  *   - d_* pointers are device memory owned by the caller; h_* pointers are host
  *     memory owned by the caller.  The library owns the system handle and an
- *     internal device workspace that grows on demand (cudaMalloc happens only
- *     when a call needs more walkers than any previous call on that handle).
+ *     internal device workspace that grows on demand (a stream-ordered
+ *     allocation on the call's stream happens only when a call needs more
+ *     walkers than any previous call on that handle).
  *   - Calls are asynchronous on the given stream (a cudaStream_t passed as
  *     void*; NULL is the legacy default stream).  Argument errors return
  *     immediately and leave device memory untouched.  Numerical problems found
@@ -37,6 +38,10 @@
  *     time from different host threads, and calls on one handle enqueued on
  *     different streams must be ordered by the caller (they share a workspace).
  *   - fn_last_error() returns a thread-local message for the last failing call.
+ *   - Environment: FN_LAYER_KERNEL=pair selects, for BF16 stream layers whose
+ *     output width is a multiple of 128, the CTA-pair tensor-core kernel
+ *     (cta_group::2) instead of the default one-CTA kernel; the outputs are
+ *     the same bits.  It is read at every layer launch.
  */
 #ifndef FNVMC_H
 #define FNVMC_H
