@@ -1062,6 +1062,72 @@ __global__ void k_envelope_values(const Wlk* __restrict__ r, const double* __res
   envv[row * a.K * sh.N + (spin ? a.K * sh.n_up : 0) + ko] = env;
 }
 
+// The same values with the envelope parameters staged in shared memory, transposed so that
+// the consecutive orbitals of a warp read consecutive words (the global layout puts each
+// orbital's 9 M values 36 M bytes apart: 18 scattered cache lines per load instruction).
+// Grid: (ceil(K (n_up^2 + n_dn^2) / 256), rows striding over the walkers).  Shared memory
+// per spin s: sigma [M][9 or 1][K n_s], then pi [M][K n_s].
+template <typename Wlk>
+__global__ void k_envelope_values_smem(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh,
+                                       OrbArgs a, float* __restrict__ envv) {
+  extern __shared__ __align__(16) float env_smem[];
+  __shared__ float nucf[3 * kMaxNuclei];
+  const int M = sh.M, nc = a.aniso ? 9 : 1;
+  const int off1 = M * (nc + 1) * a.K * sh.n_up;             // spin 1's parameters
+  for (int q = threadIdx.x; q < 3 * M; q += blockDim.x) nucf[q] = (float)nuc[q];
+  for (int sp = 0; sp < 2; ++sp) {
+    const int Kn = a.K * (sp ? sh.n_dn : sh.n_up);
+    float* sig_sp = env_smem + (sp ? off1 : 0);
+    float* pi_sp = sig_sp + M * nc * Kn;
+    const float* sg = (const float*)a.sig[sp];
+    const float* pg = (const float*)a.pi[sp];
+    for (int q = threadIdx.x; q < Kn * M * nc; q += blockDim.x) {
+      const int ko = q / (M * nc), mc = q - ko * (M * nc);           // source order (ko, m, c)
+      sig_sp[mc * Kn + ko] = sg[q];
+    }
+    for (int q = threadIdx.x; q < Kn * M; q += blockDim.x) {
+      const int ko = q / M, m = q - ko * M;
+      pi_sp[m * Kn + ko] = pg[q];
+    }
+  }
+  __syncthreads();
+  const int up_block = a.K * sh.n_up * sh.n_up;
+  const int per_walker = up_block + a.K * sh.n_dn * sh.n_dn;
+  int rem = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rem >= per_walker) return;
+  const int spin = rem < up_block ? 0 : 1;
+  if (spin) rem -= up_block;
+  const int n_s = spin ? sh.n_dn : sh.n_up, Kn = a.K * n_s;
+  const int jj = rem / Kn;
+  const int j = (spin ? sh.n_up : 0) + jj;
+  const int ko = rem - jj * Kn;
+  const float* S0 = env_smem + (spin ? off1 : 0) + ko;
+  const float* P0 = S0 + M * nc * Kn;
+  const int64_t col = (spin ? a.K * sh.n_up : 0) + ko;
+  // the grid's rows stride over the walkers, so the parameters are staged once per CTA
+  for (int w = blockIdx.y; w < sh.B; w += gridDim.y) {
+    const int64_t row = tile_row(w, j, sh.N, sh.wpt);
+    const Wlk* rj = r + ((int64_t)w * sh.N + j) * 3;
+    const float x = (float)rj[0], y = (float)rj[1], z = (float)rj[2];
+    float env = 0.f;
+    for (int m = 0; m < M; ++m) {
+      const float d0 = x - nucf[3 * m], d1 = y - nucf[3 * m + 1], d2 = z - nucf[3 * m + 2];
+      float s2;
+      if (!a.aniso) {
+        s2 = S0[m * Kn] * sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+      } else {
+        const float* S = S0 + m * 9 * Kn;
+        const float u0 = S[0] * d0 + S[Kn] * d1 + S[2 * Kn] * d2;
+        const float u1 = S[3 * Kn] * d0 + S[4 * Kn] * d1 + S[5 * Kn] * d2;
+        const float u2 = S[6 * Kn] * d0 + S[7 * Kn] * d1 + S[8 * Kn] * d2;
+        s2 = sqrtf(u0 * u0 + u1 * u1 + u2 * u2);
+      }
+      env += P0[m * Kn] * __expf(-s2);
+    }
+    envv[row * a.K * sh.N + col] = env;
+  }
+}
+
 template <typename Act, typename Cmp, typename PhiT, typename Wlk, bool FULL>
 __global__ void k_orbitals(const Wlk* __restrict__ r, const double* __restrict__ nuc, Shape sh, OrbArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1247,7 +1313,17 @@ void launch_forward(const fn_system* s, const void* walkers, const Shape& sh, bo
         const_cast<fn_system*>(s)->host_error = FN_ERR_UNSUPPORTED;
         return;
       }
-      k_envelope_values<Wlk><<<(unsigned)((n_env + 255) / 256), 256, 0, st>>>(r, s->d_nuclei, sh, oa, ws.envv);
+      const int nc = oa.aniso ? 9 : 1;
+      const size_t env_smem = sizeof(float) * (size_t)s->M * (nc + 1) * s->cfg.n_dets * (s->n_up + s->n_dn);
+      const int per_walker = s->cfg.n_dets * (s->n_up * s->n_up + s->n_dn * s->n_dn);
+      if (env_smem <= 160 * 1024) {
+        const unsigned gx = (unsigned)((per_walker + 255) / 256);
+        const unsigned gy = (unsigned)std::max(1, std::min(sh.B, (s->sm_count * 8 + (int)gx - 1) / (int)gx));
+        cudaFuncSetAttribute(k_envelope_values_smem<Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env_smem);
+        k_envelope_values_smem<Wlk><<<dim3(gx, gy), 256, env_smem, st>>>(r, s->d_nuclei, sh, oa, ws.envv);
+      } else {
+        k_envelope_values<Wlk><<<(unsigned)((n_env + 255) / 256), 256, 0, st>>>(r, s->d_nuclei, sh, oa, ws.envv);
+      }
       const float* wb[2] = {(const float*)oa.g[0], (const float*)oa.g[1]};
       const float* pis[2] = {(const float*)oa.pi[0], (const float*)oa.pi[1]};
       const float* sgs[2] = {(const float*)oa.sig[0], (const float*)oa.sig[1]};
