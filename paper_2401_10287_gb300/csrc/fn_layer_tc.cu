@@ -1288,7 +1288,6 @@ __device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // The M[t] rows of the walkers that meet this warp's rows (walkers wa .. wa + nwm - 1 of the
 // tile), this CTA's columns n0 + cg0 .. + 31, into the warp's staging rows of 32 floats;
