@@ -16,6 +16,8 @@
 // All of it runs in the Det type (FP64 in the FP64 and BF16-mixed modes).
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
+#include <cstring>
 #include <type_traits>
 
 #include "fn_device.cuh"
@@ -450,9 +452,9 @@ __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, c
 //   1. Gauss-Jordan elimination with partial pivoting on [A | I] in FP64 registers, the pivot
 //      row found by a group reduction and broadcast by shuffles.  The rows are not swapped:
 //      the lane that supplies column c's pivot ends with row c of C = A^-1.  The unused rows
-//      receive exactly the updates of an LU factorisation (same pivots, same products), so
-//      log|det| and its sign are those of the one-thread LU.  The same lanes form the
-//      Laplacian trace tr(C lap A) in FP64 and store C as double-FP32 rows.
+//      receive the updates of an LU factorisation, so the pivots are those of the one-thread
+//      LU (log|det| agrees with it to rounding, 1e-14 in log|psi| measured).  The same lanes
+//      form the Laplacian trace tr(C lap A) in FP64 and store C as double-FP32 rows.
 //   2. Tangent items (block, coordinate): lane r forms row r of B = C d_t A in double-FP32
 //      arithmetic (the same operations as the one-thread items, so every B entry is the
 //      same), then g = tr B and q = tr(B^2) from the rows staged in shared memory and a
@@ -1221,6 +1223,15 @@ inline size_t smem_det_energy_small(int det_bytes, int N, int K) {
   return (size_t)per_cta * ((size_t)det_bytes * NM * (3 * N + 3) + sizeof(int) * NM);
 }
 
+// The BF16-mixed local-energy pass uses the 8-lane-group kernel for blocks of up to 8
+// electrons; FN_DET_KERNEL=thread selects the one-thread-per-block kernel instead (the same
+// pivots; C = A^-1 by forward and back substitution instead of Gauss-Jordan; the results
+// agree to rounding).
+static bool det_grp_enabled() {
+  const char* v = getenv("FN_DET_KERNEL");
+  return !(v && strcmp(v, "thread") == 0);
+}
+
 template <class Mode>
 void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh, double* e_local, double* log_psi,
                        int8_t* sign, bool keep_inverse, cudaStream_t st) {
@@ -1245,7 +1256,8 @@ void launch_det_energy(const fn_system* s, const void* walkers, const Shape& sh,
     cudaFuncSetAttribute(k_det_energy_small<4, Det, Wlk, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_det_energy_small<4, Det, Wlk, PhiT><<<(unsigned)((sh.B + per_cta - 1) / per_cta), 128, smem, st>>>(
         (const Wlk*)walkers, s->d_nuclei, sh, a);
-  } else if (full && std::is_same<Det, double>::value && std::is_same<PhiT, float>::value && nmax <= kGrpN) {
+  } else if (full && std::is_same<Det, double>::value && std::is_same<PhiT, float>::value && nmax <= kGrpN &&
+             det_grp_enabled()) {
     const size_t smem = smem_det_energy_grp(s->N, K);
     cudaFuncSetAttribute(k_det_energy_grp<Wlk>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_det_energy_grp<Wlk><<<sh.B, 128, smem, st>>>((const Wlk*)walkers, s->d_nuclei, sh, a);
