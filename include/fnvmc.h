@@ -41,7 +41,10 @@
  *   - Environment: FN_LAYER_KERNEL=pair selects, for BF16 stream layers whose
  *     output width is a multiple of 128, the CTA-pair tensor-core kernel
  *     (cta_group::2) instead of the default one-CTA kernel; the outputs are
- *     the same bits.  It is read at every layer launch.
+ *     the same bits.  FN_DET_KERNEL=thread selects, for the BF16 local-energy
+ *     determinant stage with blocks of 5 to 8 electrons, one thread per block
+ *     instead of 8-lane groups; the results agree to rounding.  Both are read
+ *     at every launch.
  */
 #ifndef FNVMC_H
 #define FNVMC_H
