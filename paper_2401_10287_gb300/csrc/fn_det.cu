@@ -456,9 +456,9 @@ __global__ void __launch_bounds__(128) k_det_energy(const Wlk* __restrict__ r, c
 //      LU (log|det| agrees with it to rounding, 1e-14 in log|psi| measured).  The same lanes
 //      form the Laplacian trace tr(C lap A) in FP64 and store C as double-FP32 rows.
 //   2. Tangent items (block, coordinate): lane r forms row r of B = C d_t A in double-FP32
-//      arithmetic (the same operations as the one-thread items, so every B entry is the
-//      same), then g = tr B and q = tr(B^2) from the rows staged in shared memory and a
-//      double-FP32 reduction over the group.
+//      arithmetic (the operations of the one-thread items: from the same C they give the
+//      same entries), then g = tr B and q = tr(B^2) from the rows staged in shared memory
+//      and a double-FP32 reduction over the group.
 //   3. The determinant terms are combined and E_L assembled as in k_det_energy.
 constexpr int kGrpN = 8;                 // rows per group (largest block of this kernel)
 constexpr int kGrpCP = kGrpN + 1;        // padded row of a staged C copy (floats)
@@ -480,7 +480,7 @@ __device__ __forceinline__ void ff_add_xor(float& h, float& l, int off) {
 }
 
 // Row r of B = C D for an M x M block: M double-FP32 accumulators (the operations of
-// tangent_item_ff's inner loop, so every entry is the same).
+// tangent_item_ff's inner loop, in the same order).
 template <int M>
 __device__ __forceinline__ void ff_row(const float* __restrict__ chr, const float* __restrict__ clr,
                                        const float* __restrict__ D, float (&bh)[kGrpN], float (&bl)[kGrpN]) {
