@@ -193,3 +193,21 @@ def test_init_params_statistics():
     assert np.all(p["pi_up"] == 1.0)
     np.testing.assert_array_equal(p["sigma_down"][3, 1], np.eye(3))
     assert ansatz.param_count(net) == blob.shape[0]
+
+
+@pytest.mark.parametrize("make,env", [(W.n2, "aniso"), (lambda: W.lih(1), "iso"), (lambda: W.atom(6), "aniso")])
+def test_translation_invariance(make, env):
+    """The method sees positions only as differences: the one-electron features use r_i - R_m,
+    the pair features r_i - r_j, the envelopes of Eq. 4 act on r_j - R_m, and the Coulomb terms
+    on distances.  Moving every nucleus and electron by the same vector therefore leaves
+    log|psi|, its sign and E_L unchanged (up to the rounding of the shifted coordinates)."""
+    s = make()
+    net = _net(s, L=3, h1=16, h2=8, K=2, env=env)
+    blob = _perturbed(net, seed=11)
+    r = _walkers(s, 8, seed=12)
+    shift = np.array([0.75, -1.25, 2.5])
+    e0, lp0, sg0 = ansatz.local_energy(net, blob, s.nuclei, s.charges, r)
+    e1, lp1, sg1 = ansatz.local_energy(net, blob, s.nuclei + shift, s.charges, r + shift)
+    np.testing.assert_array_equal(sg1, sg0)
+    np.testing.assert_allclose(lp1, lp0, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(e1, e0, rtol=1e-8, atol=1e-8)
